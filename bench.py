@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the batched, differentiable MLS-MPM hot path on GB300.
+
+One step = the whole hot path over one batch: 1024 weakly compressible fluid
+environments (8192 particles each, 64^3 grids, moving open container) are rolled out for
+16 control steps x 25 substeps with every control step recorded on the checkpoint tape,
+then the reverse pass runs over the whole horizon (checkpoint restore, substep
+recomputation, adjoint kernels) and returns the action gradients.  The metric counts each
+particle-substep once for its forward and adjoint work:
+    value = particles x substeps x steps / device time  (fwd+adjoint particle-substeps/s).
+
+Printed as one JSON line.  --impl reference times the FP64 oracle on the host cores on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+adjoint particle-substeps/s (batched)"
+UNIT = "particle-substeps/s"
+
+# Algorithmic bytes of each kernel class: (bytes per particle per launch, bytes per active
+# grid node per launch).  FP32 SoA state x(3) v(3) C(9) H(9) = 96 B per particle.
+ALGO_BYTES = {
+    "p2g": (96, 16),       # read x, v, C, H; write (m, p) once per node
+    "g2p": (144, 16),      # read x, H; write x, v, C, H; read grid v once per node
+    "g2p_adj": (192, 32),  # read x, H + adjoint 96 B, write partial x-bar, H-bar; grid v in, v-bar out
+    "p2g_adj": (240, 16),  # read state 96 + partial 48, write adjoint 96; grid (m-bar, p-bar) in
+    "grid": (0, 48),       # read (m, p), write v, clear (m, p)
+    "grid_adj": (0, 80),   # read (m, p), v-bar; write (m-bar, p-bar); clear (m, p), v-bar
+}
+
+# dram__bytes_read.sum + dram__bytes_write.sum per particle of one launch, from the ncu
+# capture summarised in profiles/ (kernel source hash at capture time).  Reported only
+# while the kernel sources are unchanged.
+MEASURED_TRAFFIC = {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "mpm_math.cuh", "mpm_types.h"):
+        with open(os.path.join(ROOT, "paper_2412_12089_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(n_steps_sample=1, seed=0):
+    """The FP64 oracle, as it stands, on one environment of the workload: one control step
+    (25 substeps) forward + reverse, single-threaded."""
+    import numpy as np
+
+    from oracle import oracle as orc
+    from paper_2412_12089_gb300 import workloads as wl
+
+    w = wl.fluid(n_envs=1, seed=seed, T=n_steps_sample)
+    s = w.specs[0]
+    sp = orc.make_spec(s)
+    st = orc.State.from_init(w.inits[0])
+    acts = w.actions[:n_steps_sample, 0, :s.action_dim].astype(np.float64)
+    t0 = time.perf_counter()
+    orc.rollout_adj(sp, st, np.array(s.pose0, np.float64), acts, rbar=np.ones(n_steps_sample))
+    dt = time.perf_counter() - t0
+    ps = s.n_particles * s.substeps * n_steps_sample
+    return ps / dt, dt, (f"1 env x {n_steps_sample} control step(s) x {s.substeps} substeps x "
+                         f"{s.n_particles} particles, forward + checkpointed reverse, FP64, 1 thread")
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_baseline(1)
+    vals = []
+    t0 = time.perf_counter()
+    sample = ""
+    for _ in range(args.steps):
+        v, dt, sample = cpu_baseline(1)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "fluid-1024env-8192p-64grid-16x25", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--envs", type=int, default=1024)
+    ap.add_argument("--particles", type=int, default=8192)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--per-env-sample", type=int, default=32, help="envs in the per-env-launch comparison")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2412_12089_gb300 import mpm
+    from paper_2412_12089_gb300 import workloads as wl
+    from paper_2412_12089_gb300.batch import Batch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    # ---- workload: env shard of this rank (weak scaling: every rank runs a full batch)
+    w = wl.fluid(n_envs=args.envs, n=args.particles, seed=1000 * rank)
+    T, S, P = w.T, w.specs[0].substeps, w.n_particles
+    b = Batch(w.specs, max_steps=T, use_graphs=False, device=local)
+    xs = {k: torch.as_tensor(np.concatenate([getattr(i, k) for i in w.inits])).to(dev) for k in ("x", "v", "C", "F")}
+    poses = torch.as_tensor(np.array([s.pose0 for s in w.specs], np.float32)).to(dev)
+    acts = torch.as_tensor(w.actions).to(dev)
+    rbar = torch.ones(T, b.n_envs, device=dev)
+    agrad = torch.empty(T, b.n_envs, b.A, device=dev)
+    rew = torch.empty(T, b.n_envs, device=dev)
+
+    def one_step():
+        mpm.mpm_set_state(b.ctx, xs["x"], xs["v"], xs["C"], xs["F"], pose=poses)
+        for t in range(T):
+            mpm.mpm_step(b.ctx, acts[t], rew[t], mpm.MPM_STEP_RECORD)
+        mpm.mpm_backward(b.ctx, reward_adj=rbar, action_grad=agrad)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        if i == args.warmup - 1:
+            mpm.mpm_time_kernel(b.ctx, "all")  # survey: which kernel class dominates
+        one_step()
+    torch.cuda.synchronize()
+    tot, cnt = mpm.mpm_kernel_time(b.ctx, all_classes=True)
+    dominant = max((k for k in ALGO_BYTES), key=lambda k: tot[k])
+    mpm.mpm_time_kernel(b.ctx, dominant)
+    tiles = max(mpm.mpm_last_active_tiles(b.ctx), 0)
+
+    # ---- timed region
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = ClockSampler(local)
+    launches0 = mpm.mpm_kernel_launches(b.ctx)
+    barrier()
+    clocks.start()
+    ev0.record(stream)
+    step_ev[0].record(stream)
+    for k in range(args.steps):
+        one_step()
+        step_ev[k + 1].record(stream)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = mpm.mpm_kernel_launches(b.ctx) - launches0
+    dom_ms, dom_n = mpm.mpm_kernel_time(b.ctx)
+    mpm.mpm_time_kernel(b.ctx, 0)
+    step_ms = sorted(step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps))
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    code, flags = b.check_status()
+    value = world * P * T * S * args.steps / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    per_p, per_n = ALGO_BYTES[dominant]
+    n_nodes = tiles * 64
+    algo = per_p * P + per_n * n_nodes
+    avg_s = dom_ms / max(dom_n, 1) / 1e3
+    achieved = algo / avg_s / 1e9 if dom_n else None
+    mt = MEASURED_TRAFFIC.get(dominant)
+    traffic = mt[0] * P if (mt and mt[1] == kernel_source_hash()) else None
+    roofline = {"bound": "hbm", "kernel": f"k_{dominant}", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "algorithmic_bytes_per_launch": algo, "avg_launch_ms": avg_s * 1e3, "launches": dom_n,
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "class_share": {k: round(v / max(sum(tot.values()), 1e-9), 4) for k, v in tot.items() if v > 0}}
+
+    # ---- per-environment-launch path on a sample of the same workload (one control step)
+    per_env = None
+    if args.per_env_sample > 0 and rank == 0:
+        ns = min(args.per_env_sample, args.envs)
+        ws = wl.fluid(n_envs=ns, n=args.particles, seed=7, T=1)
+        res = {}
+        for mode in (False, True):
+            bb = Batch(ws.specs, max_steps=1, per_env_launch=mode, use_graphs=not mode, device=local)
+            a1 = torch.as_tensor(ws.actions[0]).to(dev)
+            rb1 = torch.ones(1, ns, device=dev)
+            ag1 = torch.empty(1, ns, bb.A, device=dev)
+            ts = []
+            for rep in range(4):
+                bb.set_inits(ws.inits)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                mpm.mpm_step(bb.ctx, a1, None, mpm.MPM_STEP_RECORD)
+                mpm.mpm_backward(bb.ctx, reward_adj=rb1, action_grad=ag1)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            res[mode] = ws.n_particles * ws.specs[0].substeps / (min(ts[1:]) / 1e3)
+            bb.close()
+        per_env = {"value": res[True], "batched_value": res[False], "unit": UNIT, "speedup": res[False] / res[True],
+                   "sample": f"{ns} envs x 1 control step x {ws.specs[0].substeps} substeps, fwd+adjoint, same kernels"}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hx = {k: v.cpu().pin_memory() for k, v in xs.items()}
+        hpose = poses.cpu().pin_memory()
+        hact = acts.cpu().pin_memory()
+        hrew = torch.empty(T, b.n_envs).pin_memory()
+        hgrad = torch.empty(T, b.n_envs, b.A).pin_memory()
+        hrbar = torch.ones(T, b.n_envs).pin_memory()
+        reps = max(1, min(args.steps, 2))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            mpm.mpm_set_state(b.ctx, hx["x"], hx["v"], hx["C"], hx["F"], pose=hpose)
+            for t in range(T):
+                mpm.mpm_step(b.ctx, hact[t], hrew[t], mpm.MPM_STEP_RECORD)
+            mpm.mpm_backward(b.ctx, reward_adj=hrbar, action_grad=hgrad)
+            torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        h2d = P * 24 * 4 + b.n_envs * 4 * 4 + acts.numel() * 4 + T * b.n_envs * 4
+        d2h = T * b.n_envs * 4 + T * b.n_envs * b.A * 4
+        e2e = {"value": world * P * T * S * reps / wall, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "reps": reps}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        v, dt, sample = cpu_baseline(1)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"fluid-{args.envs}env-{args.particles}p-64grid-{T}x{S}-fwd+adjoint",
+                       "envs_per_gpu": args.envs, "particles_per_env": args.particles, "grid": 64,
+                       "control_steps": T, "substeps": S, "parallelism": f"env-shard x{world}",
+                       "l2": "inputs larger than L2 (state and grids > 129 MB per pass)",
+                       "launch": "direct (per-class CUDA-event timing on)"},
+            "rollout_ms": {"p50": step_ms[len(step_ms) // 2], "p99": step_ms[-1], "what": "one batched fwd+adjoint rollout"},
+            "per_env_launch": per_env,
+            "clocks": clk, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "status": int(code),
+        }
+        print(json.dumps(line), flush=True)
+    b.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,265 @@
+/*
+ * mpm.h -- C ABI of the batched, differentiable MLS-MPM library for GB300 (sm_103a).
+ *
+ * The library runs the data-parallel hot path of the parallel differentiable
+ * multiphysics simulator of arXiv 2412.12089 ("Stabilizing Reinforcement Learning in
+ * Differentiable Multiphysics Simulation"): many independent MPM environments of
+ * uneven size advance together, one control step (S substeps) per call, forward and in
+ * reverse mode, so a first-order policy learner can back-propagate through them.
+ *
+ *  - One substep is the MLS-MPM P2G -> grid update -> G2P sequence of App. D.3 (the
+ *    paper's "CPIC steps 2-4" of MLS-MPM), with the von Mises elastoplastic law and
+ *    weakly compressible fluid of App. D.3, a compressible neo-Hookean solid, a
+ *    neo-Hookean muscle with an active fibre stress, and App. D.3's softened contact
+ *    s = min(exp(-alpha d), 1) against a kinematic collider moved by the actions.
+ *  - env.step(a_t) -> (s_{t+1}, r_t) is the paper's transition (Alg. 1); rewards follow
+ *    the task definitions of App. E.
+ *  - Gradients are the exact discrete adjoint of the FP32 forward pass (Sec. 4.1), with
+ *    checkpoints at control-step boundaries and the substeps recomputed in reverse
+ *    (Sec. 4.1, gradient checkpointing).
+ *
+ * General conventions
+ *  - Every call returns an mpm_status; no C++ exception crosses the ABI.  On failure
+ *    mpm_last_error() describes the cause.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *    that take a stream are stream-ordered: they enqueue work and return.
+ *  - Array arguments are plain pointers.  Unless stated otherwise they may point to
+ *    device memory or to host memory (the library copies with cudaMemcpyDefault); the
+ *    caller owns them and the library never frees them.  Device memory the library
+ *    allocates itself (particle arena, grids, checkpoint tape) belongs to the context
+ *    and is released by mpm_destroy.
+ *  - Particle arrays cover all environments back to back, in environment order, each
+ *    environment's particles in the caller's order: x[P][3], v[P][3], C[P][3][3],
+ *    F[P][3][3] (row-major 3x3), P = sum of n_particles.  The library reorders particles
+ *    internally (per-cell binning) and always returns arrays in the caller's order.
+ *  - The domain is [0,1]^3 with z up; grid spacing dx = 1/grid_res.
+ *  - Units are SI.
+ */
+#ifndef MPM_GB300_H
+#define MPM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MPM_OK = 0,
+    MPM_ERR_INVALID_ARG = 1, /* bad pointer, size or spec field */
+    MPM_ERR_OOM = 2,         /* device allocation failed */
+    MPM_ERR_CUDA = 3,        /* a CUDA call failed; see mpm_last_error */
+    MPM_ERR_NUMERIC = 4,     /* NaN/Inf or an inverted deformation gradient was flagged */
+    MPM_ERR_DOMAIN = 5,      /* a particle left the grid (its cell index was clamped) */
+    MPM_ERR_TIMEOUT = 6,     /* a bounded wait gave up */
+    MPM_NOT_READY = 7,       /* mpm_poll: the request has not finished */
+    MPM_ERR_BUDGET = 8,      /* a request can never fit the server's memory budget */
+    MPM_ERR_STATE = 9        /* call not valid in the current state (e.g. tape full) */
+} mpm_status;
+
+/* Materials (App. D.3).  NEOHOOKEAN: tau = mu (F F^T - I) + lam log(J) I.
+ * VONMISES: tau = U (2 mu eps + lam tr(eps) I) U^T, eps = log Sigma, with the von Mises
+ * return mapping (threshold c_y * yield_stress / (2 mu); the paper prints c_y = 2).
+ * FLUID: tau = bulk J (J - 1) I + visc J (C + C^T); projection F <- J^(1/3) I.
+ * MUSCLE: neo-Hookean plus a_g * act_stress * (F e_z)(F e_z)^T for particles in actuator
+ * group g (a_g = the group's action). */
+enum { MPM_MAT_NEOHOOKEAN = 0, MPM_MAT_VONMISES = 1, MPM_MAT_FLUID = 2, MPM_MAT_MUSCLE = 3 };
+
+/* Kinematic collider shapes, in the body frame (body pose q = (c_x, c_y, c_z, theta),
+ * theta = yaw about +z).  CAPSULE: axis along body x, coll_dims = (radius, half-length).
+ * BOX: coll_dims = half extents.  CONTAINER: open-top box, coll_dims = (inner half-width,
+ * wall thickness, inner half-height), origin at the cavity centre. */
+enum { MPM_COLL_NONE = 0, MPM_COLL_CAPSULE = 1, MPM_COLL_BOX = 2, MPM_COLL_CONTAINER = 3 };
+
+/* Per-control-step rewards (App. E), on the subsample of the first n_sub particles (in
+ * the caller's order).  FLAT: RollingFlat R_d + R_flat, rparam[0] = h_flat.
+ * REACH: FluidMove R_d of the collider position to rparam[0..2].
+ * JUMP: SoftJumper mean(v_x) + rparam[1] (mean(z) - rparam[0]) - rparam[2] sum(a^2). */
+enum { MPM_REWARD_NONE = 0, MPM_REWARD_FLAT = 1, MPM_REWARD_REACH = 2, MPM_REWARD_JUMP = 3 };
+
+typedef struct {
+    int32_t n_particles;  /* >= 1, <= 1,048,575 */
+    int32_t grid_res;     /* G: multiple of 4, 8..128 */
+    int32_t substeps;     /* S >= 1: substeps per control step, h = S * dt */
+    int32_t bound;        /* wall thickness in nodes (separating slip walls), >= 0 */
+    int32_t material;     /* MPM_MAT_* */
+    int32_t collider;     /* MPM_COLL_* */
+    int32_t n_coll_act;   /* 0..4 leading action entries that move the collider */
+    int32_t act_map[4];   /* pose component (0..3) that action j moves */
+    int32_t n_groups;     /* muscle actuator groups; their actions follow the collider's */
+    int32_t reward;       /* MPM_REWARD_* */
+    int32_t n_sub;        /* reward subsample size */
+    float dt;
+    float gravity[3];
+    float E, nu, rho, p_vol; /* Young's modulus, Poisson ratio, density, particle volume */
+    float yield_stress, c_y;
+    float bulk, visc, act_stress;
+    float coll_dims[4];
+    float coll_mu;        /* collider friction mu_b */
+    float alpha;          /* contact softness, s = min(exp(-alpha d), 1) */
+    float act_scale[4];   /* pose change per unit action per control step */
+    float ground_mu;      /* Coulomb friction of the bottom wall (0 = free slip) */
+    float rparam[4];
+    float pose0[4];       /* initial collider pose */
+} mpm_env_spec;
+
+typedef struct {
+    int32_t max_steps;      /* checkpoint tape capacity in control steps (0 = forward only) */
+    int32_t per_env_launch; /* 1: launch every stage once per environment (baseline path) */
+    int32_t use_graphs;     /* 1: replay control steps as captured CUDA graphs */
+    int32_t chunk;          /* particles per CTA work item, 0 = default */
+    int32_t device;         /* CUDA device ordinal */
+} mpm_options;
+
+typedef struct mpm_ctx mpm_ctx;
+
+/*
+ * Create a batch of n_envs environments.  Allocates (and owns) the particle arena, one
+ * dense grid per environment, the checkpoint tape for opt->max_steps recorded control
+ * steps with its recompute ring, and scratch.  The state starts at rest at the origin
+ * with collider poses pose0; call mpm_set_state before stepping.
+ * Errors: INVALID_ARG for an unusable spec (field named in mpm_last_error), OOM, CUDA.
+ */
+mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* opt, mpm_ctx** out);
+void mpm_destroy(mpm_ctx* ctx);
+
+int32_t mpm_n_envs(const mpm_ctx* ctx);
+int64_t mpm_n_particles(const mpm_ctx* ctx);  /* P */
+int32_t mpm_action_dim(const mpm_ctx* ctx);   /* A_max = max over envs of n_coll_act + n_groups */
+int32_t mpm_tape_length(const mpm_ctx* ctx);  /* control steps recorded since the last reset */
+/* Device bytes the context holds (arena, grids, tape, scratch). */
+int64_t mpm_device_bytes(const mpm_ctx* ctx);
+const char* mpm_last_error(const mpm_ctx* ctx);
+
+/*
+ * Set the particle state (x, v, C, F: layouts above; group: [P] actuator group per
+ * particle, -1 = passive, NULL = all passive) and collider poses (pose: [n_envs][4],
+ * NULL = keep).  Resets the checkpoint tape.  Any pointer may be host or device memory.
+ */
+mpm_status mpm_set_state(mpm_ctx* ctx, const float* x, const float* v, const float* C, const float* F,
+                         const int32_t* group, const float* pose, void* stream);
+/* Copy the current state out, in the caller's particle order (any pointer may be NULL). */
+mpm_status mpm_get_state(mpm_ctx* ctx, float* x, float* v, float* C, float* F, float* pose,
+                         void* stream);
+
+#define MPM_STEP_RECORD 1u /* checkpoint the step's start state for mpm_backward */
+
+/*
+ * Advance every environment by one control step (S substeps).
+ * actions: [n_envs][A_max]; env e reads its first n_coll_act + n_groups entries.  The
+ *   collider moves with constant pose velocity act_scale * a / h over the step.
+ * reward:  [n_envs] output, or NULL.
+ * flags:   MPM_STEP_RECORD to append the step to the tape (STATE if the tape is full);
+ *   without it the tape is reset.
+ */
+mpm_status mpm_step(mpm_ctx* ctx, const float* actions, float* reward, uint32_t flags, void* stream);
+
+/*
+ * Reverse mode over the T = mpm_tape_length recorded steps (Sec. 4.1): each step's
+ * substeps are recomputed from its checkpoint, then reversed.
+ *  xb, vb, Cb, Fb: adjoint of the current (final) state, [P][3] / [P][3][3], or NULL (0).
+ *  reward_adj:     [T][n_envs] adjoint of the rewards returned by the recorded steps, or NULL.
+ *  action_grad:    [T][n_envs][A_max] output (entries past an env's action dim are 0).
+ *  xb0..Fb0:       adjoint of the state at the start of the tape, or NULL.
+ *  pose_grad0:     [n_envs][4] adjoint of the collider pose at the start, or NULL.
+ * The tape is kept, so mpm_backward may be called again with other adjoints.
+ */
+mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const float* Cb, const float* Fb,
+                        const float* reward_adj, float* action_grad, float* xb0, float* vb0, float* Cb0,
+                        float* Fb0, float* pose_grad0, void* stream);
+
+/* Forget the recorded steps; the current state stays. */
+mpm_status mpm_reset_tape(mpm_ctx* ctx);
+
+/*
+ * Synchronise and read the per-environment status words (bit 1: a particle left the
+ * grid, bit 2: NaN/Inf, bit 4: J <= 0), accumulated since the last call, which clears
+ * them.  flags: [n_envs] host array or NULL.  Returns DOMAIN / NUMERIC if any bit is set.
+ */
+mpm_status mpm_check_status(mpm_ctx* ctx, int32_t* flags);
+
+/*
+ * Per-cell binning as the hot path uses it, exposed for bit-exact checks.  x: device
+ * [n][3] positions.  keys[i] = tile-major cell key of particle i: with the cell base
+ * b = clamp(floor(x * G - 0.5), 0, G - 3) per axis (x*G and -0.5 each rounded to
+ * nearest), key = ((bz/4 * G/4 + by/4) * G/4 + bx/4) * 64 + (bz%4)*16 + (by%4)*4 + bx%4.
+ * perm: the stable sort of keys (perm[j] = index of the j-th smallest key, ties in index
+ * order).  keys, perm: device [n].  Uses a device scratch it allocates and frees.
+ */
+mpm_status mpm_bin(const float* x, int32_t n, int32_t grid_res, uint32_t* keys, uint32_t* perm, void* stream);
+
+/* ------------------------------------------------------------------ instrumentation */
+
+/* Kernel classes for mpm_time_kernel. */
+enum { MPM_K_P2G = 1, MPM_K_GRID = 2, MPM_K_G2P = 3, MPM_K_G2P_ADJ = 4, MPM_K_GRID_ADJ = 5, MPM_K_P2G_ADJ = 6,
+       MPM_K_BIN = 7, MPM_K_OTHER = 8 };
+
+/* Number of CUDA kernels this context has launched (a replayed graph counts its kernels). */
+int64_t mpm_kernel_launches(const mpm_ctx* ctx);
+/* Time every launch of one kernel class (MPM_K_*), or of every class (-1), with CUDA events
+ * recorded on the launching stream; 0 = off.  While on, the context launches its kernels
+ * directly instead of replaying graphs. */
+mpm_status mpm_time_kernel(mpm_ctx* ctx, int32_t kernel_class);
+/* Synchronise and return the summed duration (ms) and count of the timed launches since the
+ * last call, which resets them.  One class timed: total_ms[0], launches[0].  All classes
+ * timed: total_ms[k], launches[k] for k = 0..MPM_K_OTHER (arrays of MPM_K_OTHER + 1). */
+mpm_status mpm_kernel_time(mpm_ctx* ctx, double* total_ms, int64_t* launches);
+/* Synchronise and return the number of active 4^3 grid tiles of the last substep. */
+int32_t mpm_last_active_tiles(mpm_ctx* ctx);
+
+/* ------------------------------------------------------------------ serving */
+
+typedef struct mpm_server mpm_server;
+
+typedef struct {
+    double mem_fraction;   /* admission budget as a fraction of device memory, e.g. 0.8 */
+    int32_t max_resident;  /* maximum environments resident at once (slots) */
+    int32_t device;
+    int32_t chunk;         /* particles per CTA work item, 0 = default */
+} mpm_server_options;
+
+typedef struct {
+    mpm_env_spec spec;
+    const float* x;        /* host [n][3] ... as in mpm_set_state */
+    const float* v;
+    const float* C;
+    const float* F;
+    const int32_t* group;  /* host [n] or NULL */
+    int32_t horizon;       /* control steps, >= 1 */
+    const float* actions;  /* host [horizon][A], A = n_coll_act + n_groups */
+    int32_t want_grad;     /* 1: also run the reverse pass after the rollout */
+    const float* reward_adj; /* host [horizon] adjoint of the rewards (NULL = all ones) */
+} mpm_request;
+
+typedef struct {
+    int32_t status;          /* mpm_status of the request */
+    int32_t horizon, action_dim, n_particles;
+    const float* rewards;    /* [horizon] */
+    const float* action_grad;/* [horizon][action_dim], NULL without want_grad */
+    const float* x_final;    /* [n][3], the caller's particle order */
+    double submit_ms, admit_ms, finish_ms; /* host clock, ms since server creation */
+} mpm_result;
+
+/*
+ * A continuous-batching server: requests are admitted while resident environments are
+ * running, as slots and memory free up (admission by memory budget), and all resident
+ * environments advance together, one control step per tick, forward and reverse on two
+ * streams.  Results stay library-owned until mpm_release.
+ */
+mpm_status mpm_server_create(const mpm_server_options* opt, mpm_server** out);
+void mpm_server_destroy(mpm_server* srv);
+/* Copies the request's host arrays; returns at once with a ticket.  BUDGET if the
+ * request alone can never fit the budget. */
+mpm_status mpm_submit(mpm_server* srv, const mpm_request* req, uint64_t* ticket);
+/* Non-blocking: NOT_READY, or OK with *out filled. */
+mpm_status mpm_poll(mpm_server* srv, uint64_t ticket, mpm_result* out);
+/* Block until the ticket finishes or timeout_ms passes (TIMEOUT). */
+mpm_status mpm_wait(mpm_server* srv, uint64_t ticket, double timeout_ms, mpm_result* out);
+mpm_status mpm_release(mpm_server* srv, uint64_t ticket);
+const char* mpm_server_last_error(const mpm_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -532,20 +532,24 @@ static void sdf_capsule(const double* p, const double* dims, double* d, double* 
         }
 }
 
-/* Open-top container: inner half-width a, wall w, inner half-height az; five walls. */
+/* Open-top container: inner cavity [-a,a]^2 x [-az, inf), wall thickness w, as the union
+ * of five boxes.  The walls reach down through the floor and overlap each other at the
+ * vertical edges, so the solid has no internal faces (on a shared face two boxes would
+ * report the same zero distance with opposite normals). */
 static void sdf_container(const double* p, const double* dims, double* d, double* n, double* H)
 {
     double a = dims[0], w = dims[1], az = dims[2];
+    double zc = -0.5 * w, hz = az + 0.5 * w; /* walls span z in [-az - w, az] */
     double cen[5][3] = {{0, 0, -az - 0.5 * w},
-                        {a + 0.5 * w, 0, 0},
-                        {-(a + 0.5 * w), 0, 0},
-                        {0, a + 0.5 * w, 0},
-                        {0, -(a + 0.5 * w), 0}};
+                        {a + 0.5 * w, 0, zc},
+                        {-(a + 0.5 * w), 0, zc},
+                        {0, a + 0.5 * w, zc},
+                        {0, -(a + 0.5 * w), zc}};
     double hal[5][3] = {{a + w, a + w, 0.5 * w},
-                        {0.5 * w, a + w, az},
-                        {0.5 * w, a + w, az},
-                        {a, 0.5 * w, az},
-                        {a, 0.5 * w, az}};
+                        {0.5 * w, a + w, hz},
+                        {0.5 * w, a + w, hz},
+                        {a + w, 0.5 * w, hz},
+                        {a + w, 0.5 * w, hz}};
     double best = INFINITY;
     for (int k = 0; k < 5; k++) {
         double pl[3] = {p[0] - cen[k][0], p[1] - cen[k][1], p[2] - cen[k][2]};

@@ -1,0 +1,1417 @@
+// kernels.cu -- batched MLS-MPM substep kernels and their adjoints (sm_103a, FP32).
+//
+// One substep of every environment in a batch = three launches over all environments:
+//   P2G  (App. D.3 CPIC step 2): one CTA per work item (a run of up to CHUNK particles of
+//        one environment, consecutive in the binned order).  The CTA accumulates mass and
+//        momentum into a shared-memory box spanning its particles' stencils, then flushes
+//        the box to the dense grid with float4 atomics and marks the touched 4^3 tiles
+//        active (appending them to a device list).
+//   GRID (CPIC step 3): persistent warps over the active-tile list; node-local update
+//        (p/m, gravity, softened SDF contact with friction, walls).
+//   G2P  (CPIC step 4): one thread per particle; coalesced SoA reads, 27 float4 grid
+//        gathers through L1, F update and plastic projection, coalesced SoA writes.
+// The adjoint kernels mirror them: G2P^T scatters grid-velocity adjoints with the P2G
+// box scheme, GRID^T is node-local and reduces the collider-pose adjoint per
+// environment, P2G^T gathers grid adjoints per particle (Sec. 4.1 discrete adjoint).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "kernels.h"
+#include "mpm_math.cuh"
+#include "mpm_types.h"
+
+namespace mpm {
+
+constexpr int kBlock = 128;         // threads per particle CTA
+constexpr int kPPT = 2;             // particles per thread
+constexpr int kChunk = kBlock * kPPT;
+constexpr int kBoxNodes = 2048;     // shared-memory box capacity (float4 nodes, 32 KB)
+
+// ------------------------------------------------------------------ common device helpers
+
+__device__ __forceinline__ void load_env(const EnvDesc* envs, int env, EnvDesc& s, EnvCtr& c) {
+  const int* src = reinterpret_cast<const int*>(envs + env);
+  int* dst = reinterpret_cast<int*>(&s);
+  constexpr int W = (int)(sizeof(EnvDesc) / 4);
+  for (int i = threadIdx.x; i < W; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  if (threadIdx.x < 8) reinterpret_cast<int*>(&c)[threadIdx.x] = reinterpret_cast<const int*>(s.ctr)[threadIdx.x];
+  __syncthreads();
+}
+
+__device__ __forceinline__ int ref_slot(const EnvCtr& c, int kind) {
+  switch (kind) {
+    case REF_LIVE: return c.live;
+    case REF_NEXT: return c.next;
+    case REF_REV: return c.base + c.rev;
+    case REF_REVEND: return c.base + c.rev + 1;
+    default: return 0;
+  }
+}
+
+__device__ __forceinline__ float* ref_block(const EnvDesc& e, const EnvCtr& c, StateRef r) {
+  if (r.kind == REF_RING) return e.ring + (long long)(r.k - 1) * e.block;
+  return e.slots + (long long)ref_slot(c, r.kind) * e.block;
+}
+
+// slot whose pose / actions / permutation belong to the running control step
+__device__ __forceinline__ int step_slot(const EnvCtr& c, int rev) { return rev ? c.base + c.rev : c.live; }
+
+__device__ __forceinline__ Mat env_mat(const EnvDesc& e) {
+  Mat m;
+  m.kind = e.material;
+  m.mu = e.mu;
+  m.lam = e.lam;
+  m.cyl = e.cyl;
+  m.bulk = e.bulk;
+  m.visc = e.visc;
+  m.act = e.act_stress;
+  return m;
+}
+
+__device__ __forceinline__ float group_act(const EnvDesc& e, int slot, unsigned meta) {
+  if (e.material != MAT_MUSCLE) return 0.0f;
+  int g = (int)(meta >> 20) - 1;
+  if (g < 0 || g >= e.n_groups) return 0.0f;
+  return e.act[(long long)slot * e.A + e.n_coll_act + g];
+}
+
+__device__ __forceinline__ void load_state(const float* b, long long np, int j, float* s /*24*/) {
+#pragma unroll
+  for (int c = 0; c < kComp; ++c) s[c] = b[c * np + j];
+}
+
+// Shared-memory box over a CTA's particle stencils: node (ix,iy,iz) -> box index.
+struct Box {
+  int lx, ly, lz, nx, ny, nz;
+  bool fits;
+  __device__ __forceinline__ int idx(int ix, int iy, int iz) const { return ((iz - lz) * ny + (iy - ly)) * nx + (ix - lx); }
+};
+
+// Block-wide min/max of the particles' base cells -> box of their stencils (base..base+2).
+__device__ __forceinline__ Box make_box(const int (*base)[3], const bool* valid, int* sred /*6 ints smem*/) {
+  int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-1, -1, -1};
+#pragma unroll
+  for (int p = 0; p < kPPT; ++p)
+    if (valid[p]) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        mn[k] = min(mn[k], base[p][k]);
+        mx[k] = max(mx[k], base[p][k]);
+      }
+    }
+  if (threadIdx.x < 6) sred[threadIdx.x] = threadIdx.x < 3 ? (1 << 30) : -1;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int a = __reduce_min_sync(0xffffffffu, mn[k]);
+    int b = __reduce_max_sync(0xffffffffu, mx[k]);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&sred[k], a);
+      atomicMax(&sred[3 + k], b);
+    }
+  }
+  __syncthreads();
+  Box bx;
+  bx.lx = sred[0];
+  bx.ly = sred[1];
+  bx.lz = sred[2];
+  bx.nx = sred[3] - sred[0] + 3;
+  bx.ny = sred[4] - sred[1] + 3;
+  bx.nz = sred[5] - sred[2] + 3;
+  bx.fits = sred[3] >= 0 && (long long)bx.nx * bx.ny * bx.nz <= kBoxNodes;
+  return bx;
+}
+
+__device__ __forceinline__ void mark_tile(const EnvDesc& e, int env, int ix, int iy, int iz, uint2* active,
+                                          int* active_n) {
+  int TG = e.G >> 2;
+  int t = ((iz >> 2) * TG + (iy >> 2)) * TG + (ix >> 2);
+  unsigned* f = e.tile + t;
+  if (*((volatile unsigned*)f) == 0u) {
+    if (atomicExch(f, 1u) == 0u) {
+      int s = atomicAdd(active_n, 1);
+      active[s] = make_uint2((unsigned)env, (unsigned)t);
+    }
+  }
+}
+
+// Shared-memory box, structure of arrays: component c of box node i at s[c * kBoxNodes + i]
+// (consecutive nodes fall in consecutive banks).
+struct SBox {
+  float v[4 * kBoxNodes];
+};
+
+__device__ __forceinline__ void zero_box(SBox& sb, int vol, int ncomp) {
+  for (int i = threadIdx.x; i < vol; i += blockDim.x)
+    for (int c = 0; c < ncomp; ++c) sb.v[c * kBoxNodes + i] = 0.f;
+}
+
+// Flush a shared box into a dense grid with float4 atomics (nodes whose first, or any for
+// adjoints, component is non-zero), marking tiles if requested.
+template <bool kMark, bool kAnyNonzero>
+__device__ __forceinline__ void flush_box(const EnvDesc& e, int env, const Box& bx, const SBox& sb, float4* grid,
+                                          uint2* active, int* active_n) {
+  int vol = bx.nx * bx.ny * bx.nz;
+  int G = e.G;
+  for (int i = threadIdx.x; i < vol; i += blockDim.x) {
+    float4 val = make_float4(sb.v[i], sb.v[kBoxNodes + i], sb.v[2 * kBoxNodes + i], sb.v[3 * kBoxNodes + i]);
+    bool nz = kAnyNonzero ? (val.x != 0.0f || val.y != 0.0f || val.z != 0.0f || val.w != 0.0f) : (val.x != 0.0f);
+    if (!nz) continue;
+    int ix = bx.lx + i % bx.nx;
+    int r = i / bx.nx;
+    int iy = bx.ly + r % bx.ny;
+    int iz = bx.lz + r / bx.ny;
+    atomicAdd(grid + ((long long)iz * G + iy) * G + ix, val);
+    if (kMark) mark_tile(e, env, ix, iy, iz, active, active_n);
+  }
+}
+
+// Stencil node k in 0..26 -> offsets (a, b, c); lane l visits node (n + l) mod 27 at step n,
+// so binned particles of one cell (adjacent lanes) update different shared nodes at once.
+__device__ __forceinline__ void stencil_node(int k, int& a, int& b, int& c) {
+  c = k / 9;
+  const int r = k - 9 * c;
+  b = r / 3;
+  a = r - 3 * b;
+}
+
+__device__ __forceinline__ float pick3(int i, const float* w) { return i == 0 ? w[0] : (i == 1 ? w[1] : w[2]); }
+
+// ------------------------------------------------------------------ P2G
+
+__global__ void __launch_bounds__(kBlock) k_p2g(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
+                                                int item_off, StateRef src, int use_perm, int k, int rev,
+                                                uint2* active, int* active_n) {
+  __shared__ EnvDesc e;
+  __shared__ EnvCtr c;
+  __shared__ int sred[6];
+  __shared__ SBox sb;
+  const WorkItem it = items[item_off + blockIdx.x];
+  load_env(envs, it.env, e, c);
+  const float* b = ref_block(e, c, src);
+  const int sslot = step_slot(c, rev);
+  const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
+  const long long np = e.n_pad;
+  const float G = (float)e.G;
+  int base[kPPT][3];
+  bool valid[kPPT];
+  int jj[kPPT];
+  int oob = 0;
+#pragma unroll
+  for (int p = 0; p < kPPT; ++p) {
+    int i = it.start + threadIdx.x + p * kBlock;
+    valid[p] = i < it.start + it.count;
+    int j = valid[p] ? (perm ? (int)perm[i] : i) : 0;
+    jj[p] = j;
+    if (valid[p]) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) base[p][a] = cell_base(b[a * np + j], G, e.G, &oob);
+    }
+  }
+  Box bx = make_box(base, valid, sred);
+  if (bx.fits) {
+    zero_box(sb, bx.nx * bx.ny * bx.nz, 4);
+    __syncthreads();
+  }
+  const Mat m = env_mat(e);
+  const float Dinv = 4.0f * G * G;
+  const float stress_k = -e.dt * e.p_vol * Dinv;
+  const float pm = e.p_mass;
+  const int lane_off = (threadIdx.x & 31) % 27;
+#pragma unroll 1
+  for (int p = 0; p < kPPT; ++p) {
+    if (!valid[p]) continue;
+    const int j = jj[p];
+    float s[kComp];
+    load_state(b, np, j, s);
+    unsigned meta = reinterpret_cast<const unsigned*>(b + kComp * np)[j];
+    float a_g = group_act(e, sslot, meta);
+    float tau[9];
+    kirchhoff(m, s + 15, s + 6, a_g, tau);
+    float A[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) A[q] = pm * s[6 + q] + stress_k * tau[q];
+    float fx[3], w[3][3], dw[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      fx[a] = __fmul_rn(s[a], G) - (float)base[p][a];
+      bspline(fx[a], w[a], dw);
+    }
+    const float mv0 = pm * s[3], mv1 = pm * s[4], mv2 = pm * s[5];
+    const float dx = e.dx;
+    const int b0 = base[p][0], b1 = base[p][1], b2 = base[p][2];
+#pragma unroll 9
+    for (int n = 0; n < 27; ++n) {
+      int k = n + lane_off;
+      k = k >= 27 ? k - 27 : k;
+      int cx, cy, cz;
+      stencil_node(k, cx, cy, cz);
+      const float rx = ((float)cx - fx[0]) * dx, ry = ((float)cy - fx[1]) * dx, rz = ((float)cz - fx[2]) * dx;
+      const float wt = pick3(cx, w[0]) * pick3(cy, w[1]) * pick3(cz, w[2]);
+      float4 add;
+      add.x = wt * pm;
+      add.y = wt * (mv0 + A[0] * rx + A[1] * ry + A[2] * rz);
+      add.z = wt * (mv1 + A[3] * rx + A[4] * ry + A[5] * rz);
+      add.w = wt * (mv2 + A[6] * rx + A[7] * ry + A[8] * rz);
+      const int ix = b0 + cx, iy = b1 + cy, iz = b2 + cz;
+      if (bx.fits) {
+        const int bi = bx.idx(ix, iy, iz);
+        atomicAdd(&sb.v[bi], add.x);
+        atomicAdd(&sb.v[kBoxNodes + bi], add.y);
+        atomicAdd(&sb.v[2 * kBoxNodes + bi], add.z);
+        atomicAdd(&sb.v[3 * kBoxNodes + bi], add.w);
+      } else {
+        atomicAdd(e.grid_mp + ((long long)iz * e.G + iy) * e.G + ix, add);
+      }
+    }
+    if (!bx.fits) {
+      for (int cz = 0; cz < 3; cz += 2)
+        for (int cy = 0; cy < 3; cy += 2)
+          for (int cx = 0; cx < 3; cx += 2)
+            mark_tile(e, it.env, base[p][0] + cx, base[p][1] + cy, base[p][2] + cz, active, active_n);
+    }
+  }
+  if (oob) atomicOr(&e.ctr->status, 1);
+  if (bx.fits) {
+    __syncthreads();
+    flush_box<true, false>(e, it.env, bx, sb, e.grid_mp, active, active_n);
+  }
+}
+
+// ------------------------------------------------------------------ grid update
+
+struct NodeFwd {
+  float v0[3], v1[3], v2[3], v3[3];
+  float sc, vn, L, f, gL, gf;
+  float vr[3], vt[3], vr2[3];
+  float dl[3];  // vr2 - vr, evaluated without cancellation
+  int branch, ground;
+  unsigned zero;
+  Contact ct;
+};
+
+// Forward node update; records the trace needed by its adjoint.
+template <bool kAdj>
+__device__ __forceinline__ void node_forward(const EnvDesc& e, int ix, int iy, int iz, float4 mp, const float* q,
+                                             const float* u, NodeFwd& t) {
+  const float inv_m = 1.0f / mp.x;
+  t.v0[0] = mp.y * inv_m;
+  t.v0[1] = mp.z * inv_m;
+  t.v0[2] = mp.w * inv_m;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t.v1[i] = t.v0[i] + e.dt * e.gravity[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t.v2[i] = t.v1[i];
+  t.branch = 0;
+  if (e.coll_kind != COLL_NONE) {
+    Coll cl;
+    cl.kind = e.coll_kind;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cl.dims[i] = e.coll_dims[i];
+    cl.mu = e.coll_mu;
+    cl.alpha = e.alpha;
+    contact_eval<kAdj>(cl, ix * e.dx, iy * e.dx, iz * e.dx, q, u, t.ct);
+    t.sc = t.ct.d > 0.0f ? expf(-e.alpha * t.ct.d) : 1.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t.vr[i] = t.v1[i] - t.ct.vb[i];
+    t.vn = t.vr[0] * t.ct.n[0] + t.vr[1] * t.ct.n[1] + t.vr[2] * t.ct.n[2];
+    // v2 = v1 + s (v_proj - v1) with v_proj = vr2 + vb, i.e. v1 + s (vr2 - vr).  The
+    // difference dl = vr2 - vr is formed directly: 0 when separating, vn (mu vt/L - n)
+    // when sliding, -vr when stopped.  (Adding vb back and subtracting v1 in FP32 would
+    // leave an ulp of |vb| on every node the collider touches.)
+    if (t.vn < 0.0f) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) t.vt[i] = t.vr[i] - t.vn * t.ct.n[i];
+      t.L = sqrtf(t.vt[0] * t.vt[0] + t.vt[1] * t.vt[1] + t.vt[2] * t.vt[2]);
+      t.f = t.L > 0.0f ? 1.0f + e.coll_mu * t.vn / t.L : 0.0f;
+      if (t.f > 0.0f) {
+        t.branch = 1;
+        const float muL = e.coll_mu / t.L;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          t.vr2[i] = t.f * t.vt[i];
+          t.dl[i] = t.vn * (muL * t.vt[i] - t.ct.n[i]);
+        }
+      } else {
+        t.branch = 2;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          t.vr2[i] = 0.0f;
+          t.dl[i] = -t.vr[i];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        t.vr2[i] = t.vr[i];
+        t.dl[i] = 0.0f;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t.v2[i] = t.v1[i] + t.sc * t.dl[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) t.v3[i] = t.v2[i];
+  t.ground = 0;
+  const int bnd = e.bound, G = e.G;
+  if (iz < bnd && t.v2[2] < 0.0f) {
+    t.ground = 1;
+    if (e.ground_mu > 0.0f) {
+      t.gL = sqrtf(t.v2[0] * t.v2[0] + t.v2[1] * t.v2[1]);
+      t.gf = t.gL > 0.0f ? fmaxf(0.0f, 1.0f + e.ground_mu * t.v2[2] / t.gL) : 0.0f;
+      t.v3[0] *= t.gf;
+      t.v3[1] *= t.gf;
+    }
+    t.v3[2] = 0.0f;
+  }
+  t.zero = 0u;
+  if ((ix < bnd && t.v3[0] < 0.0f) || (ix >= G - bnd && t.v3[0] > 0.0f)) t.zero |= 1u;
+  if ((iy < bnd && t.v3[1] < 0.0f) || (iy >= G - bnd && t.v3[1] > 0.0f)) t.zero |= 2u;
+  if (iz >= G - bnd && t.v3[2] > 0.0f) t.zero |= 4u;
+}
+
+__device__ __forceinline__ void step_pose(const EnvDesc& e, const EnvCtr& c, int rev, int k, float* q, float* u) {
+  const int slot = step_slot(c, rev);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    u[i] = e.acc[ACC_U + i];
+    q[i] = e.pose[slot * 4 + i] + (float)k * e.dt * u[i];
+  }
+}
+
+// Persistent warps over the active-tile list; one warp per 4^3 tile, two nodes per lane.
+__global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, const uint2* __restrict__ active,
+                                              const int* __restrict__ active_n, int k, int mode, int rev) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int n = *active_n;
+  for (int w = warp; w < n; w += nwarps) {
+    const uint2 at = active[w];
+    const EnvDesc& e = envs[at.x];
+    const EnvCtr c = *e.ctr;
+    float q[4], u[4];
+    step_pose(e, c, rev, k, q, u);
+    const int TG = e.G >> 2;
+    const int tz = at.y / (TG * TG), ty = (at.y / TG) % TG, tx = at.y % TG;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int l = lane + 32 * h;
+      const int ix = tx * 4 + (l & 3), iy = ty * 4 + ((l >> 2) & 3), iz = tz * 4 + (l >> 4);
+      const long long id = ((long long)iz * e.G + iy) * e.G + ix;
+      const float4 mp = e.grid_mp[id];
+      float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (mp.x > 0.0f) {
+        NodeFwd t;
+        node_forward<false>(e, ix, iy, iz, mp, q, u, t);
+        out.x = (t.zero & 1u) ? 0.0f : t.v3[0];
+        out.y = (t.zero & 2u) ? 0.0f : t.v3[1];
+        out.z = (t.zero & 4u) ? 0.0f : t.v3[2];
+      }
+      e.grid_v[id] = out;
+      if (mode == GRID_FWD) e.grid_mp[id] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (mode == GRID_FWD && lane == 0) e.tile[at.y] = 0u;
+  }
+}
+
+// ------------------------------------------------------------------ G2P
+
+__global__ void __launch_bounds__(kBlock) k_g2p(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
+                                                int item_off, StateRef src, StateRef dst, int use_perm, int rev) {
+  __shared__ EnvDesc e;
+  __shared__ EnvCtr c;
+  const WorkItem it = items[item_off + blockIdx.x];
+  load_env(envs, it.env, e, c);
+  const float* b = ref_block(e, c, src);
+  float* o = ref_block(e, c, dst);
+  const int sslot = step_slot(c, rev);
+  const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
+  const long long np = e.n_pad;
+  const float G = (float)e.G;
+  const Mat m = env_mat(e);
+  const float Dinv = 4.0f * G * G, dt = e.dt, dx = e.dx;
+  int status = 0;
+#pragma unroll 1
+  for (int p = 0; p < kPPT; ++p) {
+    const int i = it.start + threadIdx.x + p * kBlock;
+    if (i >= it.start + it.count) continue;
+    const int j = perm ? (int)perm[i] : i;
+    float x[3], F[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = b[a * np + j];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) F[a] = b[(15 + a) * np + j];
+    int base[3], oob = 0;
+    float fx[3], w[3][3], dw[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      base[a] = cell_base(x[a], G, e.G, &oob);
+      fx[a] = __fmul_rn(x[a], G) - (float)base[a];
+      bspline(fx[a], w[a], dw);
+    }
+    if (oob) status |= 1;
+    float v[3] = {0.f, 0.f, 0.f}, C[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) C[a] = 0.f;
+    // C = D^-1 sum w (v_i - v_c) r^T: the stencil-centre velocity v_c contributes
+    // v_c (sum w r)^T = 0, and subtracting it keeps the FP32 sum from cancelling.
+    const float4 vc = __ldg(e.grid_v + ((long long)(base[2] + 1) * e.G + (base[1] + 1)) * e.G + base[0] + 1);
+#pragma unroll
+    for (int cz = 0; cz < 3; ++cz) {
+      const float rz = ((float)cz - fx[2]) * dx;
+#pragma unroll
+      for (int cy = 0; cy < 3; ++cy) {
+        const float ry = ((float)cy - fx[1]) * dx;
+        const float wyz = w[1][cy] * w[2][cz];
+        const float4* row = e.grid_v + ((long long)(base[2] + cz) * e.G + (base[1] + cy)) * e.G + base[0];
+#pragma unroll
+        for (int cx = 0; cx < 3; ++cx) {
+          const float rx = ((float)cx - fx[0]) * dx;
+          const float wt = w[0][cx] * wyz;
+          const float4 gv = __ldg(row + cx);
+          v[0] += wt * gv.x;
+          v[1] += wt * gv.y;
+          v[2] += wt * gv.z;
+          const float d0 = Dinv * wt * (gv.x - vc.x), d1 = Dinv * wt * (gv.y - vc.y), d2 = Dinv * wt * (gv.z - vc.z);
+          C[0] += d0 * rx; C[1] += d0 * ry; C[2] += d0 * rz;
+          C[3] += d1 * rx; C[4] += d1 * ry; C[5] += d1 * rz;
+          C[6] += d2 * rx; C[7] += d2 * ry; C[8] += d2 * rz;
+        }
+      }
+    }
+    // F <- (I + dt C) F, i.e. H <- H + dt (C + C H); then the plastic projection
+    float CH[9], Ht[9], Fo[9];
+    matmul3(C, F, CH);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Ht[a] = F[a] + dt * (C[a] + CH[a]);
+    project(m, Ht, Fo);
+    float xn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      xn[a] = x[a] + dt * v[a];
+      o[a * np + i] = xn[a];
+      o[(3 + a) * np + i] = v[a];
+      if (!isfinite(xn[a])) status |= 2;
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      o[(6 + a) * np + i] = C[a];
+      o[(15 + a) * np + i] = Fo[a];
+    }
+    if (!(1.0f + detm1(Fo) > 0.0f)) status |= 4;
+    if (perm || b != o) reinterpret_cast<unsigned*>(o + kComp * np)[i] = reinterpret_cast<const unsigned*>(b + kComp * np)[j];
+  }
+  status = __reduce_or_sync(0xffffffffu, status);
+  if (status && (threadIdx.x & 31) == 0) atomicOr(&e.ctr->status, status);
+}
+
+// ------------------------------------------------------------------ step bookkeeping
+
+// One thread per environment: choose the slot the step writes, store the step's actions,
+// compute the collider's pose velocity u = act_scale * a / h.
+__global__ void k_step_begin(const EnvDesc* __restrict__ envs, int env0, int n_env, const float* act_in, int a_max,
+                             int record) {
+  int ei = env0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (ei >= env0 + n_env) return;
+  const EnvDesc& e = envs[ei];
+  EnvCtr* c = e.ctr;
+  int live = c->live;
+  c->next = record ? live + 1 : (live == 0 ? 1 : 0);
+  const float* a = act_in + (long long)ei * a_max;
+  for (int j = 0; j < e.A; ++j) e.act[(long long)live * e.A + j] = a[j];
+  const float h = e.S * e.dt;
+  float u[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int j = 0; j < e.n_coll_act; ++j) u[e.act_map[j]] += e.act_scale[j] * a[j] / h;
+  for (int i = 0; i < 4; ++i) e.acc[ACC_U + i] = u[i];
+}
+
+__device__ __forceinline__ float block_sum(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) r += sh[i];
+  return r;
+}
+
+// Reward statistics over the subsample (particles with caller id < n_sub) of a block.
+// Two passes for the variance.  Returns (mean z, var z, mean v_x, n).
+__device__ void subsample_stats(const EnvDesc& e, const float* b, float* sh, float* st) {
+  const long long np = e.n_pad;
+  const unsigned* meta = reinterpret_cast<const unsigned*>(b + kComp * np);
+  const int ns = min(e.n_sub, e.n);
+  float sz = 0.f, sv = 0.f;
+  for (int i = threadIdx.x; i < e.n; i += blockDim.x) {
+    if ((int)(meta[i] & kIdMask) < ns) {
+      sz += b[2 * np + i];
+      sv += b[3 * np + i];
+    }
+  }
+  sz = block_sum(sz, sh);
+  sv = block_sum(sv, sh);
+  const float mz = sz / ns;
+  float sq = 0.f;
+  for (int i = threadIdx.x; i < e.n; i += blockDim.x) {
+    if ((int)(meta[i] & kIdMask) < ns) {
+      float d = b[2 * np + i] - mz;
+      sq += d * d;
+    }
+  }
+  sq = block_sum(sq, sh);
+  st[0] = mz;
+  st[1] = sq / ns;
+  st[2] = sv / ns;
+  st[3] = (float)ns;
+}
+
+__device__ __forceinline__ float rd_factor(float d, float thr) { return (d > thr) ? 1.0f : 2.0f; }
+
+// One CTA per environment: reward of the finished step, end pose, counters.
+__global__ void __launch_bounds__(256) k_reward_end(const EnvDesc* __restrict__ envs, int env0, float* reward_out,
+                                                    int record) {
+  __shared__ float sh[32];
+  const int ei = env0 + blockIdx.x;
+  const EnvDesc& e = envs[ei];
+  EnvCtr* cp = e.ctr;
+  const int live = cp->live, next = cp->next;
+  const float* b = e.slots + (long long)next * e.block;
+  float stats[4] = {0.f, 0.f, 0.f, 0.f};
+  if (e.reward_kind == 1 || e.reward_kind == 3) subsample_stats(e, b, sh, stats);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float h = e.S * e.dt;
+    float qn[4];
+    for (int i = 0; i < 4; ++i) qn[i] = e.pose[live * 4 + i] + h * e.acc[ACC_U + i];
+    for (int i = 0; i < 4; ++i) e.pose[next * 4 + i] = qn[i];
+    float r = 0.f;
+    if (e.reward_kind == 1) {
+      float d = stats[0] / e.rparam[0];
+      r = rd_factor(d, 0.33f) / ((1.f + d) * (1.f + d)) - stats[1];
+    } else if (e.reward_kind == 2) {
+      float d = 0.f;
+      for (int i = 0; i < 3; ++i) d += (qn[i] - e.rparam[i]) * (qn[i] - e.rparam[i]);
+      r = rd_factor(d, 0.02f) / ((1.f + d) * (1.f + d));
+    } else if (e.reward_kind == 3) {
+      float aa = 0.f;
+      for (int j = 0; j < e.A; ++j) {
+        float a = e.act[(long long)live * e.A + j];
+        aa += a * a;
+      }
+      r = stats[2] + e.rparam[1] * (stats[0] - e.rparam[0]) - e.rparam[2] * aa;
+    }
+    if (reward_out) reward_out[ei] = r;
+    cp->live = next;
+    if (!record) cp->base = next;
+  }
+}
+
+// ------------------------------------------------------------------ adjoint: G2P^T
+
+__global__ void __launch_bounds__(kBlock) k_g2p_adj(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
+                                                    int item_off, StateRef src, int use_perm) {
+  __shared__ EnvDesc e;
+  __shared__ EnvCtr c;
+  __shared__ int sred[6];
+  __shared__ SBox sb;
+  const WorkItem it = items[item_off + blockIdx.x];
+  load_env(envs, it.env, e, c);
+  const float* b = ref_block(e, c, src);
+  float* adj = c.par ? e.adj1 : e.adj0;
+  const int sslot = step_slot(c, 1);
+  const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
+  const long long np = e.n_pad;
+  const float G = (float)e.G;
+  int base[kPPT][3];
+  bool valid[kPPT];
+  int jj[kPPT];
+  int oob = 0;
+#pragma unroll
+  for (int p = 0; p < kPPT; ++p) {
+    int i = it.start + threadIdx.x + p * kBlock;
+    valid[p] = i < it.start + it.count;
+    int j = valid[p] ? (perm ? (int)perm[i] : i) : 0;
+    jj[p] = j;
+    if (valid[p]) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) base[p][a] = cell_base(b[a * np + j], G, e.G, &oob);
+    }
+  }
+  Box bx = make_box(base, valid, sred);
+  if (bx.fits) {
+    zero_box(sb, bx.nx * bx.ny * bx.nz, 3);
+    __syncthreads();
+  }
+  const Mat m = env_mat(e);
+  const float Dinv = 4.0f * G * G, dt = e.dt, dx = e.dx;
+  const int lane_off = (threadIdx.x & 31) % 27;
+  const float vref[3] = {e.acc[ACC_VREF], e.acc[ACC_VREF + 1], e.acc[ACC_VREF + 2]};
+#pragma unroll 1
+  for (int p = 0; p < kPPT; ++p) {
+    if (!valid[p]) continue;
+    const int i = it.start + threadIdx.x + p * kBlock;
+    const int j = jj[p];
+    float x[3], F[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = b[a * np + j];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) F[a] = b[(15 + a) * np + j];
+    float fx[3], w[3][3], dwv[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      fx[a] = __fmul_rn(x[a], G) - (float)base[p][a];
+      bspline(fx[a], w[a], dwv[a]);
+    }
+    // recompute v', C'
+    float vn[3] = {0.f, 0.f, 0.f}, Cn[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Cn[a] = 0.f;
+    const float4 vc =
+        __ldg(e.grid_v + ((long long)(base[p][2] + 1) * e.G + (base[p][1] + 1)) * e.G + base[p][0] + 1);
+#pragma unroll
+    for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+      for (int cy = 0; cy < 3; ++cy) {
+        const float4* row = e.grid_v + ((long long)(base[p][2] + cz) * e.G + (base[p][1] + cy)) * e.G + base[p][0];
+#pragma unroll
+        for (int cx = 0; cx < 3; ++cx) {
+          const float wt = w[0][cx] * w[1][cy] * w[2][cz];
+          const float4 gv = __ldg(row + cx);
+          const float r[3] = {((float)cx - fx[0]) * dx, ((float)cy - fx[1]) * dx, ((float)cz - fx[2]) * dx};
+          vn[0] += wt * gv.x;
+          vn[1] += wt * gv.y;
+          vn[2] += wt * gv.z;
+          const float g3[3] = {gv.x - vc.x, gv.y - vc.y, gv.z - vc.z};
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) Cn[3 * a + bb] += Dinv * wt * g3[a] * r[bb];
+        }
+      }
+    // trial H_t = H + dt (C' + C' H)   (F here holds H = F - I)
+    float CH[9], Ft[9];
+    matmul3(Cn, F, CH);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Ft[a] = F[a] + dt * (Cn[a] + CH[a]);
+    // incoming adjoint of the end state
+    float xb[3], vb[3], Cb[9], Fob[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      xb[a] = adj[a * np + i];
+      vb[a] = adj[(3 + a) * np + i];
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      Cb[a] = adj[(6 + a) * np + i];
+      Fob[a] = adj[(15 + a) * np + i];
+    }
+    float Ftb[9];
+    project_vjp(m, Ft, Fob, Ftb);
+    // F_t = (I + dt C') F:  Cb += dt Ftb F^T = dt (Ftb + Ftb H^T);  Fb_partial = Ftb + dt C'^T Ftb
+    float Fbp[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb) {
+        Cb[3 * a + bb] += dt * (Ftb[3 * a + bb] + Ftb[3 * a] * F[3 * bb] + Ftb[3 * a + 1] * F[3 * bb + 1] +
+                                Ftb[3 * a + 2] * F[3 * bb + 2]);
+        Fbp[3 * a + bb] = Ftb[3 * a + bb] + dt * (Cn[a] * Ftb[bb] + Cn[3 + a] * Ftb[3 + bb] + Cn[6 + a] * Ftb[6 + bb]);
+      }
+    // x' = x + dt v'
+    float vnb[3] = {vb[0] + dt * xb[0], vb[1] + dt * xb[1], vb[2] + dt * xb[2]};
+    float xbp[3] = {xb[0], xb[1], xb[2]};
+    // the grid receives sum w (v-bar' - V_ref); V_ref m_i/m_p is restored in the grid adjoint
+    const float vsh[3] = {vnb[0] - vref[0], vnb[1] - vref[1], vnb[2] - vref[2]};
+#pragma unroll 3
+    for (int nn = 0; nn < 27; ++nn) {
+      int kk = nn + lane_off;
+      kk = kk >= 27 ? kk - 27 : kk;
+      int cx, cy, cz;
+      stencil_node(kk, cx, cy, cz);
+      {
+        {
+          const float wxa = pick3(cx, w[0]), wyb = pick3(cy, w[1]), wzc = pick3(cz, w[2]);
+          const float wt = wxa * wyb * wzc;
+          const float gw[3] = {pick3(cx, dwv[0]) * wyb * wzc * G, wxa * pick3(cy, dwv[1]) * wzc * G,
+                               wxa * wyb * pick3(cz, dwv[2]) * G};
+          const float r[3] = {((float)cx - fx[0]) * dx, ((float)cy - fx[1]) * dx, ((float)cz - fx[2]) * dx};
+          const float4 gv = __ldg(e.grid_v + ((long long)(base[p][2] + cz) * e.G + (base[p][1] + cy)) * e.G +
+                                  base[p][0] + cx);
+          // v_i - v_c: the stencil-uniform part of v_i adds nothing to x-bar (sum grad w = 0,
+          // sum r grad w^T = I), so it is removed before the FP32 sums
+          const float g3[3] = {gv.x - vc.x, gv.y - vc.y, gv.z - vc.z};
+          float Cr[3], CTv[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            Cr[a] = Cb[3 * a] * r[0] + Cb[3 * a + 1] * r[1] + Cb[3 * a + 2] * r[2];
+            CTv[a] = Cb[a] * g3[0] + Cb[3 + a] * g3[1] + Cb[6 + a] * g3[2];
+          }
+          float4 add;
+          add.x = wt * vsh[0] + Dinv * wt * Cr[0];
+          add.y = wt * vsh[1] + Dinv * wt * Cr[1];
+          add.z = wt * vsh[2] + Dinv * wt * Cr[2];
+          add.w = 0.0f;
+          const float sdw = vnb[0] * g3[0] + vnb[1] * g3[1] + vnb[2] * g3[2] +
+                            Dinv * (g3[0] * Cr[0] + g3[1] * Cr[1] + g3[2] * Cr[2]);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) xbp[a] += sdw * gw[a] - Dinv * wt * CTv[a];
+          const int ix = base[p][0] + cx, iy = base[p][1] + cy, iz = base[p][2] + cz;
+          if (bx.fits) {
+            const int bi = bx.idx(ix, iy, iz);
+            atomicAdd(&sb.v[bi], add.x);
+            atomicAdd(&sb.v[kBoxNodes + bi], add.y);
+            atomicAdd(&sb.v[2 * kBoxNodes + bi], add.z);
+          } else {
+            atomicAdd(e.grid_vb + ((long long)iz * e.G + iy) * e.G + ix, add);
+          }
+        }
+      }
+    }
+    // partial adjoint in place: x-bar and F-bar slots
+#pragma unroll
+    for (int a = 0; a < 3; ++a) adj[a * np + i] = xbp[a];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) adj[(15 + a) * np + i] = Fbp[a];
+  }
+  if (bx.fits) {
+    __syncthreads();
+    flush_box<false, true>(e, it.env, bx, sb, e.grid_vb, nullptr, nullptr);
+  }
+}
+
+// ------------------------------------------------------------------ adjoint: grid^T
+
+// Reverse of node_forward for the velocity adjoint vob (linear in vob), given its trace t.
+__device__ __forceinline__ void node_reverse(const EnvDesc& e, int ix, int iy, int iz, float4 mp, const float* q,
+                                             const float* u, const NodeFwd& t, float4 vob, float4& mpb, float* qb,
+                                             float* ub) {
+  float v3b[3] = {(t.zero & 1u) ? 0.f : vob.x, (t.zero & 2u) ? 0.f : vob.y, (t.zero & 4u) ? 0.f : vob.z};
+  float v2b[3];
+  if (t.ground) {
+    if (e.ground_mu > 0.0f) {
+      if (t.gL > 0.0f && t.gf > 0.0f) {
+        const float dot = v3b[0] * t.v2[0] + v3b[1] * t.v2[1];
+        const float iL3 = 1.0f / (t.gL * t.gL * t.gL);
+        v2b[0] = t.gf * v3b[0] - dot * e.ground_mu * t.v2[2] * t.v2[0] * iL3;
+        v2b[1] = t.gf * v3b[1] - dot * e.ground_mu * t.v2[2] * t.v2[1] * iL3;
+        v2b[2] = dot * e.ground_mu / t.gL;
+      } else {
+        v2b[0] = v2b[1] = v2b[2] = 0.0f;
+      }
+    } else {
+      v2b[0] = v3b[0];
+      v2b[1] = v3b[1];
+      v2b[2] = 0.0f;
+    }
+  } else {
+    v2b[0] = v3b[0];
+    v2b[1] = v3b[1];
+    v2b[2] = v3b[2];
+  }
+  float v1b[3];
+  if (e.coll_kind != COLL_NONE) {
+    const float sc = t.sc;
+    float scb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      v1b[i] = (1.0f - sc) * v2b[i];
+      scb += v2b[i] * t.dl[i];
+    }
+    float vr2b[3] = {sc * v2b[0], sc * v2b[1], sc * v2b[2]};
+    float vbb[3] = {vr2b[0], vr2b[1], vr2b[2]};
+    float vrb[3] = {0.f, 0.f, 0.f}, nb[3] = {0.f, 0.f, 0.f};
+    if (t.branch == 0) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) vrb[i] = vr2b[i];
+    } else if (t.branch == 1) {
+      const float dot = vr2b[0] * t.vt[0] + vr2b[1] * t.vt[1] + vr2b[2] * t.vt[2];
+      const float iL = 1.0f / t.L;
+      const float c3 = dot * e.coll_mu * t.vn * iL * iL * iL;
+      float vtb[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) vtb[i] = t.f * vr2b[i] - c3 * t.vt[i];
+      float vnb = dot * e.coll_mu * iL;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        vrb[i] += vtb[i];
+        nb[i] -= t.vn * vtb[i];
+      }
+      vnb -= vtb[0] * t.ct.n[0] + vtb[1] * t.ct.n[1] + vtb[2] * t.ct.n[2];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        vrb[i] += vnb * t.ct.n[i];
+        nb[i] += vnb * t.vr[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      v1b[i] += vrb[i];
+      vbb[i] -= vrb[i];
+    }
+    const float db = t.ct.d > 0.0f ? scb * (-e.alpha * sc) : 0.0f;
+    const float* H = t.ct.H;  // xx xy xz yy yz zz
+    const float Hn0 = H[0] * nb[0] + H[1] * nb[1] + H[2] * nb[2];
+    const float Hn1 = H[1] * nb[0] + H[3] * nb[1] + H[4] * nb[2];
+    const float Hn2 = H[2] * nb[0] + H[4] * nb[1] + H[5] * nb[2];
+    qb[0] += -t.ct.n[0] * db - Hn0 - u[3] * vbb[1];
+    qb[1] += -t.ct.n[1] * db - Hn1 + u[3] * vbb[0];
+    qb[2] += -t.ct.n[2] * db - Hn2;
+    qb[3] += t.ct.dd_dth * db + t.ct.dn_dth[0] * nb[0] + t.ct.dn_dth[1] * nb[1] + t.ct.dn_dth[2] * nb[2];
+    const float rx = ix * e.dx - q[0], ry = iy * e.dx - q[1];
+    ub[0] += vbb[0];
+    ub[1] += vbb[1];
+    ub[2] += vbb[2];
+    ub[3] += -ry * vbb[0] + rx * vbb[1];
+  } else {
+    v1b[0] = v2b[0];
+    v1b[1] = v2b[1];
+    v1b[2] = v2b[2];
+  }
+  const float inv_m = 1.0f / mp.x;
+  mpb.x = -(v1b[0] * t.v0[0] + v1b[1] * t.v0[1] + v1b[2] * t.v0[2]) * inv_m;
+  mpb.y = v1b[0] * inv_m;
+  mpb.z = v1b[1] * inv_m;
+  mpb.w = v1b[2] * inv_m;
+}
+
+__global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ envs, const uint2* __restrict__ active,
+                                                  const int* __restrict__ active_n, int k) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int n = *active_n;
+  for (int w = warp; w < n; w += nwarps) {
+    const uint2 at = active[w];
+    const EnvDesc& e = envs[at.x];
+    const EnvCtr c = *e.ctr;
+    float q[4], u[4];
+    step_pose(e, c, 1, k, q, u);
+    const int TG = e.G >> 2;
+    const int tz = at.y / (TG * TG), ty = (at.y / TG) % TG, tx = at.y % TG;
+    float qb[4] = {0.f, 0.f, 0.f, 0.f}, ub[4] = {0.f, 0.f, 0.f, 0.f};
+    const float vref[3] = {e.acc[ACC_VREF], e.acc[ACC_VREF + 1], e.acc[ACC_VREF + 2]};
+    const float inv_pm = 1.0f / e.p_mass;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const int l = lane + 32 * h;
+      const int ix = tx * 4 + (l & 3), iy = ty * 4 + ((l >> 2) & 3), iz = tz * 4 + (l >> 4);
+      const long long id = ((long long)iz * e.G + iy) * e.G + ix;
+      const float4 mp = e.grid_mp[id];
+      float4 mpb = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (mp.x > 0.0f) {
+        // grid_vb holds sum w (v-bar' - V_ref); the full adjoint is that + V_ref m / m_p
+        const float4 vd = e.grid_vb[id];
+        NodeFwd t;
+        node_forward<true>(e, ix, iy, iz, mp, q, u, t);
+        const bool ident = t.zero == 0u && !t.ground && (e.coll_kind == COLL_NONE || t.sc == 0.0f);
+        if (ident) {
+          // the node update is the identity map on velocities here: p-bar = v-bar/m exactly,
+          // with the V_ref part a single FP32 constant (it cancels exactly in P2G^T)
+          const float inv_m = 1.0f / mp.x;
+          const float r0 = vref[0] * inv_pm, r1 = vref[1] * inv_pm, r2 = vref[2] * inv_pm;
+          mpb.y = vd.x * inv_m + r0;
+          mpb.z = vd.y * inv_m + r1;
+          mpb.w = vd.z * inv_m + r2;
+          mpb.x = -((vd.x * t.v0[0] + vd.y * t.v0[1] + vd.z * t.v0[2]) * inv_m +
+                    (r0 * t.v0[0] + r1 * t.v0[1] + r2 * t.v0[2]));
+        } else {
+          const float sc = mp.x * inv_pm;
+          const float4 vob = make_float4(vd.x + vref[0] * sc, vd.y + vref[1] * sc, vd.z + vref[2] * sc, 0.f);
+          node_reverse(e, ix, iy, iz, mp, q, u, t, vob, mpb, qb, ub);
+        }
+      }
+      e.grid_mpb[id] = mpb;
+      e.grid_mp[id] = make_float4(0.f, 0.f, 0.f, 0.f);
+      e.grid_vb[id] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (e.coll_kind != COLL_NONE) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float a = qb[i], b2 = ub[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+        }
+        qb[i] = a;
+        ub[i] = b2;
+      }
+      if (lane == 0) {
+        const float kdt = (float)k * e.dt;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (qb[i] != 0.0f) {
+            atomicAdd(e.acc + ACC_QKB + i, qb[i]);
+            atomicAdd(e.acc + ACC_KQKB + i, kdt * qb[i]);
+          }
+          if (ub[i] != 0.0f) atomicAdd(e.acc + ACC_UB + i, ub[i]);
+        }
+      }
+    }
+    if (lane == 0) e.tile[at.y] = 0u;
+  }
+}
+
+// ------------------------------------------------------------------ adjoint: P2G^T
+
+__global__ void __launch_bounds__(kBlock) k_p2g_adj(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
+                                                    int item_off, StateRef src, int use_perm) {
+  __shared__ EnvDesc e;
+  __shared__ EnvCtr c;
+  const WorkItem it = items[item_off + blockIdx.x];
+  load_env(envs, it.env, e, c);
+  const float* b = ref_block(e, c, src);
+  float* adj = c.par ? e.adj1 : e.adj0;
+  float* adj_out = use_perm ? (c.par ? e.adj0 : e.adj1) : adj;
+  const int sslot = step_slot(c, 1);
+  const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
+  const long long np = e.n_pad;
+  const float G = (float)e.G;
+  const Mat m = env_mat(e);
+  const float Dinv = 4.0f * G * G, dx = e.dx, pm = e.p_mass;
+  const float stress_k = -e.dt * e.p_vol * Dinv;
+#pragma unroll 1
+  for (int p = 0; p < kPPT; ++p) {
+    const int i = it.start + threadIdx.x + p * kBlock;
+    if (i >= it.start + it.count) continue;
+    const int j = perm ? (int)perm[i] : i;
+    float s[kComp];
+    load_state(b, np, j, s);
+    const unsigned meta = reinterpret_cast<const unsigned*>(b + kComp * np)[j];
+    const float a_g = group_act(e, sslot, meta);
+    int base[3], oob = 0;
+    float fx[3], w[3][3], dwv[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      base[a] = cell_base(s[a], G, e.G, &oob);
+      fx[a] = __fmul_rn(s[a], G) - (float)base[a];
+      bspline(fx[a], w[a], dwv[a]);
+    }
+    float tau[9], A[9];
+    kirchhoff(m, s + 15, s + 6, a_g, tau);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) A[q] = pm * s[6 + q] + stress_k * tau[q];
+    float Ab[9], vbn[3] = {0.f, 0.f, 0.f}, xbn[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Ab[q] = 0.f;
+    // The stencil-centre node's (m-bar, p-bar) adds nothing to A-bar and x-bar (sum w r = 0,
+    // sum grad w = 0, sum r grad w^T = I); subtracting it keeps the FP32 sums from cancelling.
+    const float4 gc =
+        __ldg(e.grid_mpb + ((long long)(base[2] + 1) * e.G + (base[1] + 1)) * e.G + base[0] + 1);
+#pragma unroll
+    for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+      for (int cy = 0; cy < 3; ++cy) {
+        const float4* row = e.grid_mpb + ((long long)(base[2] + cz) * e.G + (base[1] + cy)) * e.G + base[0];
+#pragma unroll
+        for (int cx = 0; cx < 3; ++cx) {
+          const float wt = w[0][cx] * w[1][cy] * w[2][cz];
+          const float gw[3] = {dwv[0][cx] * w[1][cy] * w[2][cz] * G, w[0][cx] * dwv[1][cy] * w[2][cz] * G,
+                               w[0][cx] * w[1][cy] * dwv[2][cz] * G};
+          const float r[3] = {((float)cx - fx[0]) * dx, ((float)cy - fx[1]) * dx, ((float)cz - fx[2]) * dx};
+          const float4 gb = __ldg(row + cx);
+          const float pb[3] = {gb.y - gc.y, gb.z - gc.z, gb.w - gc.w};
+          float qv[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) qv[a] = pm * s[3 + a] + A[3 * a] * r[0] + A[3 * a + 1] * r[1] + A[3 * a + 2] * r[2];
+          const float coef = (gb.x - gc.x) * pm + pb[0] * qv[0] + pb[1] * qv[1] + pb[2] * qv[2];
+          vbn[0] += pm * wt * gb.y;
+          vbn[1] += pm * wt * gb.z;
+          vbn[2] += pm * wt * gb.w;
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) Ab[3 * a + bb] += wt * pb[a] * r[bb];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float ATp = A[a] * pb[0] + A[3 + a] * pb[1] + A[6 + a] * pb[2];
+            xbn[a] += coef * gw[a] - wt * ATp;
+          }
+        }
+      }
+    float Cbn[9], taub[9], Fbn[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      Cbn[q] = pm * Ab[q];
+      taub[q] = stress_k * Ab[q];
+      Fbn[q] = adj[(15 + q) * np + i];
+    }
+    float agb = 0.0f;
+    kirchhoff_vjp(m, s + 15, s + 6, a_g, taub, Fbn, Cbn, &agb);
+    const int o = perm ? j : i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float xp = adj[a * np + i];
+      adj_out[a * np + o] = xp + xbn[a];
+      adj_out[(3 + a) * np + o] = vbn[a];
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      adj_out[(6 + q) * np + o] = Cbn[q];
+      adj_out[(15 + q) * np + o] = Fbn[q];
+    }
+    if (e.material == MAT_MUSCLE) {
+      const int g = (int)(meta >> 20) - 1;
+      if (g >= 0 && g < e.n_groups) atomicAdd(e.acc + ACC_ACT + e.n_coll_act + g, agb);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ reverse-step bookkeeping
+
+// Start of a reverse pass over T steps: adjoint parity 0, pose adjoint 0, step index T.
+__global__ void k_bwd_init(const EnvDesc* __restrict__ envs, int env0, int n_env, int T) {
+  int ei = env0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (ei >= env0 + n_env) return;
+  const EnvDesc& e = envs[ei];
+  e.ctr->par = 0;
+  e.ctr->rev = T;
+  for (int i = 0; i < 4; ++i) e.acc[ACC_QB + i] = 0.f;
+}
+
+// Next step of the reverse pass: t = rev - 1; pose velocity of step t; zero accumulators.
+__global__ void k_rev_begin(const EnvDesc* __restrict__ envs, int env0, int n_env) {
+  int ei = env0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (ei >= env0 + n_env) return;
+  const EnvDesc& e = envs[ei];
+  EnvCtr* c = e.ctr;
+  const int t = c->rev - 1;
+  c->rev = t;
+  const int slot = c->base + t;
+  const float h = e.S * e.dt;
+  float u[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int j = 0; j < e.n_coll_act; ++j) u[e.act_map[j]] += e.act_scale[j] * e.act[(long long)slot * e.A + j] / h;
+  for (int i = 0; i < 4; ++i) {
+    e.acc[ACC_U + i] = u[i];
+    e.acc[ACC_QKB + i] = 0.f;
+    e.acc[ACC_KQKB + i] = 0.f;
+    e.acc[ACC_UB + i] = 0.f;
+  }
+  for (int j = 0; j < e.A; ++j) e.acc[ACC_ACT + j] = 0.f;
+}
+
+// One CTA per env: add rbar_t * d r_t / d(end state, end pose, action).
+__global__ void __launch_bounds__(256) k_reward_adj(const EnvDesc* __restrict__ envs, int env0, const float* rbar,
+                                                    int n_tot) {
+  __shared__ float sh[32];
+  const int ei = env0 + blockIdx.x;
+  const EnvDesc& e = envs[ei];
+  const EnvCtr c = *e.ctr;
+  const float rb = rbar ? rbar[(long long)c.rev * n_tot + ei] : 0.0f;
+  if (rb == 0.0f || e.reward_kind == 0) return;
+  const int slot = c.base + c.rev;
+  const float* b = e.slots + (long long)(slot + 1) * e.block;
+  float* adj = c.par ? e.adj1 : e.adj0;
+  const long long np = e.n_pad;
+  const unsigned* meta = reinterpret_cast<const unsigned*>(b + kComp * np);
+  const int ns = min(e.n_sub, e.n);
+  if (e.reward_kind == 1) {
+    float st[4];
+    subsample_stats(e, b, sh, st);
+    const float d = st[0] / e.rparam[0];
+    const float dRd = -2.0f * rd_factor(d, 0.33f) / ((1.f + d) * (1.f + d) * (1.f + d));
+    for (int i = threadIdx.x; i < e.n; i += blockDim.x)
+      if ((int)(meta[i] & kIdMask) < ns)
+        adj[2 * np + i] += rb * (dRd / (e.rparam[0] * ns) - 2.0f * (b[2 * np + i] - st[0]) / ns);
+  } else if (e.reward_kind == 2) {
+    if (threadIdx.x == 0) {
+      const float* q = e.pose + (slot + 1) * 4;
+      float d = 0.f;
+      for (int i = 0; i < 3; ++i) d += (q[i] - e.rparam[i]) * (q[i] - e.rparam[i]);
+      const float dRd = -2.0f * rd_factor(d, 0.02f) / ((1.f + d) * (1.f + d) * (1.f + d));
+      for (int i = 0; i < 3; ++i) e.acc[ACC_QB + i] += rb * dRd * 2.0f * (q[i] - e.rparam[i]);
+    }
+  } else if (e.reward_kind == 3) {
+    for (int i = threadIdx.x; i < e.n; i += blockDim.x)
+      if ((int)(meta[i] & kIdMask) < ns) {
+        adj[3 * np + i] += rb / ns;
+        adj[2 * np + i] += rb * e.rparam[1] / ns;
+      }
+    if (threadIdx.x == 0)
+      for (int j = 0; j < e.A; ++j) e.acc[ACC_ACT + j] += rb * (-2.0f * e.rparam[2] * e.act[(long long)slot * e.A + j]);
+  }
+}
+
+// One CTA per env: V_ref = mean over the env's particles of the adjoint v-bar + dt x-bar of
+// the step's end state (any fixed value is exact; a representative one keeps the shifted
+// adjoint small).
+__global__ void __launch_bounds__(256) k_adj_ref(const EnvDesc* __restrict__ envs, int env0) {
+  __shared__ float sh[32];
+  const int ei = env0 + blockIdx.x;
+  const EnvDesc& e = envs[ei];
+  const EnvCtr c = *e.ctr;
+  const float* adj = c.par ? e.adj1 : e.adj0;
+  const long long np = e.n_pad;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  for (int i = threadIdx.x; i < e.n; i += blockDim.x) {
+    s0 += adj[3 * np + i] + e.dt * adj[i];
+    s1 += adj[4 * np + i] + e.dt * adj[np + i];
+    s2 += adj[5 * np + i] + e.dt * adj[2 * np + i];
+  }
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    const float inv = 1.0f / (float)e.n;
+    e.acc[ACC_VREF] = s0 * inv;
+    e.acc[ACC_VREF + 1] = s1 * inv;
+    e.acc[ACC_VREF + 2] = s2 * inv;
+  }
+}
+
+__global__ void k_rev_end(const EnvDesc* __restrict__ envs, int env0, int n_env, float* act_grad, int n_tot,
+                          int a_max) {
+  int ei = env0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (ei >= env0 + n_env) return;
+  const EnvDesc& e = envs[ei];
+  EnvCtr* c = e.ctr;
+  const float h = e.S * e.dt;
+  float ub[4];
+  for (int i = 0; i < 4; ++i) {
+    ub[i] = h * e.acc[ACC_QB + i] + e.acc[ACC_KQKB + i] + e.acc[ACC_UB + i];
+    e.acc[ACC_QB + i] += e.acc[ACC_QKB + i];
+  }
+  float* out = act_grad + ((long long)c->rev * n_tot + ei) * a_max;
+  for (int j = 0; j < a_max; ++j) {
+    float g = 0.f;
+    if (j < e.A) {
+      g = e.acc[ACC_ACT + j];
+      if (j < e.n_coll_act) g += ub[e.act_map[j]] * e.act_scale[j] / h;
+    }
+    out[j] = g;
+  }
+  c->par ^= 1;
+}
+
+// ------------------------------------------------------------------ state I/O
+
+// Caller order (particle-major AoS) -> slot 0, meta = id | (group+1) << 20.
+__global__ void k_set_state(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items, int item_off,
+                            const float* x, const float* v, const float* C, const float* F, const int* group) {
+  const WorkItem it = items[item_off + blockIdx.x];
+  const EnvDesc& e = envs[it.env];
+  float* b = e.slots;
+  const long long np = e.n_pad;
+  for (int p = threadIdx.x; p < it.count; p += blockDim.x) {
+    const int i = it.start + p;
+    const long long g = e.poff + i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      b[a * np + i] = x[g * 3 + a];
+      b[(3 + a) * np + i] = v[g * 3 + a];
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      b[(6 + a) * np + i] = C[g * 9 + a];
+      b[(15 + a) * np + i] = F[g * 9 + a] - ((a % 4 == 0) ? 1.0f : 0.0f);  // stored as H = F - I
+    }
+    int gr = group ? group[g] : -1;
+    if (gr < -1 || gr > 4094) gr = -1;
+    reinterpret_cast<unsigned*>(b + kComp * np)[i] = (unsigned)i | ((unsigned)(gr + 1) << 20);
+  }
+}
+
+// block -> caller order by meta id.
+__global__ void k_get_state(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items, int item_off,
+                            StateRef src, float* x, float* v, float* C, float* F) {
+  __shared__ EnvDesc e;
+  __shared__ EnvCtr c;
+  const WorkItem it = items[item_off + blockIdx.x];
+  load_env(envs, it.env, e, c);
+  const float* b = ref_block(e, c, src);
+  const long long np = e.n_pad;
+  for (int p = threadIdx.x; p < it.count; p += blockDim.x) {
+    const int i = it.start + p;
+    const long long g = e.poff + (reinterpret_cast<const unsigned*>(b + kComp * np)[i] & kIdMask);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (x) x[g * 3 + a] = b[a * np + i];
+      if (v) v[g * 3 + a] = b[(3 + a) * np + i];
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      if (C) C[g * 9 + a] = b[(6 + a) * np + i];
+      if (F) F[g * 9 + a] = b[(15 + a) * np + i] + ((a % 4 == 0) ? 1.0f : 0.0f);
+    }
+  }
+}
+
+// Caller-order adjoint of the live state -> adj[par] in the live block's order.
+__global__ void k_adj_in(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items, int item_off,
+                         const float* xb, const float* vb, const float* Cb, const float* Fb) {
+  __shared__ EnvDesc e;
+  __shared__ EnvCtr c;
+  const WorkItem it = items[item_off + blockIdx.x];
+  load_env(envs, it.env, e, c);
+  const float* b = e.slots + (long long)c.live * e.block;
+  float* adj = c.par ? e.adj1 : e.adj0;
+  const long long np = e.n_pad;
+  for (int p = threadIdx.x; p < it.count; p += blockDim.x) {
+    const int i = it.start + p;
+    const long long g = e.poff + (reinterpret_cast<const unsigned*>(b + kComp * np)[i] & kIdMask);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      adj[a * np + i] = xb ? xb[g * 3 + a] : 0.f;
+      adj[(3 + a) * np + i] = vb ? vb[g * 3 + a] : 0.f;
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      adj[(6 + a) * np + i] = Cb ? Cb[g * 9 + a] : 0.f;
+      adj[(15 + a) * np + i] = Fb ? Fb[g * 9 + a] : 0.f;
+    }
+  }
+}
+
+// adj[par] (order of block src) -> caller order.
+__global__ void k_adj_out(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items, int item_off,
+                          StateRef src, float* xb, float* vb, float* Cb, float* Fb) {
+  __shared__ EnvDesc e;
+  __shared__ EnvCtr c;
+  const WorkItem it = items[item_off + blockIdx.x];
+  load_env(envs, it.env, e, c);
+  const float* b = ref_block(e, c, src);
+  const float* adj = c.par ? e.adj1 : e.adj0;
+  const long long np = e.n_pad;
+  for (int p = threadIdx.x; p < it.count; p += blockDim.x) {
+    const int i = it.start + p;
+    const long long g = e.poff + (reinterpret_cast<const unsigned*>(b + kComp * np)[i] & kIdMask);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (xb) xb[g * 3 + a] = adj[a * np + i];
+      if (vb) vb[g * 3 + a] = adj[(3 + a) * np + i];
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      if (Cb) Cb[g * 9 + a] = adj[(6 + a) * np + i];
+      if (Fb) Fb[g * 9 + a] = adj[(15 + a) * np + i];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+
+static std::atomic<long long> g_launches{0};
+static TimingHook g_hook;
+long long kernel_launch_count() { return g_launches.load(); }
+void set_timing_hook(const TimingHook* h) { g_hook = h ? *h : TimingHook{}; }
+void count_launches(int n) { g_launches += n; }
+
+struct Timed {  // records the hook's events around one launch of class kc
+  int kc;
+  cudaStream_t st;
+  bool on() const { return g_hook.before && (g_hook.kc == kc || g_hook.kc == -1); }
+  Timed(int k, cudaStream_t s) : kc(k), st(s) {
+    if (on()) g_hook.before(g_hook.user, kc, st);
+  }
+  ~Timed() {
+    g_launches += 1;
+    if (on()) g_hook.after(g_hook.user, kc, st);
+  }
+};
+
+static inline int nblk(int n, int b) { return (n + b - 1) / b; }
+
+void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k) {
+  if (L.n_items == 0) return;
+  Timed tm_(KC_P2G, L.stream);
+  k_p2g<<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k,
+                                            src.kind == REF_RING || src.kind == REF_REV ? 1 : 0, L.active, L.active_n);
+}
+
+void launch_grid(const Launch& L, int k, GridMode mode, bool rev) {
+  Timed tm_(KC_GRID, L.stream);
+  k_grid<<<L.grid_blocks, 256, 0, L.stream>>>(L.envs, L.active, L.active_n, k, (int)mode, rev ? 1 : 0);
+}
+
+void launch_g2p(const Launch& L, StateRef src, StateRef dst, bool use_perm, int k) {
+  (void)k;
+  if (L.n_items == 0) return;
+  Timed tm_(KC_G2P, L.stream);
+  const int rev = (dst.kind == REF_RING) ? 1 : 0;
+  k_g2p<<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev);
+}
+
+void launch_step_begin(const Launch& L, const float* act_in, int a_max, bool record) {
+  Timed tm_(KC_OTHER, L.stream);
+  k_step_begin<<<nblk(L.n_env, 128), 128, 0, L.stream>>>(L.envs, L.env0, L.n_env, act_in, a_max, record ? 1 : 0);
+}
+
+void launch_reward_end(const Launch& L, float* reward_out, bool record) {
+  Timed tm_(KC_OTHER, L.stream);
+  k_reward_end<<<L.n_env, 256, 0, L.stream>>>(L.envs, L.env0, reward_out, record ? 1 : 0);
+}
+
+void launch_g2p_adj(const Launch& L, StateRef src, bool use_perm, int k) {
+  (void)k;
+  if (L.n_items == 0) return;
+  Timed tm_(KC_G2P_ADJ, L.stream);
+  k_g2p_adj<<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0);
+}
+
+void launch_grid_adj(const Launch& L, int k) {
+  Timed tm_(KC_GRID_ADJ, L.stream);
+  k_grid_adj<<<L.grid_blocks, 256, 0, L.stream>>>(L.envs, L.active, L.active_n, k);
+}
+
+void launch_p2g_adj(const Launch& L, StateRef src, bool use_perm, int k) {
+  (void)k;
+  if (L.n_items == 0) return;
+  Timed tm_(KC_P2G_ADJ, L.stream);
+  k_p2g_adj<<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0);
+}
+
+void launch_bwd_init(const Launch& L, int T) {
+  Timed tm_(KC_OTHER, L.stream);
+  k_bwd_init<<<nblk(L.n_env, 128), 128, 0, L.stream>>>(L.envs, L.env0, L.n_env, T);
+}
+
+void launch_rev_begin(const Launch& L) {
+  Timed tm_(KC_OTHER, L.stream);
+  k_rev_begin<<<nblk(L.n_env, 128), 128, 0, L.stream>>>(L.envs, L.env0, L.n_env);
+}
+
+void launch_reward_adj(const Launch& L, const float* rbar, int n_tot) {
+  Timed tm_(KC_OTHER, L.stream);
+  k_reward_adj<<<L.n_env, 256, 0, L.stream>>>(L.envs, L.env0, rbar, n_tot);
+}
+
+void launch_adj_ref(const Launch& L) { Timed tm_(KC_OTHER, L.stream); k_adj_ref<<<L.n_env, 256, 0, L.stream>>>(L.envs, L.env0); }
+
+void launch_rev_end(const Launch& L, float* act_grad, int n_tot, int a_max) {
+  Timed tm_(KC_OTHER, L.stream);
+  k_rev_end<<<nblk(L.n_env, 128), 128, 0, L.stream>>>(L.envs, L.env0, L.n_env, act_grad, n_tot, a_max);
+}
+
+void launch_set_state(const Launch& L, const float* x, const float* v, const float* C, const float* F,
+                      const int* group) {
+  if (L.n_items == 0) return;
+  Timed tm_(KC_OTHER, L.stream);
+  k_set_state<<<L.n_items, 256, 0, L.stream>>>(L.envs, L.items, L.item_offset, x, v, C, F, group);
+}
+
+void launch_get_state(const Launch& L, StateRef src, float* x, float* v, float* C, float* F) {
+  if (L.n_items == 0) return;
+  Timed tm_(KC_OTHER, L.stream);
+  k_get_state<<<L.n_items, 256, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, x, v, C, F);
+}
+
+void launch_adj_in(const Launch& L, const float* xb, const float* vb, const float* Cb, const float* Fb) {
+  if (L.n_items == 0) return;
+  Timed tm_(KC_OTHER, L.stream);
+  k_adj_in<<<L.n_items, 256, 0, L.stream>>>(L.envs, L.items, L.item_offset, xb, vb, Cb, Fb);
+}
+
+void launch_adj_out(const Launch& L, StateRef src, float* xb, float* vb, float* Cb, float* Fb) {
+  if (L.n_items == 0) return;
+  Timed tm_(KC_OTHER, L.stream);
+  k_adj_out<<<L.n_items, 256, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, xb, vb, Cb, Fb);
+}
+
+}  // namespace mpm

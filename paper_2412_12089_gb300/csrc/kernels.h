@@ -1,0 +1,84 @@
+// kernels.h -- host-side launchers of the batched MPM kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "mpm_types.h"
+
+namespace mpm {
+
+// Kernel classes (for launch counting and per-class event timing).
+enum KernelClass {
+  KC_P2G = 1, KC_GRID = 2, KC_G2P = 3, KC_G2P_ADJ = 4, KC_GRID_ADJ = 5, KC_P2G_ADJ = 6, KC_BIN = 7, KC_OTHER = 8
+};
+
+// Every launcher below adds the number of kernels it enqueued to this counter.
+long long kernel_launch_count();
+void count_launches(int n);
+
+// Optional timing hook: when set, launchers of class kc record start/stop events around the
+// launch on its stream (direct launches only; no effect inside graph capture).
+struct TimingHook {
+  int kc = 0;  // class to time, -1 = every class
+  void (*before)(void* user, int kc, cudaStream_t st) = nullptr;
+  void (*after)(void* user, int kc, cudaStream_t st) = nullptr;
+  void* user = nullptr;
+};
+void set_timing_hook(const TimingHook* h);
+
+struct Launch {
+  const EnvDesc* envs;   // device array
+  const WorkItem* items; // device array of particle work items
+  int n_items;
+  int item_offset;       // first item (per-environment launches)
+  uint2* active;         // active-tile list (env, tile)
+  int* active_n;         // its length (device)
+  int grid_blocks;       // CTAs of the persistent grid kernels
+  int env0, n_env;       // environment range of the per-env kernels
+  cudaStream_t stream;
+};
+
+enum GridMode { GRID_FWD = 0, GRID_KEEP = 1 };
+
+void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k);
+void launch_grid(const Launch& L, int k, GridMode mode, bool rev);
+void launch_g2p(const Launch& L, StateRef src, StateRef dst, bool use_perm, int k);
+
+void launch_step_begin(const Launch& L, const float* act_in, int a_max, bool record);
+void launch_reward_end(const Launch& L, float* reward_out, bool record);
+
+void launch_g2p_adj(const Launch& L, StateRef src, bool use_perm, int k);
+void launch_grid_adj(const Launch& L, int k);
+void launch_p2g_adj(const Launch& L, StateRef src, bool use_perm, int k);
+// Reverse pass bookkeeping.  bwd_init sets the step index to T; each rev_begin decrements
+// it, so one captured reverse-step graph serves every step.  rbar: [T][n_tot] reward
+// adjoints (or NULL); act_grad: [T][n_tot][a_max] output.
+void launch_bwd_init(const Launch& L, int T);
+void launch_rev_begin(const Launch& L);
+void launch_reward_adj(const Launch& L, const float* rbar, int n_tot);
+void launch_adj_ref(const Launch& L);
+void launch_rev_end(const Launch& L, float* act_grad, int n_tot, int a_max);
+
+// State I/O: caller order (AoS) <-> arena blocks.
+void launch_set_state(const Launch& L, const float* x, const float* v, const float* C, const float* F,
+                      const int* group);
+void launch_get_state(const Launch& L, StateRef src, float* x, float* v, float* C, float* F);
+void launch_adj_in(const Launch& L, const float* xb, const float* vb, const float* Cb, const float* Fb);
+void launch_adj_out(const Launch& L, StateRef src, float* xb, float* vb, float* Cb, float* Fb);
+
+// Binning: keys of the live state, LSD radix sort, per-env permutations.
+struct SortScratch {
+  unsigned* keys[2];
+  unsigned* vals[2];
+  unsigned* hist;
+  long long cap;
+  int max_blocks;
+};
+// Sort the live state of the launch's environments (global indices [poff0, poff0+n_total))
+// and store each environment's permutation in perm[live].
+void bin_envs(const Launch& L, long long poff0, long long n_total, int cell_bits, int key_bits, SortScratch& s);
+// Stable LSD radix sort of (keys, vals) on the low key_bits bits; returns the buffer index
+// (0 or 1) holding the result.
+int radix_sort(unsigned** keys, unsigned** vals, long long n, int key_bits, unsigned* hist, cudaStream_t st);
+void launch_bin_keys_plain(const float* x, int n, int G, unsigned* keys, unsigned* vals, cudaStream_t st);
+
+}  // namespace mpm

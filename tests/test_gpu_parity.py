@@ -1,0 +1,207 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (infinity-norm relative errors, per environment and quantity):
+  one substep from the same FP32 state .......... 1e-5 on x, v, F (C: 1e-4)
+  a control-step horizon ......................... 1e-3
+  gradients against the FP64 oracle .............. 1e-3
+  binning ........................................ bit-exact
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2412_12089_gb300 import workloads as wl
+
+from gpu_helpers import gpu_run, oracle_run, perturb, rel_err, split
+
+pytestmark = pytest.mark.gpu
+
+
+def small(name, seed=0, substeps=None, T=1, **kw):
+    if name == "cube":
+        w = wl.cube(seed=seed, n=kw.pop("n", 1000), G=kw.pop("G", 32), substeps=substeps or 1, T=T)
+    elif name == "dough":
+        w = wl.dough(n_envs=kw.pop("n_envs", 3), seed=seed, n_range=kw.pop("n_range", (500, 3000)),
+                     substeps=substeps or 1, T=T)
+    elif name == "fluid":
+        w = wl.fluid(n_envs=kw.pop("n_envs", 2), seed=seed, n=kw.pop("n", 1500), substeps=substeps or 1, T=T)
+    elif name == "jumper":
+        w = wl.jumper(n_envs=kw.pop("n_envs", 2), seed=seed, n=kw.pop("n", 3000), G=kw.pop("G", 48),
+                      substeps=substeps or 1, T=T)
+    else:
+        raise ValueError(name)
+    return w
+
+
+# ------------------------------------------------------------------ binning
+
+@pytest.mark.parametrize("n,G", [(1, 32), (1000, 32), (100_003, 48), (300_000, 96)])
+def test_bin_bitexact(n, G):
+    import torch
+
+    from paper_2412_12089_gb300 import mpm
+
+    rng = np.random.default_rng(n)
+    x = (0.05 + 0.9 * rng.random((n, 3))).astype(np.float32)
+    k = min(n, 500)
+    x[:k] = ((np.floor(x[:k] * G - 0.5) + 0.5) / G).astype(np.float32)  # on cell boundaries
+    xd = torch.as_tensor(x).cuda()
+    keys = torch.empty(n, dtype=torch.int32, device="cuda")
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    mpm.mpm_bin(xd, n, G, keys, perm)
+    torch.cuda.synchronize()
+    kg = keys.cpu().numpy().view(np.uint32)
+    pg = perm.cpu().numpy().view(np.uint32)
+    ko = orc.bin_keys_f32(x, G)
+    assert np.array_equal(kg, ko)
+    assert np.array_equal(pg, orc.stable_sort(ko))
+
+
+# ------------------------------------------------------------------ one substep
+
+@pytest.mark.parametrize("name", ["cube", "dough", "fluid", "jumper"])
+def test_substep_parity(name):
+    w = perturb(small(name, seed=1, substeps=1, T=1), seed=2)
+    b, rew, st = gpu_run(w, 1)
+    for e in range(w.n_envs):
+        o, q, r = oracle_run(w, e, 1)
+        xs = split(w, st["x"])[e]
+        vs = split(w, st["v"])[e]
+        Cs = split(w, st["C"])[e]
+        Fs = split(w, st["F"])[e]
+        assert rel_err(xs, o.x) < 1e-5, (name, e, "x", rel_err(xs, o.x))
+        assert rel_err(vs, o.v) < 1e-5, (name, e, "v", rel_err(vs, o.v))
+        assert rel_err(Fs, o.F) < 1e-5, (name, e, "F", rel_err(Fs, o.F))
+        assert rel_err(Cs, o.C) < 1e-4, (name, e, "C", rel_err(Cs, o.C))
+        assert np.allclose(st["pose"][e], q, atol=1e-6)
+        if w.specs[e].reward != "none":
+            assert abs(rew[0, e] - r[0]) <= 1e-4 * max(1.0, abs(r[0])), (name, e, rew[0, e], r[0])
+    code, flags = b.check_status()
+    assert code == 0 and not flags.any()
+
+
+# ------------------------------------------------------------------ horizons
+
+def test_cube_horizon_c1():
+    """The single-environment neo-Hookean cube at its full size: 4096 particles, 32^3 grid,
+    50 substeps."""
+    w = wl.cube(seed=0)
+    w.specs[0] = w.specs[0].replace(substeps=50)
+    b, rew, st = gpu_run(w, 1)
+    o, q, r = oracle_run(w, 0, 1)
+    for k in ("x", "v", "F"):
+        assert rel_err(st[k], getattr(o, k)) < 1e-3, (k, rel_err(st[k], getattr(o, k)))
+
+
+@pytest.mark.parametrize("name,T,S", [("dough", 2, 20), ("fluid", 2, 25), ("jumper", 2, 20)])
+def test_horizon_parity(name, T, S):
+    w = small(name, seed=3, substeps=S, T=T)
+    b, rew, st = gpu_run(w, T)
+    for e in range(w.n_envs):
+        o, q, r = oracle_run(w, e, T)
+        for k in ("x", "v", "F"):
+            got = split(w, st[k])[e]
+            assert rel_err(got, getattr(o, k)) < 1e-3, (name, e, k, rel_err(got, getattr(o, k)))
+        assert np.allclose(rew[:, e], r, rtol=1e-3, atol=1e-5), (name, e, rew[:, e], r)
+
+
+# ------------------------------------------------------------------ batching
+
+def test_batched_equals_alone_and_per_env_launch():
+    """Uneven environments stepped together give each environment's own result, and the
+    one-launch-per-environment path gives the same result as the batched one."""
+    w = small("dough", seed=5, substeps=4, T=2, n_envs=4, n_range=(200, 5000))
+    _, rew_b, st_b = gpu_run(w, 2)
+    _, rew_p, st_p = gpu_run(w, 2, per_env=True)
+    assert rel_err(st_p["x"], st_b["x"]) < 1e-6
+    assert np.allclose(rew_p, rew_b, rtol=1e-5, atol=1e-7)
+    for e in range(w.n_envs):
+        we = wl.Workload("one", [w.specs[e]], [w.inits[e]], w.actions[:, e:e + 1, :], w.T)
+        _, rew_1, st_1 = gpu_run(we, 2)
+        assert rel_err(st_1["x"], split(w, st_b["x"])[e]) < 1e-6
+        assert np.allclose(rew_1[:, 0], rew_b[:, e], rtol=1e-5, atol=1e-7)
+
+
+def test_graphs_equal_direct_launches():
+    w = small("fluid", seed=6, substeps=5, T=3)
+    _, rew_g, st_g = gpu_run(w, 3, use_graphs=True)
+    _, rew_d, st_d = gpu_run(w, 3, use_graphs=False)
+    assert rel_err(st_g["x"], st_d["x"]) < 1e-6
+    assert np.allclose(rew_g, rew_d, rtol=1e-5, atol=1e-7)
+
+
+def test_edge_cases_tiny_envs():
+    """Single-particle and sub-warp environments next to a normal one."""
+    w = small("cube", seed=7, substeps=3, T=1, n=700)
+    s0, i0 = w.specs[0], w.inits[0]
+    specs = [s0.replace(n_particles=1, p_vol=s0.p_vol), s0.replace(n_particles=17), s0]
+    inits = [wl.EnvInit(i0.x[:1].copy(), i0.v[:1].copy(), i0.C[:1].copy(), i0.F[:1].copy()),
+             wl.EnvInit(i0.x[:17].copy(), i0.v[:17].copy(), i0.C[:17].copy(), i0.F[:17].copy()), i0]
+    w2 = wl.Workload("tiny", specs, inits, np.zeros((1, 3, 1), np.float32), 1)
+    _, _, st = gpu_run(w2, 1)
+    for e in range(3):
+        o, _, _ = oracle_run(w2, e, 1)
+        assert rel_err(split(w2, st["x"])[e], o.x) < 1e-5
+
+
+def test_domain_status_flag():
+    w = small("cube", seed=8, substeps=1, T=1, n=300)
+    w.inits[0].x[5] = np.array([0.001, 0.5, 0.5], np.float32)  # below the first cell: base clamped
+    b, _, _ = gpu_run(w, 1)
+    code, flags = b.check_status()
+    assert code == 5 and flags[0] & 1
+
+
+# ------------------------------------------------------------------ gradients
+
+def _gpu_grads(w, T, xbT=None, rbar=None, S=None):
+    import torch
+
+    from paper_2412_12089_gb300.batch import Batch
+
+    b = Batch(w.specs, max_steps=T)
+    b.set_inits(w.inits)
+    for t in range(T):
+        b.step(torch.as_tensor(w.actions[t]).cuda(), record=True)
+    st = b.get_state()
+    xb = None
+    if xbT is not None:
+        xb = xbT(st["x"].cpu().numpy())
+    out = b.backward(xb=xb, reward_adj=rbar)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}, st
+
+
+def test_gradient_cube_c1():
+    """d/d(x0, v0, C0, F0) of sum |x_50 - x*|^2, x* = x0 + (0.05, 0, 0), on the full C1 cube."""
+    w = wl.cube(seed=0)
+    w.specs[0] = w.specs[0].replace(substeps=50)
+    x0 = w.inits[0].x.astype(np.float64)
+    target = x0 + np.array([0.05, 0.0, 0.0])
+    g, st = _gpu_grads(w, 1, xbT=lambda xT: (2.0 * (xT - target)).astype(np.float32))
+    s = w.specs[0]
+    sp = orc.make_spec(s)
+    so = orc.State.from_init(w.inits[0])
+    oT, _, _ = oracle_run(w, 0, 1)
+    ag, (xb, vb, Cb, Fb), qb = orc.rollout_adj(sp, so, np.zeros(4), np.zeros((1, 1)),
+                                               adj_final=(2.0 * (oT.x - target), None, None, None))
+    for name, got, ref in (("x", g["xb0"], xb), ("v", g["vb0"], vb), ("C", g["Cb0"], Cb), ("F", g["Fb0"], Fb)):
+        assert rel_err(got, ref) < 1e-3, (name, rel_err(got, ref))
+
+
+@pytest.mark.parametrize("name,S", [("dough", 4), ("fluid", 4), ("jumper", 3)])
+def test_action_gradients(name, S):
+    T = 2
+    w = small(name, seed=9, substeps=S, T=T, n_envs=2)
+    rbar = np.ones((T, w.n_envs), np.float32)
+    g, st = _gpu_grads(w, T, rbar=rbar)
+    for e in range(w.n_envs):
+        s = w.specs[e]
+        sp = orc.make_spec(s)
+        so = orc.State.from_init(w.inits[e])
+        A = s.action_dim
+        ag, (xb, vb, Cb, Fb), qb = orc.rollout_adj(sp, so, np.array(s.pose0, np.float64),
+                                                   w.actions[:T, e, :A].astype(np.float64), rbar=np.ones(T))
+        assert rel_err(g["action_grad"][:, e, :A], ag) < 1e-3, (name, e, rel_err(g["action_grad"][:, e, :A], ag))
+        assert rel_err(split(w, g["xb0"])[e], xb) < 1e-3, (name, e, "xb0")
+        assert rel_err(g["pose_grad0"][e], qb) < 1e-3 or np.abs(qb).max() < 1e-8, (name, e, g["pose_grad0"][e], qb)
