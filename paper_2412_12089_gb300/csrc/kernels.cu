@@ -26,7 +26,6 @@ namespace mpm {
 
 constexpr int kBlock = 128;         // threads per particle CTA
 constexpr int kPPT = 2;             // particles per thread
-constexpr int kChunk = kBlock * kPPT;
 constexpr int kBoxNodes = 2048;     // shared-memory box capacity (float4 nodes, 32 KB)
 
 // ------------------------------------------------------------------ common device helpers
@@ -169,19 +168,78 @@ __device__ __forceinline__ void flush_box(const EnvDesc& e, int env, const Box& 
   }
 }
 
-// Stencil node k in 0..26 -> offsets (a, b, c); lane l visits node (n + l) mod 27 at step n,
-// so binned particles of one cell (adjacent lanes) update different shared nodes at once.
-__device__ __forceinline__ void stencil_node(int k, int& a, int& b, int& c) {
-  c = k / 9;
-  const int r = k - 9 * c;
-  b = r / 3;
-  a = r - 3 * b;
+__device__ __forceinline__ float pick3(int i, const float* w) { return i == 0 ? w[0] : (i == 1 ? w[1] : w[2]); }
+
+// One axis of a particle's 3-node stencil, visited in an order rotated by r (node offsets
+// o[h] = (h + r) mod 3) with the matching weights, weight derivatives and node offsets
+// r[h] = (o[h] - fx) dx.  Lanes with different rotations update different nodes at the
+// same loop step, yet the 27-node loop stays static.
+struct Axis3 {
+  int o[3];
+  float w[3], dw[3], r[3];
+};
+
+__device__ __forceinline__ void rot_axis(int rot, const float* w, const float* dw, float fx, float dx, Axis3& a) {
+#pragma unroll
+  for (int h = 0; h < 3; ++h) {
+    int o = h + rot;
+    o = o >= 3 ? o - 3 : o;
+    a.o[h] = o;
+    a.w[h] = pick3(o, w);
+    a.dw[h] = pick3(o, dw);
+    a.r[h] = ((float)o - fx) * dx;
+  }
 }
 
-__device__ __forceinline__ float pick3(int i, const float* w) { return i == 0 ? w[0] : (i == 1 ? w[1] : w[2]); }
+// Runs of equal keys among the lanes of a warp.  Binned particles sharing a cell base sit in
+// adjacent lanes and update the same 27 nodes, so their contributions are summed inside the
+// run (warp shuffles) and only the run's first lane issues the shared-memory atomics.
+struct Runs {
+  int span;       // lanes after this one in its run
+  int maxspan;    // longest span in the warp (shuffle steps: ceil(log2(maxspan + 1)))
+  int head_lane;  // first lane of this lane's run
+  bool head;
+};
+
+__device__ __forceinline__ Runs warp_runs(unsigned key) {
+  const int lane = threadIdx.x & 31;
+  const unsigned prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const bool head = lane == 0 || key != prev;
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);  // lanes 0..lane
+  const unsigned after = heads & ~upto;                                   // heads past lane
+  Runs r;
+  r.head = head;
+  r.head_lane = 31 - __clz(heads & upto);
+  r.span = (after ? (__ffs(after) - 1) : 32) - lane - 1;
+  r.maxspan = __reduce_max_sync(0xffffffffu, r.span);
+  return r;
+}
+
+// Sum of a, b, c (and d) over the lane and the following r.span lanes of its run; exact for
+// the run's head (a lane's partial sums past the head are not used).
+__device__ __forceinline__ void run_sum4(float& a, float& b, float& c, float& d, const Runs& r) {
+  for (int st = 1; st <= r.maxspan; st <<= 1) {
+    const float ta = __shfl_down_sync(0xffffffffu, a, st);
+    const float tb = __shfl_down_sync(0xffffffffu, b, st);
+    const float tc = __shfl_down_sync(0xffffffffu, c, st);
+    const float td = __shfl_down_sync(0xffffffffu, d, st);
+    if (st <= r.span) {
+      a += ta;
+      b += tb;
+      c += tc;
+      d += td;
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned cell_pack(int b0, int b1, int b2) {
+  return (unsigned)b0 | ((unsigned)b1 << 10) | ((unsigned)b2 << 20);
+}
 
 // ------------------------------------------------------------------ P2G
 
+template <int MAT>
 __global__ void __launch_bounds__(kBlock) k_p2g(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
                                                 int item_off, StateRef src, int use_perm, int k, int rev,
                                                 uint2* active, int* active_n) {
@@ -216,62 +274,95 @@ __global__ void __launch_bounds__(kBlock) k_p2g(const EnvDesc* __restrict__ envs
     zero_box(sb, bx.nx * bx.ny * bx.nz, 4);
     __syncthreads();
   }
-  const Mat m = env_mat(e);
+  Mat m = env_mat(e);
+  m.kind = MAT;  // compile-time material: the other laws' code is folded away
   const float Dinv = 4.0f * G * G;
   const float stress_k = -e.dt * e.p_vol * Dinv;
   const float pm = e.p_mass;
-  const int lane_off = (threadIdx.x & 31) % 27;
+  const int nxy = bx.nx * bx.ny;
+  const float dx = e.dx;
+  // Every lane runs the loop (warp collectives); lanes past the item's end carry zeros in
+  // their own run, which issues no atomics.
 #pragma unroll 1
   for (int p = 0; p < kPPT; ++p) {
-    if (!valid[p]) continue;
+    const bool vp = valid[p];
     const int j = jj[p];
     float s[kComp];
-    load_state(b, np, j, s);
-    unsigned meta = reinterpret_cast<const unsigned*>(b + kComp * np)[j];
-    float a_g = group_act(e, sslot, meta);
+    if (vp) {
+      load_state(b, np, j, s);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kComp; ++q) s[q] = 0.0f;
+      base[p][0] = bx.lx;
+      base[p][1] = bx.ly;
+      base[p][2] = bx.lz;
+    }
+    const int b0 = base[p][0], b1 = base[p][1], b2 = base[p][2];
+    const Runs run = warp_runs(vp ? cell_pack(b0, b1, b2) : 0xffffffffu);
+    const bool writer = run.head && vp;
+    int rot_x = run.head_lane % 3, rot_y = (run.head_lane / 3) % 3, rot_z = (run.head_lane / 9) % 3;
+    const unsigned meta = vp ? reinterpret_cast<const unsigned*>(b + kComp * np)[j] : 0u;
+    const float a_g = MAT == MAT_MUSCLE ? group_act(e, sslot, meta) : 0.0f;
     float tau[9];
     kirchhoff(m, s + 15, s + 6, a_g, tau);
+    const float pmv = vp ? pm : 0.0f;
     float A[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) A[q] = pm * s[6 + q] + stress_k * tau[q];
-    float fx[3], w[3][3], dw[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      fx[a] = __fmul_rn(s[a], G) - (float)base[p][a];
-      bspline(fx[a], w[a], dw);
+    for (int q = 0; q < 9; ++q) A[q] = pmv * s[6 + q] + (vp ? stress_k * tau[q] : 0.0f);
+    Axis3 ax, ay, az;
+    {
+      float w[3], dw[3];
+      const float f0 = vp ? __fmul_rn(s[0], G) - (float)b0 : 1.0f;
+      const float f1 = vp ? __fmul_rn(s[1], G) - (float)b1 : 1.0f;
+      const float f2 = vp ? __fmul_rn(s[2], G) - (float)b2 : 1.0f;
+      bspline(f0, w, dw);
+      rot_axis(rot_x, w, dw, f0, dx, ax);
+      bspline(f1, w, dw);
+      rot_axis(rot_y, w, dw, f1, dx, ay);
+      bspline(f2, w, dw);
+      rot_axis(rot_z, w, dw, f2, dx, az);
     }
-    const float mv0 = pm * s[3], mv1 = pm * s[4], mv2 = pm * s[5];
-    const float dx = e.dx;
-    const int b0 = base[p][0], b1 = base[p][1], b2 = base[p][2];
-#pragma unroll 9
-    for (int n = 0; n < 27; ++n) {
-      int k = n + lane_off;
-      k = k >= 27 ? k - 27 : k;
-      int cx, cy, cz;
-      stencil_node(k, cx, cy, cz);
-      const float rx = ((float)cx - fx[0]) * dx, ry = ((float)cy - fx[1]) * dx, rz = ((float)cz - fx[2]) * dx;
-      const float wt = pick3(cx, w[0]) * pick3(cy, w[1]) * pick3(cz, w[2]);
-      float4 add;
-      add.x = wt * pm;
-      add.y = wt * (mv0 + A[0] * rx + A[1] * ry + A[2] * rz);
-      add.z = wt * (mv1 + A[3] * rx + A[4] * ry + A[5] * rz);
-      add.w = wt * (mv2 + A[6] * rx + A[7] * ry + A[8] * rz);
-      const int ix = b0 + cx, iy = b1 + cy, iz = b2 + cz;
-      if (bx.fits) {
-        const int bi = bx.idx(ix, iy, iz);
-        atomicAdd(&sb.v[bi], add.x);
-        atomicAdd(&sb.v[kBoxNodes + bi], add.y);
-        atomicAdd(&sb.v[2 * kBoxNodes + bi], add.z);
-        atomicAdd(&sb.v[3 * kBoxNodes + bi], add.w);
-      } else {
-        atomicAdd(e.grid_mp + ((long long)iz * e.G + iy) * e.G + ix, add);
+    const float mv0 = pmv * s[3], mv1 = pmv * s[4], mv2 = pmv * s[5];
+    const int bi0 = bx.fits ? bx.idx(b0, b1, b2) : 0;
+#pragma unroll
+    for (int jz = 0; jz < 3; ++jz) {
+#pragma unroll
+      for (int jy = 0; jy < 3; ++jy) {
+        const float wyz = ay.w[jy] * az.w[jz];
+        const float ry = ay.r[jy], rz = az.r[jz];
+        const float t0 = mv0 + A[1] * ry + A[2] * rz;
+        const float t1 = mv1 + A[4] * ry + A[5] * rz;
+        const float t2 = mv2 + A[7] * ry + A[8] * rz;
+        const int row = bi0 + az.o[jz] * nxy + ay.o[jy] * bx.nx;
+#pragma unroll
+        for (int jx = 0; jx < 3; ++jx) {
+          const float wt = ax.w[jx] * wyz;
+          const float rx = ax.r[jx];
+          float a0 = wt * pmv;
+          float a1 = wt * (t0 + A[0] * rx);
+          float a2 = wt * (t1 + A[3] * rx);
+          float a3 = wt * (t2 + A[6] * rx);
+          run_sum4(a0, a1, a2, a3, run);
+          if (writer) {
+            if (bx.fits) {
+              const int bi = row + ax.o[jx];
+              atomicAdd(&sb.v[bi], a0);
+              atomicAdd(&sb.v[kBoxNodes + bi], a1);
+              atomicAdd(&sb.v[2 * kBoxNodes + bi], a2);
+              atomicAdd(&sb.v[3 * kBoxNodes + bi], a3);
+            } else {
+              const int ix = b0 + ax.o[jx], iy = b1 + ay.o[jy], iz = b2 + az.o[jz];
+              atomicAdd(e.grid_mp + ((long long)iz * e.G + iy) * e.G + ix, make_float4(a0, a1, a2, a3));
+            }
+          }
+        }
       }
     }
-    if (!bx.fits) {
+    if (!bx.fits && vp) {
       for (int cz = 0; cz < 3; cz += 2)
         for (int cy = 0; cy < 3; cy += 2)
           for (int cx = 0; cx < 3; cx += 2)
-            mark_tile(e, it.env, base[p][0] + cx, base[p][1] + cy, base[p][2] + cz, active, active_n);
+            mark_tile(e, it.env, b0 + cx, b1 + cy, b2 + cz, active, active_n);
     }
   }
   if (oob) atomicOr(&e.ctr->status, 1);
@@ -420,6 +511,7 @@ __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, 
 
 // ------------------------------------------------------------------ G2P
 
+template <int MAT>
 __global__ void __launch_bounds__(kBlock) k_g2p(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
                                                 int item_off, StateRef src, StateRef dst, int use_perm, int rev) {
   __shared__ EnvDesc e;
@@ -432,7 +524,8 @@ __global__ void __launch_bounds__(kBlock) k_g2p(const EnvDesc* __restrict__ envs
   const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
   const long long np = e.n_pad;
   const float G = (float)e.G;
-  const Mat m = env_mat(e);
+  Mat m = env_mat(e);
+  m.kind = MAT;  // compile-time material: the other laws' code is folded away
   const float Dinv = 4.0f * G * G, dt = e.dt, dx = e.dx;
   int status = 0;
 #pragma unroll 1
@@ -615,8 +708,10 @@ __global__ void __launch_bounds__(256) k_reward_end(const EnvDesc* __restrict__ 
 
 // ------------------------------------------------------------------ adjoint: G2P^T
 
-__global__ void __launch_bounds__(kBlock) k_g2p_adj(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
-                                                    int item_off, StateRef src, int use_perm) {
+template <int MAT>
+__global__ void __launch_bounds__(kBlock, 4) k_g2p_adj(const EnvDesc* __restrict__ envs,
+                                                       const WorkItem* __restrict__ items, int item_off, StateRef src,
+                                                       StateRef nxt, int use_perm) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   __shared__ int sred[6];
@@ -624,6 +719,7 @@ __global__ void __launch_bounds__(kBlock) k_g2p_adj(const EnvDesc* __restrict__ 
   const WorkItem it = items[item_off + blockIdx.x];
   load_env(envs, it.env, e, c);
   const float* b = ref_block(e, c, src);
+  const float* bn = ref_block(e, c, nxt);  // the substep's end state: holds v' and C'
   float* adj = c.par ? e.adj1 : e.adj0;
   const int sslot = step_slot(c, 1);
   const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
@@ -649,52 +745,39 @@ __global__ void __launch_bounds__(kBlock) k_g2p_adj(const EnvDesc* __restrict__ 
     zero_box(sb, bx.nx * bx.ny * bx.nz, 3);
     __syncthreads();
   }
-  const Mat m = env_mat(e);
+  Mat m = env_mat(e);
+  m.kind = MAT;  // compile-time material: the other laws' code is folded away
   const float Dinv = 4.0f * G * G, dt = e.dt, dx = e.dx;
-  const int lane_off = (threadIdx.x & 31) % 27;
+  const int nxy = bx.nx * bx.ny;
   const float vref[3] = {e.acc[ACC_VREF], e.acc[ACC_VREF + 1], e.acc[ACC_VREF + 2]};
 #pragma unroll 1
   for (int p = 0; p < kPPT; ++p) {
-    if (!valid[p]) continue;
-    const int i = it.start + threadIdx.x + p * kBlock;
+    // every lane runs the loop (warp collectives); lanes past the item's end carry zeros
+    const bool vp = valid[p];
+    const int i = vp ? it.start + threadIdx.x + p * kBlock : it.start;
     const int j = jj[p];
+    if (!vp) {
+      base[p][0] = bx.lx;
+      base[p][1] = bx.ly;
+      base[p][2] = bx.lz;
+    }
     float x[3], F[9];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] = b[a * np + j];
+    for (int a = 0; a < 3; ++a) x[a] = vp ? b[a * np + j] : (float)base[p][a] * dx + dx;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) F[a] = b[(15 + a) * np + j];
+    for (int a = 0; a < 9; ++a) F[a] = vp ? b[(15 + a) * np + j] : 0.0f;
     float fx[3], w[3][3], dwv[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       fx[a] = __fmul_rn(x[a], G) - (float)base[p][a];
       bspline(fx[a], w[a], dwv[a]);
     }
-    // recompute v', C'
-    float vn[3] = {0.f, 0.f, 0.f}, Cn[9];
+    // v' and C' as the forward G2P stored them in the substep's end state
+    float Cn[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) Cn[a] = 0.f;
+    for (int a = 0; a < 9; ++a) Cn[a] = vp ? bn[(6 + a) * np + i] : 0.0f;
     const float4 vc =
         __ldg(e.grid_v + ((long long)(base[p][2] + 1) * e.G + (base[p][1] + 1)) * e.G + base[p][0] + 1);
-#pragma unroll
-    for (int cz = 0; cz < 3; ++cz)
-#pragma unroll
-      for (int cy = 0; cy < 3; ++cy) {
-        const float4* row = e.grid_v + ((long long)(base[p][2] + cz) * e.G + (base[p][1] + cy)) * e.G + base[p][0];
-#pragma unroll
-        for (int cx = 0; cx < 3; ++cx) {
-          const float wt = w[0][cx] * w[1][cy] * w[2][cz];
-          const float4 gv = __ldg(row + cx);
-          const float r[3] = {((float)cx - fx[0]) * dx, ((float)cy - fx[1]) * dx, ((float)cz - fx[2]) * dx};
-          vn[0] += wt * gv.x;
-          vn[1] += wt * gv.y;
-          vn[2] += wt * gv.z;
-          const float g3[3] = {gv.x - vc.x, gv.y - vc.y, gv.z - vc.z};
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int bb = 0; bb < 3; ++bb) Cn[3 * a + bb] += Dinv * wt * g3[a] * r[bb];
-        }
-      }
     // trial H_t = H + dt (C' + C' H)   (F here holds H = F - I)
     float CH[9], Ft[9];
     matmul3(Cn, F, CH);
@@ -704,13 +787,13 @@ __global__ void __launch_bounds__(kBlock) k_g2p_adj(const EnvDesc* __restrict__ 
     float xb[3], vb[3], Cb[9], Fob[9];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      xb[a] = adj[a * np + i];
-      vb[a] = adj[(3 + a) * np + i];
+      xb[a] = vp ? adj[a * np + i] : 0.0f;
+      vb[a] = vp ? adj[(3 + a) * np + i] : 0.0f;
     }
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      Cb[a] = adj[(6 + a) * np + i];
-      Fob[a] = adj[(15 + a) * np + i];
+      Cb[a] = vp ? adj[(6 + a) * np + i] : 0.0f;
+      Fob[a] = vp ? adj[(15 + a) * np + i] : 0.0f;
     }
     float Ftb[9];
     project_vjp(m, Ft, Fob, Ftb);
@@ -728,57 +811,69 @@ __global__ void __launch_bounds__(kBlock) k_g2p_adj(const EnvDesc* __restrict__ 
     float vnb[3] = {vb[0] + dt * xb[0], vb[1] + dt * xb[1], vb[2] + dt * xb[2]};
     float xbp[3] = {xb[0], xb[1], xb[2]};
     // the grid receives sum w (v-bar' - V_ref); V_ref m_i/m_p is restored in the grid adjoint
-    const float vsh[3] = {vnb[0] - vref[0], vnb[1] - vref[1], vnb[2] - vref[2]};
-#pragma unroll 3
-    for (int nn = 0; nn < 27; ++nn) {
-      int kk = nn + lane_off;
-      kk = kk >= 27 ? kk - 27 : kk;
-      int cx, cy, cz;
-      stencil_node(kk, cx, cy, cz);
-      {
-        {
-          const float wxa = pick3(cx, w[0]), wyb = pick3(cy, w[1]), wzc = pick3(cz, w[2]);
-          const float wt = wxa * wyb * wzc;
-          const float gw[3] = {pick3(cx, dwv[0]) * wyb * wzc * G, wxa * pick3(cy, dwv[1]) * wzc * G,
-                               wxa * wyb * pick3(cz, dwv[2]) * G};
-          const float r[3] = {((float)cx - fx[0]) * dx, ((float)cy - fx[1]) * dx, ((float)cz - fx[2]) * dx};
-          const float4 gv = __ldg(e.grid_v + ((long long)(base[p][2] + cz) * e.G + (base[p][1] + cy)) * e.G +
-                                  base[p][0] + cx);
+    const float vsh[3] = {vp ? vnb[0] - vref[0] : 0.0f, vp ? vnb[1] - vref[1] : 0.0f, vp ? vnb[2] - vref[2] : 0.0f};
+    // each lane visits its stencil in its own rotated order (lanes of one cell then update
+    // different shared nodes at each step)
+    const int lane = threadIdx.x & 31;
+    const int rot_x = lane % 3, rot_y = (lane / 3) % 3, rot_z = (lane / 9) % 3;
+    Axis3 ax, ay, az;
+    rot_axis(rot_x, w[0], dwv[0], fx[0], dx, ax);
+    rot_axis(rot_y, w[1], dwv[1], fx[1], dx, ay);
+    rot_axis(rot_z, w[2], dwv[2], fx[2], dx, az);
+    const int b0 = base[p][0], b1 = base[p][1], b2 = base[p][2];
+    const int bi0 = bx.fits ? bx.idx(b0, b1, b2) : 0;
+#pragma unroll
+    for (int jz = 0; jz < 3; ++jz) {
+#pragma unroll
+      for (int jy = 0; jy < 3; ++jy) {
+        const float wyz = ay.w[jy] * az.w[jz], dwy_wz = ay.dw[jy] * az.w[jz], wy_dwz = ay.w[jy] * az.dw[jz];
+        const float ry = ay.r[jy], rz = az.r[jz];
+        // C-bar r = C-bar[:,0] rx + (C-bar[:,1] ry + C-bar[:,2] rz)
+        const float c0 = Cb[1] * ry + Cb[2] * rz, c1 = Cb[4] * ry + Cb[5] * rz, c2 = Cb[7] * ry + Cb[8] * rz;
+        const float4* rowp = e.grid_v + ((long long)(b2 + az.o[jz]) * e.G + (b1 + ay.o[jy])) * e.G + b0;
+        const int row = bi0 + az.o[jz] * nxy + ay.o[jy] * bx.nx;
+#pragma unroll
+        for (int jx = 0; jx < 3; ++jx) {
+          const float wt = ax.w[jx] * wyz;
+          const float gw0 = ax.dw[jx] * wyz * G, gw1 = ax.w[jx] * dwy_wz * G, gw2 = ax.w[jx] * wy_dwz * G;
+          const float rx = ax.r[jx];
+          const float Cr0 = c0 + Cb[0] * rx, Cr1 = c1 + Cb[3] * rx, Cr2 = c2 + Cb[6] * rx;
+          const float4 gv = __ldg(rowp + ax.o[jx]);
           // v_i - v_c: the stencil-uniform part of v_i adds nothing to x-bar (sum grad w = 0,
           // sum r grad w^T = I), so it is removed before the FP32 sums
-          const float g3[3] = {gv.x - vc.x, gv.y - vc.y, gv.z - vc.z};
-          float Cr[3], CTv[3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            Cr[a] = Cb[3 * a] * r[0] + Cb[3 * a + 1] * r[1] + Cb[3 * a + 2] * r[2];
-            CTv[a] = Cb[a] * g3[0] + Cb[3 + a] * g3[1] + Cb[6 + a] * g3[2];
-          }
-          float4 add;
-          add.x = wt * vsh[0] + Dinv * wt * Cr[0];
-          add.y = wt * vsh[1] + Dinv * wt * Cr[1];
-          add.z = wt * vsh[2] + Dinv * wt * Cr[2];
-          add.w = 0.0f;
-          const float sdw = vnb[0] * g3[0] + vnb[1] * g3[1] + vnb[2] * g3[2] +
-                            Dinv * (g3[0] * Cr[0] + g3[1] * Cr[1] + g3[2] * Cr[2]);
-#pragma unroll
-          for (int a = 0; a < 3; ++a) xbp[a] += sdw * gw[a] - Dinv * wt * CTv[a];
-          const int ix = base[p][0] + cx, iy = base[p][1] + cy, iz = base[p][2] + cz;
-          if (bx.fits) {
-            const int bi = bx.idx(ix, iy, iz);
-            atomicAdd(&sb.v[bi], add.x);
-            atomicAdd(&sb.v[kBoxNodes + bi], add.y);
-            atomicAdd(&sb.v[2 * kBoxNodes + bi], add.z);
-          } else {
-            atomicAdd(e.grid_vb + ((long long)iz * e.G + iy) * e.G + ix, add);
+          const float g0 = gv.x - vc.x, g1 = gv.y - vc.y, g2 = gv.z - vc.z;
+          const float CTv0 = Cb[0] * g0 + Cb[3] * g1 + Cb[6] * g2;
+          const float CTv1 = Cb[1] * g0 + Cb[4] * g1 + Cb[7] * g2;
+          const float CTv2 = Cb[2] * g0 + Cb[5] * g1 + Cb[8] * g2;
+          const float dwt = Dinv * wt;
+          float a0 = wt * vsh[0] + dwt * Cr0;
+          float a1 = wt * vsh[1] + dwt * Cr1;
+          float a2 = wt * vsh[2] + dwt * Cr2;
+          const float sdw = vnb[0] * g0 + vnb[1] * g1 + vnb[2] * g2 + Dinv * (g0 * Cr0 + g1 * Cr1 + g2 * Cr2);
+          xbp[0] += sdw * gw0 - dwt * CTv0;
+          xbp[1] += sdw * gw1 - dwt * CTv1;
+          xbp[2] += sdw * gw2 - dwt * CTv2;
+          if (vp) {
+            if (bx.fits) {
+              const int bi = row + ax.o[jx];
+              atomicAdd(&sb.v[bi], a0);
+              atomicAdd(&sb.v[kBoxNodes + bi], a1);
+              atomicAdd(&sb.v[2 * kBoxNodes + bi], a2);
+            } else {
+              const int ix = b0 + ax.o[jx], iy = b1 + ay.o[jy], iz = b2 + az.o[jz];
+              atomicAdd(e.grid_vb + ((long long)iz * e.G + iy) * e.G + ix, make_float4(a0, a1, a2, 0.f));
+            }
           }
         }
       }
     }
     // partial adjoint in place: x-bar and F-bar slots
+    if (vp) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) adj[a * np + i] = xbp[a];
+      for (int a = 0; a < 3; ++a) adj[a * np + i] = xbp[a];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) adj[(15 + a) * np + i] = Fbp[a];
+      for (int a = 0; a < 9; ++a) adj[(15 + a) * np + i] = Fbp[a];
+    }
   }
   if (bx.fits) {
     __syncthreads();
@@ -961,7 +1056,8 @@ __global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ en
 
 // ------------------------------------------------------------------ adjoint: P2G^T
 
-__global__ void __launch_bounds__(kBlock) k_p2g_adj(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
+template <int MAT>
+__global__ void __launch_bounds__(kBlock, 4) k_p2g_adj(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
                                                     int item_off, StateRef src, int use_perm) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
@@ -974,7 +1070,8 @@ __global__ void __launch_bounds__(kBlock) k_p2g_adj(const EnvDesc* __restrict__ 
   const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
   const long long np = e.n_pad;
   const float G = (float)e.G;
-  const Mat m = env_mat(e);
+  Mat m = env_mat(e);
+  m.kind = MAT;  // compile-time material: the other laws' code is folded away
   const float Dinv = 4.0f * G * G, dx = e.dx, pm = e.p_mass;
   const float stress_k = -e.dt * e.p_vol * Dinv;
 #pragma unroll 1
@@ -985,7 +1082,7 @@ __global__ void __launch_bounds__(kBlock) k_p2g_adj(const EnvDesc* __restrict__ 
     float s[kComp];
     load_state(b, np, j, s);
     const unsigned meta = reinterpret_cast<const unsigned*>(b + kComp * np)[j];
-    const float a_g = group_act(e, sslot, meta);
+    const float a_g = MAT == MAT_MUSCLE ? group_act(e, sslot, meta) : 0.0f;
     int base[3], oob = 0;
     float fx[3], w[3][3], dwv[3][3];
 #pragma unroll
@@ -1057,7 +1154,7 @@ __global__ void __launch_bounds__(kBlock) k_p2g_adj(const EnvDesc* __restrict__ 
       adj_out[(6 + q) * np + o] = Cbn[q];
       adj_out[(15 + q) * np + o] = Fbn[q];
     }
-    if (e.material == MAT_MUSCLE) {
+    if (MAT == MAT_MUSCLE) {
       const int g = (int)(meta >> 20) - 1;
       if (g >= 0 && g < e.n_groups) atomicAdd(e.acc + ACC_ACT + e.n_coll_act + g, agb);
     }
@@ -1321,8 +1418,13 @@ static inline int nblk(int n, int b) { return (n + b - 1) / b; }
 void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k) {
   if (L.n_items == 0) return;
   Timed tm_(KC_P2G, L.stream);
-  k_p2g<<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k,
-                                            src.kind == REF_RING || src.kind == REF_REV ? 1 : 0, L.active, L.active_n);
+  const int rev = src.kind == REF_RING || src.kind == REF_REV ? 1 : 0;
+  switch (L.material) {
+    case MAT_NEOHOOKEAN: k_p2g<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n); break;
+    case MAT_VONMISES: k_p2g<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n); break;
+    case MAT_FLUID: k_p2g<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n); break;
+    default: k_p2g<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n); break;
+  }
 }
 
 void launch_grid(const Launch& L, int k, GridMode mode, bool rev) {
@@ -1335,7 +1437,12 @@ void launch_g2p(const Launch& L, StateRef src, StateRef dst, bool use_perm, int 
   if (L.n_items == 0) return;
   Timed tm_(KC_G2P, L.stream);
   const int rev = (dst.kind == REF_RING) ? 1 : 0;
-  k_g2p<<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev);
+  switch (L.material) {
+    case MAT_NEOHOOKEAN: k_g2p<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev); break;
+    case MAT_VONMISES: k_g2p<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev); break;
+    case MAT_FLUID: k_g2p<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev); break;
+    default: k_g2p<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev); break;
+  }
 }
 
 void launch_step_begin(const Launch& L, const float* act_in, int a_max, bool record) {
@@ -1348,11 +1455,16 @@ void launch_reward_end(const Launch& L, float* reward_out, bool record) {
   k_reward_end<<<L.n_env, 256, 0, L.stream>>>(L.envs, L.env0, reward_out, record ? 1 : 0);
 }
 
-void launch_g2p_adj(const Launch& L, StateRef src, bool use_perm, int k) {
+void launch_g2p_adj(const Launch& L, StateRef src, StateRef nxt, bool use_perm, int k) {
   (void)k;
   if (L.n_items == 0) return;
   Timed tm_(KC_G2P_ADJ, L.stream);
-  k_g2p_adj<<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0);
+  switch (L.material) {
+    case MAT_NEOHOOKEAN: k_g2p_adj<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0); break;
+    case MAT_VONMISES: k_g2p_adj<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0); break;
+    case MAT_FLUID: k_g2p_adj<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0); break;
+    default: k_g2p_adj<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0); break;
+  }
 }
 
 void launch_grid_adj(const Launch& L, int k) {
@@ -1364,7 +1476,12 @@ void launch_p2g_adj(const Launch& L, StateRef src, bool use_perm, int k) {
   (void)k;
   if (L.n_items == 0) return;
   Timed tm_(KC_P2G_ADJ, L.stream);
-  k_p2g_adj<<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0);
+  switch (L.material) {
+    case MAT_NEOHOOKEAN: k_p2g_adj<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0); break;
+    case MAT_VONMISES: k_p2g_adj<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0); break;
+    case MAT_FLUID: k_p2g_adj<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0); break;
+    default: k_p2g_adj<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0); break;
+  }
 }
 
 void launch_bwd_init(const Launch& L, int T) {

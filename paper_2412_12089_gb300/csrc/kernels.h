@@ -28,6 +28,7 @@ void set_timing_hook(const TimingHook* h);
 struct Launch {
   const EnvDesc* envs;   // device array
   const WorkItem* items; // device array of particle work items
+  int material = 0;      // material of every item in [item_offset, item_offset + n_items)
   int n_items;
   int item_offset;       // first item (per-environment launches)
   uint2* active;         // active-tile list (env, tile)
@@ -46,7 +47,8 @@ void launch_g2p(const Launch& L, StateRef src, StateRef dst, bool use_perm, int 
 void launch_step_begin(const Launch& L, const float* act_in, int a_max, bool record);
 void launch_reward_end(const Launch& L, float* reward_out, bool record);
 
-void launch_g2p_adj(const Launch& L, StateRef src, bool use_perm, int k);
+// nxt: the substep's end state (v', C' written by the forward G2P)
+void launch_g2p_adj(const Launch& L, StateRef src, StateRef nxt, bool use_perm, int k);
 void launch_grid_adj(const Launch& L, int k);
 void launch_p2g_adj(const Launch& L, StateRef src, bool use_perm, int k);
 // Reverse pass bookkeeping.  bwd_init sets the step index to T; each rev_begin decrements

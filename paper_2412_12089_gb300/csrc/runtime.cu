@@ -18,7 +18,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mpm.h"
+#include "mpm.h"
 #include "kernels.h"
 #include "mpm_types.h"
 
@@ -52,9 +52,14 @@ struct mpm_ctx {
   std::vector<mpm_env_spec> specs;
   std::vector<EnvDesc> desc;
   EnvDesc* d_desc = nullptr;
-  std::vector<WorkItem> items;            // sorted by substep count, descending
+  std::vector<WorkItem> items;            // grouped by material, then by substep count descending
   WorkItem* d_items = nullptr;
-  std::vector<int> items_with_S_gt;       // [k] = #items whose env has S > k
+  struct MatGroup {
+    int material;
+    int item0;               // first item of the group
+    std::vector<int> n_gt;   // [k] = items of the group whose env has S > k
+  };
+  std::vector<MatGroup> groups;
   std::vector<int> env_item0, env_nitems; // per-env item ranges (per-env launches)
   std::vector<WorkItem> items_env_order;  // items grouped by env (per-env launches)
   WorkItem* d_items_env = nullptr;
@@ -162,18 +167,24 @@ Launch env_launch(mpm_ctx* c, int e, cudaStream_t st) {
 
 // ---------------------------------------------------------------- step bodies
 
-// All substeps of a forward control step for the launch's items (L.n_items scaled per k).
-void enqueue_substeps_fwd(mpm_ctx* c, Launch L, const std::vector<int>* nk) {
+// Launch of one material group's items whose env runs more than k substeps.
+Launch group_launch(mpm_ctx* c, const Launch& L, const mpm_ctx::MatGroup& g, int k) {
+  Launch Lg = L;
+  Lg.material = g.material;
+  Lg.item_offset = g.item0;
+  Lg.n_items = g.n_gt[std::min(k, c->S_max)];
+  return Lg;
+}
+
+// All substeps of a forward control step, every material group.
+void enqueue_substeps_fwd(mpm_ctx* c, Launch L) {
   for (int k = 0; k < c->S_max; ++k) {
-    Launch Lk = L;
-    if (nk) Lk.n_items = (*nk)[k];
-    if (Lk.n_items == 0) break;
     cudaMemsetAsync(c->active_n, 0, sizeof(int), L.stream);
     const StateRef src{k == 0 ? REF_LIVE : REF_NEXT, k};
     const StateRef dst{REF_NEXT, k};
-    launch_p2g(Lk, src, k == 0, k);
-    launch_grid(Lk, k, GRID_FWD, false);
-    launch_g2p(Lk, src, dst, k == 0, k);
+    for (auto& g : c->groups) launch_p2g(group_launch(c, L, g, k), src, k == 0, k);
+    launch_grid(L, k, GRID_FWD, false);
+    for (auto& g : c->groups) launch_g2p(group_launch(c, L, g, k), src, dst, k == 0, k);
   }
 }
 
@@ -182,12 +193,13 @@ void enqueue_forward(mpm_ctx* c, cudaStream_t st, bool record) {
     Launch L = make_launch(c, st);
     launch_step_begin(L, c->act_in, c->A_max, record);
     bin_envs(L, 0, c->P, c->cell_bits, c->key_bits, c->sort);
-    enqueue_substeps_fwd(c, L, &c->items_with_S_gt);
+    enqueue_substeps_fwd(c, L);
     launch_reward_end(L, c->rew, record);
   } else {
     // baseline path: every stage launched once per environment
     for (int e = 0; e < c->n_envs; ++e) {
       Launch L = env_launch(c, e, st);
+      L.material = c->specs[e].material;
       launch_step_begin(L, c->act_in, c->A_max, record);
       bin_envs(L, c->desc[e].poff, c->specs[e].n_particles, c->cell_bits, c->cell_bits, c->sort);
       for (int k = 0; k < c->specs[e].substeps; ++k) {
@@ -203,35 +215,61 @@ void enqueue_forward(mpm_ctx* c, cudaStream_t st, bool record) {
   }
 }
 
-// One reverse control step (the step index comes from the device counters).
-void enqueue_reverse_step(mpm_ctx* c, Launch L, int S, const std::vector<int>* nk, bool have_rbar) {
+// One reverse control step (the step index comes from the device counters).  groups: the
+// material groups to launch (per-environment launches pass a single group).
+void enqueue_reverse_step(mpm_ctx* c, Launch L, int S, const std::vector<mpm_ctx::MatGroup>& groups, bool have_rbar) {
   launch_rev_begin(L);
   if (have_rbar) launch_reward_adj(L, c->rbar, c->n_envs);
   launch_adj_ref(L);
-  // recompute substep states 1..S-1 into the ring
+  auto gl = [&](const mpm_ctx::MatGroup& g, int k) {
+    Launch Lg = L;
+    Lg.material = g.material;
+    Lg.item_offset = g.item0;
+    Lg.n_items = g.n_gt[std::min(k, (int)g.n_gt.size() - 1)];
+    return Lg;
+  };
+  // recompute substep states 1..S-1 into the ring (envs with S > k + 1)
   for (int k = 0; k + 1 < S; ++k) {
-    Launch Lk = L;
-    if (nk) Lk.n_items = (*nk)[k + 1];
-    if (Lk.n_items == 0) break;
     cudaMemsetAsync(c->active_n, 0, sizeof(int), L.stream);
     const StateRef src{k == 0 ? REF_REV : REF_RING, k};
     const StateRef dst{REF_RING, k + 1};
-    launch_p2g(Lk, src, k == 0, k);
-    launch_grid(Lk, k, GRID_FWD, true);
-    launch_g2p(Lk, src, dst, k == 0, k);
+    for (auto& g : groups) {
+      Launch Lg = gl(g, k);
+      Lg.n_items = g.n_gt[std::min(k + 1, (int)g.n_gt.size() - 1)];
+      launch_p2g(Lg, src, k == 0, k);
+    }
+    launch_grid(L, k, GRID_FWD, true);
+    for (auto& g : groups) {
+      Launch Lg = gl(g, k);
+      Lg.n_items = g.n_gt[std::min(k + 1, (int)g.n_gt.size() - 1)];
+      launch_g2p(Lg, src, dst, k == 0, k);
+    }
   }
-  // adjoint substeps, last to first
+  // adjoint substeps, last to first (envs with S > k)
   for (int k = S - 1; k >= 0; --k) {
-    Launch Lk = L;
-    if (nk) Lk.n_items = (*nk)[k];
-    if (Lk.n_items == 0) continue;
     cudaMemsetAsync(c->active_n, 0, sizeof(int), L.stream);
     const StateRef src{k == 0 ? REF_REV : REF_RING, k};
-    launch_p2g(Lk, src, k == 0, k);
-    launch_grid(Lk, k, GRID_KEEP, true);
-    launch_g2p_adj(Lk, src, k == 0, k);
-    launch_grid_adj(Lk, k);
-    launch_p2g_adj(Lk, src, k == 0, k);
+    for (auto& g : groups) launch_p2g(gl(g, k), src, k == 0, k);
+    launch_grid(L, k, GRID_KEEP, true);
+    // the end state of substep k is ring block k+1 for envs with S > k+1 (a prefix of the
+    // group) and the step's end checkpoint for envs whose last substep is k
+    for (auto& g : groups) {
+      Launch Lg = gl(g, k);
+      const int n_ring = g.n_gt[std::min(k + 1, (int)g.n_gt.size() - 1)];
+      if (n_ring > 0) {
+        Launch La = Lg;
+        La.n_items = n_ring;
+        launch_g2p_adj(La, src, StateRef{REF_RING, k + 1}, k == 0, k);
+      }
+      if (Lg.n_items > n_ring) {
+        Launch Lb = Lg;
+        Lb.item_offset += n_ring;
+        Lb.n_items -= n_ring;
+        launch_g2p_adj(Lb, src, StateRef{REF_REVEND, 0}, k == 0, k);
+      }
+    }
+    launch_grid_adj(L, k);
+    for (auto& g : groups) launch_p2g_adj(gl(g, k), src, k == 0, k);
   }
   launch_rev_end(L, c->agrad, c->n_envs, c->A_max);
 }
@@ -304,7 +342,7 @@ void body_fwd(mpm_ctx* c, cudaStream_t st, void* arg) { enqueue_forward(c, st, *
 
 void body_rev(mpm_ctx* c, cudaStream_t st, void* arg) {
   Launch L = make_launch(c, st);
-  enqueue_reverse_step(c, L, c->S_max, &c->items_with_S_gt, *(bool*)arg);
+  enqueue_reverse_step(c, L, c->S_max, c->groups, *(bool*)arg);
 }
 
 }  // namespace
@@ -475,16 +513,21 @@ mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* 
     }
     ctx->env_nitems.push_back(cnt);
   }
+  // particle kernels are compiled per material: group the items by material, and within
+  // a group by substep count (descending) so substep k launches a prefix of the group
   ctx->items = ctx->items_env_order;
   std::stable_sort(ctx->items.begin(), ctx->items.end(), [&](const WorkItem& a, const WorkItem& b) {
-    return ctx->specs[a.env].substeps > ctx->specs[b.env].substeps;
+    const auto &sa = ctx->specs[a.env], &sb = ctx->specs[b.env];
+    if (sa.material != sb.material) return sa.material < sb.material;
+    return sa.substeps > sb.substeps;
   });
-  ctx->items_with_S_gt.assign(S_max + 1, 0);
-  for (int k = 0; k <= S_max; ++k) {
-    int c = 0;
-    for (auto& it : ctx->items)
-      if (ctx->specs[it.env].substeps > k) ++c;
-    ctx->items_with_S_gt[k] = c;
+  for (size_t i = 0; i < ctx->items.size(); ++i) {
+    const int mat = ctx->specs[ctx->items[i].env].material;
+    if (ctx->groups.empty() || ctx->groups.back().material != mat)
+      ctx->groups.push_back({mat, (int)i, std::vector<int>(S_max + 1, 0)});
+    auto& g = ctx->groups.back();
+    for (int k = 0; k <= S_max; ++k)
+      if (ctx->specs[ctx->items[i].env].substeps > k) g.n_gt[k] += 1;
   }
 
   // ---- device arrays
@@ -678,7 +721,11 @@ mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const fl
       Enqueue q(ctx);
       for (int e = 0; e < ctx->n_envs; ++e) {
         Launch Le = env_launch(ctx, e, st);
-        enqueue_reverse_step(ctx, Le, ctx->specs[e].substeps, nullptr, have_rbar);
+        const int S = ctx->specs[e].substeps;
+        std::vector<mpm_ctx::MatGroup> one{{ctx->specs[e].material, ctx->env_item0[e],
+                                            std::vector<int>(S + 1, ctx->env_nitems[e])}};
+        one[0].n_gt[S] = 0;
+        enqueue_reverse_step(ctx, Le, S, one, have_rbar);
       }
       CK(cudaGetLastError());
     } else {
