@@ -1,0 +1,394 @@
+// engine.cu -- step machinery shared by the batch context and the server (see engine.h).
+//
+// A forward control step (the paper's env.step, Alg. 1): bin the live state, then S substeps
+// of P2G -> grid -> G2P, then rewards.  A reverse control step (Sec. 4.1): restore the step's
+// checkpoint, recompute its substeps into the ring, then run G2P^T -> grid^T -> P2G^T from the
+// last substep to the first.
+#include "engine.h"
+
+#include <algorithm>
+#include <cstring>
+
+namespace mpm {
+
+namespace {
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+int bits_for(unsigned long long v) {
+  int b = 0;
+  while (b < 64 && (v >> b) != 0ull) ++b;
+  return b;
+}
+}  // namespace
+
+const char* check_spec(const mpm_env_spec& s) {
+  if (s.n_particles < 1 || s.n_particles > (int)kIdMask) return "n_particles";
+  if (s.grid_res < 8 || s.grid_res > 128 || s.grid_res % 4) return "grid_res";
+  if (s.substeps < 1 || s.substeps > 4096) return "substeps";
+  if (s.bound < 0 || 2 * s.bound >= s.grid_res) return "bound";
+  if (s.material < 0 || s.material > 3) return "material";
+  if (s.collider < 0 || s.collider > 3) return "collider";
+  if (s.n_coll_act < 0 || s.n_coll_act > 4) return "n_coll_act";
+  for (int j = 0; j < s.n_coll_act; ++j)
+    if (s.act_map[j] < 0 || s.act_map[j] > 3) return "act_map";
+  if (s.n_groups < 0 || s.n_groups > 4094) return "n_groups";
+  if (s.n_coll_act + s.n_groups > kMaxAct) return "action dim";
+  if (s.reward < 0 || s.reward > 3) return "reward";
+  if (s.reward != 0 && s.n_sub < 1) return "n_sub";
+  if (!(s.dt > 0.f) || !(s.p_vol > 0.f) || !(s.rho > 0.f)) return "dt/p_vol/rho";
+  if (s.reward == 1 && !(s.rparam[0] != 0.f)) return "rparam (h_flat)";
+  if ((s.material == 0 || s.material == 1 || s.material == 3) && !(s.E > 0.f && s.nu >= 0.f && s.nu < 0.5f))
+    return "E/nu";
+  return nullptr;
+}
+
+EnvLayout env_layout(const mpm_env_spec& s, int n_slots, bool tape, bool own, int T) {
+  EnvLayout L;
+  L.n_slots = n_slots;
+  L.tape = tape;
+  L.own = own;
+  L.T = own ? T : 0;
+  const long long n_pad = ((long long)s.n_particles + 31) / 32 * 32;
+  L.n_pad = n_pad;
+  const long long block = 25 * n_pad;
+  const long long G3 = (long long)s.grid_res * s.grid_res * s.grid_res;
+  const long long TG3 = (long long)(s.grid_res / 4) * (s.grid_res / 4) * (s.grid_res / 4);
+  const int A = std::max(1, s.n_coll_act + s.n_groups);
+  size_t cur = 0;
+  L.slots = cur; cur = align256(cur + (size_t)n_slots * block * 4);
+  L.ring = cur;  if (tape) cur = align256(cur + (size_t)std::max(s.substeps - 1, 0) * block * 4);
+  L.adj = cur;   if (tape) cur = align256(cur + (size_t)2 * kComp * n_pad * 4);
+  L.perm = cur;  cur = align256(cur + (size_t)n_slots * n_pad * 4);
+  L.grid = cur;  cur = align256(cur + (size_t)(tape ? 4 : 2) * G3 * 16);
+  L.tile = cur;  cur = align256(cur + (size_t)TG3 * 4);
+  L.pose = cur;  cur = align256(cur + (size_t)n_slots * 4 * 4);
+  L.act = cur;   cur = align256(cur + (size_t)n_slots * A * 4);
+  if (own) {
+    L.acc = cur;       cur = align256(cur + (size_t)(ACC_ACT + A) * 4);
+    L.ctr = cur;       cur = align256(cur + sizeof(EnvCtr));
+    L.act_env = cur;   cur = align256(cur + (size_t)std::max(T, 1) * A * 4);
+    L.rew_env = cur;   cur = align256(cur + (size_t)std::max(T, 1) * 4);
+    L.rbar_env = cur;  cur = align256(cur + (size_t)std::max(T, 1) * 4);
+    L.agrad_env = cur; cur = align256(cur + (size_t)std::max(T, 1) * A * 4);
+    L.xout = cur;      cur = align256(cur + (size_t)s.n_particles * 3 * 4);
+  }
+  L.total = cur;
+  return L;
+}
+
+void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base, float* acc, EnvCtr* ctr) {
+  memset(&d, 0, sizeof d);
+  d.n = s.n_particles;
+  d.n_pad = (int)L.n_pad;
+  d.G = s.grid_res;
+  d.S = s.substeps;
+  d.bound = s.bound;
+  d.n_slots = L.n_slots;
+  d.material = s.material;
+  d.coll_kind = s.collider;
+  d.n_coll_act = s.n_coll_act;
+  d.n_groups = s.n_groups;
+  d.reward_kind = s.reward;
+  d.n_sub = s.n_sub;
+  d.A = s.n_coll_act + s.n_groups;
+  for (int j = 0; j < 4; ++j) {
+    d.act_map[j] = s.act_map[j];
+    d.coll_dims[j] = s.coll_dims[j];
+    d.act_scale[j] = s.act_scale[j];
+    d.rparam[j] = s.rparam[j];
+  }
+  d.dt = s.dt;
+  d.dx = 1.0f / (float)s.grid_res;
+  d.inv_dx = (float)s.grid_res;
+  d.p_vol = s.p_vol;
+  d.p_mass = s.rho * s.p_vol;
+  for (int i = 0; i < 3; ++i) d.gravity[i] = s.gravity[i];
+  if (s.material == 0 || s.material == 1 || s.material == 3) {
+    const double E = s.E, nu = s.nu;
+    d.mu = (float)(E / (2.0 * (1.0 + nu)));
+    d.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+  }
+  d.cyl = d.mu > 0.f ? (float)((double)s.c_y * s.yield_stress / (2.0 * d.mu)) : 0.f;
+  d.bulk = s.bulk;
+  d.visc = s.visc;
+  d.act_stress = s.act_stress;
+  d.coll_mu = s.coll_mu;
+  d.alpha = s.alpha;
+  d.ground_mu = s.ground_mu;
+  d.block = 25 * L.n_pad;
+  const long long G3 = (long long)d.G * d.G * d.G;
+  d.slots = (float*)(base + L.slots);
+  d.ring = L.tape ? (float*)(base + L.ring) : nullptr;
+  d.adj0 = L.tape ? (float*)(base + L.adj) : nullptr;
+  d.adj1 = L.tape ? d.adj0 + (size_t)kComp * L.n_pad : nullptr;
+  d.perm = (unsigned*)(base + L.perm);
+  float4* g = (float4*)(base + L.grid);
+  d.grid_mp = g;
+  d.grid_v = g + G3;
+  d.grid_vb = L.tape ? g + 2 * G3 : nullptr;
+  d.grid_mpb = L.tape ? g + 3 * G3 : nullptr;
+  d.tile = (unsigned*)(base + L.tile);
+  d.pose = (float*)(base + L.pose);
+  d.act = (float*)(base + L.act);
+  if (L.own) {
+    d.acc = (float*)(base + L.acc);
+    d.ctr = (EnvCtr*)(base + L.ctr);
+    d.act_env = (const float*)(base + L.act_env);
+    d.rew_env = (float*)(base + L.rew_env);
+    d.rbar_env = (const float*)(base + L.rbar_env);
+    d.agrad_env = (float*)(base + L.agrad_env);
+  } else {
+    d.acc = acc;
+    d.ctr = ctr;
+  }
+}
+
+void Group::release() {
+  void* ptrs[] = {d_desc, d_items, d_items_env, active, active_n, sort.keys[0], sort.keys[1], sort.vals[0],
+                  sort.vals[1], sort.hist};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  d_desc = nullptr;
+  d_items = d_items_env = nullptr;
+  active = nullptr;
+  active_n = nullptr;
+  sort = SortScratch{};
+  desc_cap = items_cap = 0;
+  active_cap = hist_cap = 0;
+}
+
+namespace {
+template <typename T>
+cudaError_t ensure(T*& p, size_t& cap, size_t n) {
+  if (n <= cap && p) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  const size_t want = std::max<size_t>(n + n / 4, 16);
+  cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+  cap = e == cudaSuccess ? want : 0;
+  return e;
+}
+}  // namespace
+
+cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::vector<mpm_env_spec>& specs) {
+  g.desc = descs;
+  g.spec = specs;
+  g.n_envs = (int)descs.size();
+  g.S_max = 1;
+  g.A_max = 1;
+  g.P = 0;
+  g.tiles = 0;
+  int G_max = 8;
+  for (int e = 0; e < g.n_envs; ++e) {
+    const auto& s = specs[e];
+    g.S_max = std::max(g.S_max, s.substeps);
+    g.A_max = std::max(g.A_max, s.n_coll_act + s.n_groups);
+    G_max = std::max(G_max, s.grid_res);
+    g.desc[e].key_env = (unsigned)e;
+    g.desc[e].poff = g.P;
+    g.P += s.n_particles;
+    g.tiles += (long long)(s.grid_res / 4) * (s.grid_res / 4) * (s.grid_res / 4);
+  }
+  const unsigned long long max_cell = (unsigned long long)(G_max / 4) * (G_max / 4) * (G_max / 4) * 64ull - 1ull;
+  g.cell_bits = bits_for(max_cell);
+  g.key_bits = g.cell_bits + bits_for((unsigned long long)std::max(g.n_envs - 1, 0));
+  // work items: runs of <= kChunk particles of one environment
+  g.items_env.clear();
+  g.env_item0.clear();
+  g.env_nitems.clear();
+  for (int e = 0; e < g.n_envs; ++e) {
+    g.env_item0.push_back((int)g.items_env.size());
+    int cnt = 0;
+    for (int s0 = 0; s0 < specs[e].n_particles; s0 += kChunk) {
+      g.items_env.push_back(WorkItem{e, s0, std::min(kChunk, specs[e].n_particles - s0), 0});
+      ++cnt;
+    }
+    g.env_nitems.push_back(cnt);
+  }
+  // particle kernels are compiled per material: items grouped by material, then by
+  // substep count (descending) so substep k launches a prefix of each material's items
+  g.items = g.items_env;
+  std::stable_sort(g.items.begin(), g.items.end(), [&](const WorkItem& a, const WorkItem& b) {
+    const auto &sa = specs[a.env], &sb = specs[b.env];
+    if (sa.material != sb.material) return sa.material < sb.material;
+    return sa.substeps > sb.substeps;
+  });
+  g.mats.clear();
+  for (size_t i = 0; i < g.items.size(); ++i) {
+    const int mat = specs[g.items[i].env].material;
+    if (g.mats.empty() || g.mats.back().material != mat)
+      g.mats.push_back({mat, (int)i, std::vector<int>(g.S_max + 1, 0)});
+    auto& m = g.mats.back();
+    for (int k = 0; k <= g.S_max; ++k)
+      if (specs[g.items[i].env].substeps > k) m.n_gt[k] += 1;
+  }
+  cudaError_t e;
+  size_t cap;
+  cap = g.desc_cap;
+  if ((e = ensure(g.d_desc, cap, std::max<size_t>(g.n_envs, 1))) != cudaSuccess) return e;
+  g.desc_cap = cap;
+  if (g.n_envs && (e = cudaMemcpy(g.d_desc, g.desc.data(), sizeof(EnvDesc) * g.n_envs, cudaMemcpyHostToDevice)))
+    return e;
+  size_t cap1 = g.items_cap, cap2 = g.items_cap;
+  if ((e = ensure(g.d_items, cap1, std::max<size_t>(g.items.size(), 1))) != cudaSuccess) return e;
+  if ((e = ensure(g.d_items_env, cap2, std::max<size_t>(g.items.size(), 1))) != cudaSuccess) return e;
+  g.items_cap = std::min(cap1, cap2);
+  if (!g.items.empty()) {
+    if ((e = cudaMemcpy(g.d_items, g.items.data(), sizeof(WorkItem) * g.items.size(), cudaMemcpyHostToDevice))) return e;
+    if ((e = cudaMemcpy(g.d_items_env, g.items_env.data(), sizeof(WorkItem) * g.items_env.size(),
+                        cudaMemcpyHostToDevice)))
+      return e;
+  }
+  size_t acap = (size_t)g.active_cap;
+  if ((e = ensure(g.active, acap, std::max<size_t>((size_t)g.tiles, 1))) != cudaSuccess) return e;
+  g.active_cap = (long long)acap;
+  if (!g.active_n) {
+    if ((e = cudaMalloc(&g.active_n, sizeof(int)))) return e;
+    cudaMemset(g.active_n, 0, sizeof(int));
+  }
+  size_t scap = (size_t)g.sort.cap;
+  size_t c0 = scap, c1 = scap, c2 = scap, c3 = scap;
+  const size_t P = std::max<size_t>((size_t)g.P, 1);
+  if ((e = ensure(g.sort.keys[0], c0, P)) || (e = ensure(g.sort.keys[1], c1, P)) || (e = ensure(g.sort.vals[0], c2, P)) ||
+      (e = ensure(g.sort.vals[1], c3, P)))
+    return e;
+  g.sort.cap = (long long)std::min(std::min(c0, c1), std::min(c2, c3));
+  size_t hcap = (size_t)g.hist_cap;
+  if ((e = ensure(g.sort.hist, hcap, 256 * ((P + 4095) / 4096)))) return e;
+  g.hist_cap = (long long)hcap;
+  return cudaSuccess;
+}
+
+Launch group_launch(const Group& g, cudaStream_t st) {
+  Launch L;
+  L.envs = g.d_desc;
+  L.items = g.d_items;
+  L.material = 0;
+  L.n_items = (int)g.items.size();
+  L.item_offset = 0;
+  L.active = g.active;
+  L.active_n = g.active_n;
+  L.grid_blocks = 152 * 8;
+  L.env0 = 0;
+  L.n_env = g.n_envs;
+  L.stream = st;
+  return L;
+}
+
+Launch env_launch(const Group& g, int e, cudaStream_t st) {
+  Launch L = group_launch(g, st);
+  L.items = g.d_items_env;
+  L.item_offset = g.env_item0[e];
+  L.n_items = g.env_nitems[e];
+  L.material = g.spec[e].material;
+  L.env0 = e;
+  L.n_env = 1;
+  const int G = g.spec[e].grid_res;
+  L.grid_blocks = std::max(1, std::min(152 * 8, (G / 4) * (G / 4) * (G / 4) / 8));
+  return L;
+}
+
+namespace {
+
+Launch mat_launch(const Launch& L, const MatGroup& m, int k) {
+  Launch Lm = L;
+  Lm.material = m.material;
+  Lm.item_offset = m.item0;
+  Lm.n_items = m.n_gt[std::min(k, (int)m.n_gt.size() - 1)];
+  return Lm;
+}
+
+void substeps_forward(Group& g, const Launch& L, const std::vector<MatGroup>& mats, int S) {
+  for (int k = 0; k < S; ++k) {
+    cudaMemsetAsync(L.active_n, 0, sizeof(int), L.stream);
+    const StateRef src{k == 0 ? REF_LIVE : REF_NEXT, k};
+    const StateRef dst{REF_NEXT, k};
+    for (auto& m : mats) launch_p2g(mat_launch(L, m, k), src, k == 0, k);
+    launch_grid(L, k, GRID_FWD, false);
+    for (auto& m : mats) launch_g2p(mat_launch(L, m, k), src, dst, k == 0, k);
+  }
+}
+
+void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, const float* rbar, float* agrad,
+                  int n_tot, int a_max) {
+  launch_rev_begin(L);
+  launch_reward_adj(L, rbar, n_tot);
+  launch_adj_ref(L);
+  // recompute substep states 1..S-1 into the ring (envs with S > k + 1)
+  for (int k = 0; k + 1 < S; ++k) {
+    cudaMemsetAsync(L.active_n, 0, sizeof(int), L.stream);
+    const StateRef src{k == 0 ? REF_REV : REF_RING, k};
+    const StateRef dst{REF_RING, k + 1};
+    for (auto& m : mats) launch_p2g(mat_launch(L, m, k + 1), src, k == 0, k);
+    launch_grid(L, k, GRID_FWD, true);
+    for (auto& m : mats) launch_g2p(mat_launch(L, m, k + 1), src, dst, k == 0, k);
+  }
+  // adjoint substeps, last to first (envs with S > k)
+  for (int k = S - 1; k >= 0; --k) {
+    cudaMemsetAsync(L.active_n, 0, sizeof(int), L.stream);
+    const StateRef src{k == 0 ? REF_REV : REF_RING, k};
+    for (auto& m : mats) launch_p2g(mat_launch(L, m, k), src, k == 0, k);
+    launch_grid(L, k, GRID_KEEP, true);
+    // the end state of substep k: ring block k+1 for envs with S > k+1 (a prefix of the
+    // material's items), the step's end checkpoint for envs whose last substep is k
+    for (auto& m : mats) {
+      const Launch Lm = mat_launch(L, m, k);
+      const int n_ring = m.n_gt[std::min(k + 1, (int)m.n_gt.size() - 1)];
+      if (n_ring > 0) {
+        Launch La = Lm;
+        La.n_items = n_ring;
+        launch_g2p_adj(La, src, StateRef{REF_RING, k + 1}, k == 0, k);
+      }
+      if (Lm.n_items > n_ring) {
+        Launch Lb = Lm;
+        Lb.item_offset += n_ring;
+        Lb.n_items -= n_ring;
+        launch_g2p_adj(Lb, src, StateRef{REF_REVEND, 0}, k == 0, k);
+      }
+    }
+    launch_grid_adj(L, k);
+    for (auto& m : mats) launch_p2g_adj(mat_launch(L, m, k), src, k == 0, k);
+  }
+  launch_rev_end(L, agrad, n_tot, a_max);
+}
+
+}  // namespace
+
+void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in, int a_max, float* rew,
+                     bool per_env) {
+  if (g.n_envs == 0) return;
+  if (!per_env) {
+    Launch L = group_launch(g, st);
+    launch_step_begin(L, act_in, a_max, record);
+    bin_envs(L, 0, g.P, g.cell_bits, g.key_bits, g.sort);
+    substeps_forward(g, L, g.mats, g.S_max);
+    launch_reward_end(L, rew, record);
+    return;
+  }
+  // baseline path: every stage launched once per environment
+  for (int e = 0; e < g.n_envs; ++e) {
+    Launch L = env_launch(g, e, st);
+    const int S = g.spec[e].substeps;
+    std::vector<MatGroup> one{{g.spec[e].material, g.env_item0[e], std::vector<int>(S + 1, g.env_nitems[e])}};
+    one[0].n_gt[S] = 0;
+    launch_step_begin(L, act_in, a_max, record);
+    bin_envs(L, g.desc[e].poff, g.spec[e].n_particles, g.cell_bits, g.cell_bits, g.sort);
+    substeps_forward(g, L, one, S);
+    launch_reward_end(L, rew, record);
+  }
+}
+
+void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env) {
+  if (g.n_envs == 0) return;
+  if (!per_env) {
+    reverse_step(group_launch(g, st), g.mats, g.S_max, rbar, agrad, n_tot, a_max);
+    return;
+  }
+  for (int e = 0; e < g.n_envs; ++e) {
+    const int S = g.spec[e].substeps;
+    std::vector<MatGroup> one{{g.spec[e].material, g.env_item0[e], std::vector<int>(S + 1, g.env_nitems[e])}};
+    one[0].n_gt[S] = 0;
+    reverse_step(env_launch(g, e, st), one, S, rbar, agrad, n_tot, a_max);
+  }
+}
+
+}  // namespace mpm

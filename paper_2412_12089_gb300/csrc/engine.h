@@ -1,0 +1,80 @@
+// engine.h -- internal step machinery shared by the batch context and the server.
+//
+// A Group is a set of environments advanced together: every stage of a control step is one
+// launch (one per material present) over all of the group's particle work items.  The
+// batch context (runtime.cu) owns one group; the server (server.cu) keeps one group for
+// environments running forward and one for environments running their reverse pass.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "kernels.h"
+#include "mpm.h"
+#include "mpm_types.h"
+
+namespace mpm {
+
+constexpr int kChunk = 256;  // particles per work item (CTA)
+
+const char* check_spec(const mpm_env_spec& s);
+
+// Byte offsets of one environment's buffers inside one allocation.
+struct EnvLayout {
+  int n_slots = 2;
+  bool tape = false;
+  bool own = false;  // accumulators, counters and horizon arrays live in the allocation
+  int T = 0;         // horizon arrays (own only)
+  long long n_pad = 0;
+  size_t slots = 0, ring = 0, adj = 0, perm = 0, grid = 0, tile = 0, pose = 0, act = 0;
+  size_t acc = 0, ctr = 0, act_env = 0, rew_env = 0, rbar_env = 0, agrad_env = 0, xout = 0;
+  size_t total = 0;
+};
+
+EnvLayout env_layout(const mpm_env_spec& s, int n_slots, bool tape, bool own, int T);
+// Parameters and buffer addresses of one environment; acc/ctr are taken from the layout when
+// it owns them, else from the given pointers.
+void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base, float* acc, EnvCtr* ctr);
+
+struct MatGroup {
+  int material;
+  int item0;               // first item of the material in the group's item list
+  std::vector<int> n_gt;   // [k] = items of the material whose env runs more than k substeps
+};
+
+struct Group {
+  std::vector<EnvDesc> desc;
+  std::vector<mpm_env_spec> spec;
+  int n_envs = 0, S_max = 1, A_max = 1, cell_bits = 0, key_bits = 0;
+  long long P = 0, tiles = 0;
+  std::vector<WorkItem> items, items_env;
+  std::vector<MatGroup> mats;
+  std::vector<int> env_item0, env_nitems;
+  EnvDesc* d_desc = nullptr;
+  size_t desc_cap = 0;
+  WorkItem* d_items = nullptr;
+  WorkItem* d_items_env = nullptr;
+  size_t items_cap = 0;
+  uint2* active = nullptr;
+  int* active_n = nullptr;
+  long long active_cap = 0;
+  SortScratch sort{};
+  long long hist_cap = 0;
+  void release();
+};
+
+// (Re)build the group's work lists and device scratch for these environments (their
+// descriptors' key_env and poff are assigned here).  Keeps scratch that is large enough.
+cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::vector<mpm_env_spec>& specs);
+
+Launch group_launch(const Group& g, cudaStream_t st);
+Launch env_launch(const Group& g, int e, cudaStream_t st);
+
+// One forward control step of every environment of the group (batched launches, or one
+// launch per stage per environment when per_env).
+void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in, int a_max, float* rew,
+                     bool per_env);
+// One reverse control step of every environment (step index from the device counters).
+void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env);
+
+}  // namespace mpm

@@ -614,7 +614,7 @@ __global__ void k_step_begin(const EnvDesc* __restrict__ envs, int env0, int n_e
   EnvCtr* c = e.ctr;
   int live = c->live;
   c->next = record ? live + 1 : (live == 0 ? 1 : 0);
-  const float* a = act_in + (long long)ei * a_max;
+  const float* a = e.act_env ? e.act_env + (long long)c->t * e.A : act_in + (long long)ei * a_max;
   for (int j = 0; j < e.A; ++j) e.act[(long long)live * e.A + j] = a[j];
   const float h = e.S * e.dt;
   float u[4] = {0.f, 0.f, 0.f, 0.f};
@@ -700,7 +700,11 @@ __global__ void __launch_bounds__(256) k_reward_end(const EnvDesc* __restrict__ 
       }
       r = stats[2] + e.rparam[1] * (stats[0] - e.rparam[0]) - e.rparam[2] * aa;
     }
-    if (reward_out) reward_out[ei] = r;
+    if (e.rew_env)
+      e.rew_env[cp->t] = r;
+    else if (reward_out)
+      reward_out[ei] = r;
+    cp->t += 1;
     cp->live = next;
     if (!record) cp->base = next;
   }
@@ -1201,7 +1205,7 @@ __global__ void __launch_bounds__(256) k_reward_adj(const EnvDesc* __restrict__ 
   const int ei = env0 + blockIdx.x;
   const EnvDesc& e = envs[ei];
   const EnvCtr c = *e.ctr;
-  const float rb = rbar ? rbar[(long long)c.rev * n_tot + ei] : 0.0f;
+  const float rb = e.rbar_env ? e.rbar_env[c.rev] : (rbar ? rbar[(long long)c.rev * n_tot + ei] : 0.0f);
   if (rb == 0.0f || e.reward_kind == 0) return;
   const int slot = c.base + c.rev;
   const float* b = e.slots + (long long)(slot + 1) * e.block;
@@ -1275,8 +1279,16 @@ __global__ void k_rev_end(const EnvDesc* __restrict__ envs, int env0, int n_env,
     ub[i] = h * e.acc[ACC_QB + i] + e.acc[ACC_KQKB + i] + e.acc[ACC_UB + i];
     e.acc[ACC_QB + i] += e.acc[ACC_QKB + i];
   }
-  float* out = act_grad + ((long long)c->rev * n_tot + ei) * a_max;
-  for (int j = 0; j < a_max; ++j) {
+  float* out;
+  int width;
+  if (e.agrad_env) {
+    out = e.agrad_env + (long long)c->rev * e.A;
+    width = e.A;
+  } else {
+    out = act_grad + ((long long)c->rev * n_tot + ei) * a_max;
+    width = a_max;
+  }
+  for (int j = 0; j < width; ++j) {
     float g = 0.f;
     if (j < e.A) {
       g = e.acc[ACC_ACT + j];

@@ -29,7 +29,8 @@ struct EnvCtr {
   int rev;    // reverse pass: index t of the step being reversed
   int par;    // reverse pass: adj[par] holds the running adjoint
   int status; // status bits (1 domain, 2 NaN, 4 inverted)
-  int pad[2];
+  int t;      // control steps taken since the state was set
+  int pad;
 };
 
 // Accumulator layout (floats) inside EnvDesc::acc.
@@ -72,6 +73,12 @@ struct EnvDesc {
   float* act;
   float* acc;
   EnvCtr* ctr;
+  // Optional per-environment horizon arrays (a served request carries its whole rollout on
+  // the device); NULL = the batch-wide buffers passed to the launch.
+  const float* act_env;   // [T][A] actions
+  float* rew_env;         // [T] rewards
+  const float* rbar_env;  // [T] reward adjoints
+  float* agrad_env;       // [T][A] action gradients
   long long poff;     // offset of this env's particles in the batch's global index space
   unsigned key_env;   // environment index placed in the high bits of the binning key
   int pad_;

@@ -291,3 +291,70 @@ def mpm_kernel_time(ctx, all_classes=False):
 
 def mpm_last_active_tiles(ctx):
     return lib().mpm_last_active_tiles(ctx)
+
+
+# ----------------------------------------------------------------------------- serving
+
+def mpm_server_create(mem_fraction=0.8, max_resident=64, device=0, chunk=0):
+    opt = MpmServerOptions(mem_fraction, max_resident, device, chunk)
+    h = _P()
+    code = lib().mpm_server_create(ct.byref(opt), ct.byref(h))
+    if code != MPM_OK:
+        raise MpmError(code, "mpm_server_create")
+    return h
+
+
+def mpm_server_destroy(srv):
+    lib().mpm_server_destroy(srv)
+
+
+def mpm_submit(srv, spec, init, actions, horizon, want_grad=False, reward_adj=None):
+    """Submit one rollout request (host arrays are copied before this returns)."""
+    x = np.ascontiguousarray(init.x, np.float32)
+    v = np.ascontiguousarray(init.v, np.float32)
+    C = np.ascontiguousarray(init.C, np.float32)
+    F = np.ascontiguousarray(init.F, np.float32)
+    g = np.ascontiguousarray(init.group, np.int32) if init.group is not None else None
+    a = np.ascontiguousarray(actions, np.float32).reshape(horizon, -1) if actions is not None else None
+    rb = np.ascontiguousarray(reward_adj, np.float32) if reward_adj is not None else None
+    req = MpmRequest()
+    req.spec = to_c_spec(spec)
+    req.x, req.v, req.C, req.F = x.ctypes.data, v.ctypes.data, C.ctypes.data, F.ctypes.data
+    req.group = g.ctypes.data if g is not None else None
+    req.horizon = horizon
+    req.actions = a.ctypes.data if a is not None else None
+    req.want_grad = 1 if want_grad else 0
+    req.reward_adj = rb.ctypes.data if rb is not None else None
+    t = ct.c_uint64()
+    check(lib().mpm_submit(srv, ct.byref(req), ct.byref(t)), srv=srv)
+    return t.value
+
+
+def _result(res):
+    out = {"status": res.status, "horizon": res.horizon, "submit_ms": res.submit_ms, "admit_ms": res.admit_ms,
+           "finish_ms": res.finish_ms}
+    T, A, n = res.horizon, res.action_dim, res.n_particles
+    out["rewards"] = np.ctypeslib.as_array(res.rewards, (T,)).copy() if res.rewards else None
+    out["action_grad"] = np.ctypeslib.as_array(res.action_grad, (T, A)).copy() if (res.action_grad and A) else None
+    out["x_final"] = np.ctypeslib.as_array(res.x_final, (n, 3)).copy() if res.x_final else None
+    return out
+
+
+def mpm_poll(srv, ticket):
+    """None while the request runs, else its result dict."""
+    res = MpmResult()
+    code = lib().mpm_poll(srv, ticket, ct.byref(res))
+    if code == MPM_NOT_READY:
+        return None
+    check(code, srv=srv)
+    return _result(res)
+
+
+def mpm_wait(srv, ticket, timeout_ms=60000.0):
+    res = MpmResult()
+    check(lib().mpm_wait(srv, ticket, timeout_ms, ct.byref(res)), srv=srv)
+    return _result(res)
+
+
+def mpm_release(srv, ticket):
+    return check(lib().mpm_release(srv, ticket), srv=srv)
