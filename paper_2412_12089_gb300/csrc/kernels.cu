@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(256) k_reward_end(const EnvDesc* __restrict__ 
 template <int MAT>
 __global__ void __launch_bounds__(kBlock, 4) k_g2p_adj(const EnvDesc* __restrict__ envs,
                                                        const WorkItem* __restrict__ items, int item_off, StateRef src,
-                                                       StateRef nxt, int use_perm) {
+                                                       StateRef nxt, int use_perm, int k) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   __shared__ int sred[6];
@@ -753,7 +753,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_g2p_adj(const EnvDesc* __restrict
   m.kind = MAT;  // compile-time material: the other laws' code is folded away
   const float Dinv = 4.0f * G * G, dt = e.dt, dx = e.dx;
   const int nxy = bx.nx * bx.ny;
-  const float vref[3] = {e.acc[ACC_VREF], e.acc[ACC_VREF + 1], e.acc[ACC_VREF + 2]};
+  // reference = mean of v-bar + dt x-bar over the env's particles at this substep's end
+  // (summed by P2G^T of the next substep, or by k_adj_ref for the step's last substep)
+  const float inv_n = 1.0f / (float)e.n;
+  const float* vs = e.acc + ACC_VSUM + 4 * (k & 1);
+  const float vref[3] = {vs[0] * inv_n, vs[1] * inv_n, vs[2] * inv_n};
+  if (it.start == 0 && threadIdx.x < 4) e.acc[ACC_VSUM + 4 * ((k + 1) & 1) + threadIdx.x] = 0.0f;
 #pragma unroll 1
   for (int p = 0; p < kPPT; ++p) {
     // every lane runs the loop (warp collectives); lanes past the item's end carry zeros
@@ -995,7 +1000,9 @@ __global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ en
     const int TG = e.G >> 2;
     const int tz = at.y / (TG * TG), ty = (at.y / TG) % TG, tx = at.y % TG;
     float qb[4] = {0.f, 0.f, 0.f, 0.f}, ub[4] = {0.f, 0.f, 0.f, 0.f};
-    const float vref[3] = {e.acc[ACC_VREF], e.acc[ACC_VREF + 1], e.acc[ACC_VREF + 2]};
+    const float inv_n = 1.0f / (float)e.n;
+    const float* vs = e.acc + ACC_VSUM + 4 * (k & 1);
+    const float vref[3] = {vs[0] * inv_n, vs[1] * inv_n, vs[2] * inv_n};
     const float inv_pm = 1.0f / e.p_mass;
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
@@ -1061,8 +1068,10 @@ __global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ en
 // ------------------------------------------------------------------ adjoint: P2G^T
 
 template <int MAT>
-__global__ void __launch_bounds__(kBlock, 4) k_p2g_adj(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
-                                                    int item_off, StateRef src, int use_perm) {
+__global__ void __launch_bounds__(kBlock, 4) k_p2g_adj(const EnvDesc* __restrict__ envs,
+                                                       const WorkItem* __restrict__ items, int item_off, StateRef src,
+                                                       int use_perm, int k) {
+  __shared__ float vsum_s[3];
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   const WorkItem it = items[item_off + blockIdx.x];
@@ -1078,6 +1087,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_p2g_adj(const EnvDesc* __restrict
   m.kind = MAT;  // compile-time material: the other laws' code is folded away
   const float Dinv = 4.0f * G * G, dx = e.dx, pm = e.p_mass;
   const float stress_k = -e.dt * e.p_vol * Dinv;
+  if (threadIdx.x < 3) vsum_s[threadIdx.x] = 0.0f;
+  __syncthreads();
+  float vsum[3] = {0.f, 0.f, 0.f};
 #pragma unroll 1
   for (int p = 0; p < kPPT; ++p) {
     const int i = it.start + threadIdx.x + p * kBlock;
@@ -1152,6 +1164,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_p2g_adj(const EnvDesc* __restrict
       const float xp = adj[a * np + i];
       adj_out[a * np + o] = xp + xbn[a];
       adj_out[(3 + a) * np + o] = vbn[a];
+      vsum[a] += vbn[a] + e.dt * (xp + xbn[a]);
     }
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -1163,6 +1176,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_p2g_adj(const EnvDesc* __restrict
       if (g >= 0 && g < e.n_groups) atomicAdd(e.acc + ACC_ACT + e.n_coll_act + g, agb);
     }
   }
+  // per-env sum of the produced adjoint (v-bar + dt x-bar): the reference of substep k-1
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float v = vsum[a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&vsum_s[a], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) atomicAdd(e.acc + ACC_VSUM + 4 * ((k + 1) & 1) + threadIdx.x, vsum_s[threadIdx.x]);
 }
 
 // ------------------------------------------------------------------ reverse-step bookkeeping
@@ -1240,9 +1263,9 @@ __global__ void __launch_bounds__(256) k_reward_adj(const EnvDesc* __restrict__ 
   }
 }
 
-// One CTA per env: V_ref = mean over the env's particles of the adjoint v-bar + dt x-bar of
-// the step's end state (any fixed value is exact; a representative one keeps the shifted
-// adjoint small).
+// One CTA per env: sum over the env's particles of the adjoint v-bar + dt x-bar of the step's
+// end state, the reference of the step's last substep (any value is exact; the mean of the
+// current adjoint keeps the shifted adjoint small).
 __global__ void __launch_bounds__(256) k_adj_ref(const EnvDesc* __restrict__ envs, int env0) {
   __shared__ float sh[32];
   const int ei = env0 + blockIdx.x;
@@ -1260,10 +1283,10 @@ __global__ void __launch_bounds__(256) k_adj_ref(const EnvDesc* __restrict__ env
   s1 = block_sum(s1, sh);
   s2 = block_sum(s2, sh);
   if (threadIdx.x == 0) {
-    const float inv = 1.0f / (float)e.n;
-    e.acc[ACC_VREF] = s0 * inv;
-    e.acc[ACC_VREF + 1] = s1 * inv;
-    e.acc[ACC_VREF + 2] = s2 * inv;
+    float* vs = e.acc + ACC_VSUM + 4 * ((e.S - 1) & 1);
+    vs[0] = s0;
+    vs[1] = s1;
+    vs[2] = s2;
   }
 }
 
@@ -1472,10 +1495,10 @@ void launch_g2p_adj(const Launch& L, StateRef src, StateRef nxt, bool use_perm, 
   if (L.n_items == 0) return;
   Timed tm_(KC_G2P_ADJ, L.stream);
   switch (L.material) {
-    case MAT_NEOHOOKEAN: k_g2p_adj<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0); break;
-    case MAT_VONMISES: k_g2p_adj<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0); break;
-    case MAT_FLUID: k_g2p_adj<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0); break;
-    default: k_g2p_adj<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0); break;
+    case MAT_NEOHOOKEAN: k_g2p_adj<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0, k); break;
+    case MAT_VONMISES: k_g2p_adj<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0, k); break;
+    case MAT_FLUID: k_g2p_adj<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0, k); break;
+    default: k_g2p_adj<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0, k); break;
   }
 }
 
@@ -1489,10 +1512,10 @@ void launch_p2g_adj(const Launch& L, StateRef src, bool use_perm, int k) {
   if (L.n_items == 0) return;
   Timed tm_(KC_P2G_ADJ, L.stream);
   switch (L.material) {
-    case MAT_NEOHOOKEAN: k_p2g_adj<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0); break;
-    case MAT_VONMISES: k_p2g_adj<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0); break;
-    case MAT_FLUID: k_p2g_adj<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0); break;
-    default: k_p2g_adj<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0); break;
+    case MAT_NEOHOOKEAN: k_p2g_adj<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k); break;
+    case MAT_VONMISES: k_p2g_adj<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k); break;
+    case MAT_FLUID: k_p2g_adj<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k); break;
+    default: k_p2g_adj<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k); break;
   }
 }
 

@@ -41,9 +41,10 @@ enum {
   ACC_KQKB = 12,  // sum over substeps of k dt dL/dq_k (4)
   ACC_UB = 16,    // dL/du through the body velocity (4)
   ACC_RSTAT = 20, // reward statistics of the running step (4)
-  ACC_VREF = 24,  // reverse step: reference particle-velocity adjoint subtracted before the
-                  // G2P^T scatter and restored node by node (3 + pad)
-  ACC_ACT = 28,   // dL/d(action) accumulated in the reverse step (A)
+  ACC_VSUM = 24,  // reverse pass: two sums (by substep parity) over the env's particles of
+                  // the particle-velocity adjoint v-bar + dt x-bar; their mean is the reference
+                  // subtracted before the G2P^T scatter and restored node by node (2 x 4)
+  ACC_ACT = 32,   // dL/d(action) accumulated in the reverse step (A)
 };
 
 struct EnvDesc {
