@@ -189,6 +189,26 @@ mpm_status mpm_check_status(mpm_ctx* ctx, int32_t* flags);
  */
 mpm_status mpm_bin(const float* x, int32_t n, int32_t grid_res, uint32_t* keys, uint32_t* perm, void* stream);
 
+/*
+ * mpm_bin without any allocation (no counterpart in the paper: a systems entry point).
+ * Same arguments, keys and perm as mpm_bin, bit for bit, but the sort scratch is a fixed
+ * file-scope device array sized for mpm_bin_static_max() = 262144 particles (4 MiB + 64 KiB),
+ * so it calls no cudaMalloc, cudaFree or allocating library routine.  It is for callers that
+ * cannot allocate: the serving loop, where a per-call cudaFree would synchronise the whole
+ * device and stall the forward and reverse streams running other requests, and callers that
+ * have committed the device's memory to resident environments (the admission budget), where
+ * a cudaMalloc can fail in the middle of a run.
+ *   n > mpm_bin_static_max(): MPM_ERR_INVALID_ARG, nothing launched.  Other argument errors
+ *   as mpm_bin.  The work is enqueued on `stream` and the call returns without waiting.
+ *   The first call on a device, with that device current, looks up the array's device
+ *   address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Every call shares the one array: calls whose work overlaps on the GPU (other streams,
+ *   unordered threads) race and give wrong keys and perm.  Nothing in the array needs to
+ *   start at zero, so stale contents of an earlier call do not matter.
+ */
+mpm_status mpm_bin_static(const float* x, int32_t n, int32_t grid_res, uint32_t* keys, uint32_t* perm, void* stream);
+int32_t mpm_bin_static_max(void);
+
 /* ------------------------------------------------------------------ instrumentation */
 
 /* Kernel classes for mpm_time_kernel. */

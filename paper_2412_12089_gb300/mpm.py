@@ -96,6 +96,8 @@ def lib():
         "mpm_reset_tape": (i32, [_P]),
         "mpm_check_status": (i32, [_P, _P]),
         "mpm_bin": (i32, [_P, i32, i32, _P, _P, _P]),
+        "mpm_bin_static": (i32, [_P, i32, i32, _P, _P, _P]),
+        "mpm_bin_static_max": (i32, []),
         "mpm_kernel_launches": (i64, [_P]),
         "mpm_time_kernel": (i32, [_P, i32]),
         "mpm_kernel_time": (i32, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
@@ -254,6 +256,17 @@ def mpm_bin(x, n, grid_res, keys, perm, stream=None):
     if code != MPM_OK:
         raise MpmError(code, "mpm_bin")
     return code
+
+
+def mpm_bin_static(x, n, grid_res, keys, perm, stream=None):
+    code = lib().mpm_bin_static(ptr(x), n, grid_res, ptr(keys), ptr(perm), stream_ptr(stream))
+    if code != MPM_OK:
+        raise MpmError(code, "mpm_bin_static")
+    return code
+
+
+def mpm_bin_static_max():
+    return lib().mpm_bin_static_max()
 
 
 def mpm_tape_length(ctx):
