@@ -148,15 +148,15 @@ __device__ __forceinline__ void zero_box(SBox& sb, int vol, int ncomp) {
     for (int c = 0; c < ncomp; ++c) sb.v[c * kBoxNodes + i] = 0.f;
 }
 
-// Flush a shared box into a dense grid with float4 atomics (nodes whose first, or any for
-// adjoints, component is non-zero), marking tiles if requested.
-template <bool kMark, bool kAnyNonzero>
-__device__ __forceinline__ void flush_box(const EnvDesc& e, int env, const Box& bx, const SBox& sb, float4* grid,
-                                          uint2* active, int* active_n) {
+// Flush a shared box of kNc components into a dense grid with float4 atomics (nodes whose
+// first, or any for adjoints, component is non-zero), marking tiles if requested.
+template <bool kMark, bool kAnyNonzero, int kNc>
+__device__ __forceinline__ void flush_box(const EnvDesc& e, int env, const Box& bx, const float* sv, int stride,
+                                          float4* grid, uint2* active, int* active_n) {
   int vol = bx.nx * bx.ny * bx.nz;
   int G = e.G;
   for (int i = threadIdx.x; i < vol; i += blockDim.x) {
-    float4 val = make_float4(sb.v[i], sb.v[kBoxNodes + i], sb.v[2 * kBoxNodes + i], sb.v[3 * kBoxNodes + i]);
+    float4 val = make_float4(sv[i], sv[stride + i], sv[2 * stride + i], kNc == 4 ? sv[3 * stride + i] : 0.0f);
     bool nz = kAnyNonzero ? (val.x != 0.0f || val.y != 0.0f || val.z != 0.0f || val.w != 0.0f) : (val.x != 0.0f);
     if (!nz) continue;
     int ix = bx.lx + i % bx.nx;
@@ -191,62 +191,167 @@ __device__ __forceinline__ void rot_axis(int rot, const float* w, const float* d
   }
 }
 
-// Runs of equal keys among the lanes of a warp.  Binned particles sharing a cell base sit in
-// adjacent lanes and update the same 27 nodes, so their contributions are summed inside the
-// run (warp shuffles) and only the run's first lane issues the shared-memory atomics.
-struct Runs {
-  int span;       // lanes after this one in its run
-  int maxspan;    // longest span in the warp (shuffle steps: ceil(log2(maxspan + 1)))
-  int head_lane;  // first lane of this lane's run
-  bool head;
-};
-
-__device__ __forceinline__ Runs warp_runs(unsigned key) {
-  const int lane = threadIdx.x & 31;
-  const unsigned prev = __shfl_up_sync(0xffffffffu, key, 1);
-  const bool head = lane == 0 || key != prev;
-  const unsigned heads = __ballot_sync(0xffffffffu, head);
-  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);  // lanes 0..lane
-  const unsigned after = heads & ~upto;                                   // heads past lane
-  Runs r;
-  r.head = head;
-  r.head_lane = 31 - __clz(heads & upto);
-  r.span = (after ? (__ffs(after) - 1) : 32) - lane - 1;
-  r.maxspan = __reduce_max_sync(0xffffffffu, r.span);
-  return r;
-}
-
-// Sum of a, b, c (and d) over the lane and the following r.span lanes of its run; exact for
-// the run's head (a lane's partial sums past the head are not used).
-__device__ __forceinline__ void run_sum4(float& a, float& b, float& c, float& d, const Runs& r) {
-  for (int st = 1; st <= r.maxspan; st <<= 1) {
-    const float ta = __shfl_down_sync(0xffffffffu, a, st);
-    const float tb = __shfl_down_sync(0xffffffffu, b, st);
-    const float tc = __shfl_down_sync(0xffffffffu, c, st);
-    const float td = __shfl_down_sync(0xffffffffu, d, st);
-    if (st <= r.span) {
-      a += ta;
-      b += tb;
-      c += tc;
-      d += td;
-    }
-  }
-}
-
 __device__ __forceinline__ unsigned cell_pack(int b0, int b1, int b2) {
   return (unsigned)b0 | ((unsigned)b1 << 10) | ((unsigned)b2 << 20);
 }
 
+// ------------------------------------------------------------------ grouped scatter
+//
+// P2G and G2P^T both add, for every particle p and every node i of its stencil,
+//     w_ip (q_p + A_p r_ip)            (r_ip = x_i - x_p)
+// (and w_ip m_p for P2G's mass).  A CTA does it for its chunk of binned particles group by
+// group, a group being a run of consecutive particles with the same cell base (a whole cell
+// right after binning).  (1) Every particle writes a record to shared memory: q, its offsets
+// g = f dx from the base node, the weights of the three axes and A.  (2) Work units (group,
+// y offset b, z offset c) sum the group's contributions to the three nodes base + (0..2, b, c)
+// in registers and add them into a shared-memory box (no two units of a group touch the same
+// node), or, when the chunk's box is too large, straight into the grid with float4 atomics.
+// (3) The box is flushed to the grid with float4 atomics.
+
+constexpr int kScBox = 512;  // nodes of the shared box (a 256-particle chunk spans 150-400)
+constexpr int kRec = 24;     // floats per particle record
+
+struct ScatterShared {
+  float4 rec[kBlock * kPPT * kRec / 4];      // particle records in chunk order (24 KB)
+  float box[4 * kScBox];                     // box nodes, component-major (8 KB)
+  unsigned key[kBlock * kPPT];               // packed cell base per particle (~0u: none)
+  unsigned short gstart[kBlock * kPPT + 1];  // first particle of each group, then the end
+  int seg[kPPT * kBlock / 32];               // group heads per (particle slot, warp)
+};
+
+// Record layout: (q0 q1 q2 gx) (gy gz wx0 wx1) (wx2 wy0 wy1 wy2) (wz0 wz1 wz2 A00)
+// (A01 A02 A10 A11) (A12 A20 A21 A22).
+__device__ __forceinline__ void write_record(float4* r, const float* q, const float* g, const float* wx,
+                                             const float* wy, const float* wz, const float* A) {
+  r[0] = make_float4(q[0], q[1], q[2], g[0]);
+  r[1] = make_float4(g[1], g[2], wx[0], wx[1]);
+  r[2] = make_float4(wx[2], wy[0], wy[1], wy[2]);
+  r[3] = make_float4(wz[0], wz[1], wz[2], A[0]);
+  r[4] = make_float4(A[1], A[2], A[3], A[4]);
+  r[5] = make_float4(A[5], A[6], A[7], A[8]);
+}
+
+// Steps (2) and (3), after make_box (whose barriers publish the records and keys).
+// kMass: P2G (mass component m w, tiles marked active); else G2P^T (three components).
+template <bool kMass>
+__device__ __forceinline__ void scatter_groups(ScatterShared& sh, const EnvDesc& e, int env, int count,
+                                               const bool* valid, const int (*base)[3], const int* sred,
+                                               const Box& bx, float pm, float4* grid, uint2* active,
+                                               int* active_n) {
+  const bool fits = sred[3] >= 0 && bx.nx * bx.ny * bx.nz <= kScBox;
+  if (fits) {
+    const int vol = bx.nx * bx.ny * bx.nz;
+    for (int q = threadIdx.x; q < vol; q += kBlock) {
+      sh.box[q] = 0.f;
+      sh.box[kScBox + q] = 0.f;
+      sh.box[2 * kScBox + q] = 0.f;
+      if (kMass) sh.box[3 * kScBox + q] = 0.f;
+    }
+  } else if (kMass) {
+#pragma unroll
+    for (int p = 0; p < kPPT; ++p)
+      if (valid[p])
+        for (int cz = 0; cz < 3; cz += 2)
+          for (int cy = 0; cy < 3; cy += 2)
+            for (int cx = 0; cx < 3; cx += 2)
+              mark_tile(e, env, base[p][0] + cx, base[p][1] + cy, base[p][2] + cz, active, active_n);
+  }
+  // groups: runs of equal keys in chunk order, numbered by a scan over (slot, warp) segments
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned heads[kPPT];
+#pragma unroll
+  for (int p = 0; p < kPPT; ++p) {
+    const int l = threadIdx.x + p * kBlock;
+    const bool h = valid[p] && (l == 0 || sh.key[l - 1] != sh.key[l]);
+    heads[p] = __ballot_sync(0xffffffffu, h);
+    if (lane == 0) sh.seg[p * (kBlock / 32) + warp] = __popc(heads[p]);
+  }
+  __syncthreads();
+  int ngrp = 0;
+#pragma unroll
+  for (int p = 0; p < kPPT; ++p) {
+    const int sidx = p * (kBlock / 32) + warp;
+    int off = 0;
+    for (int q = 0; q < sidx; ++q) off += sh.seg[q];
+    if (heads[p] >> lane & 1u)
+      sh.gstart[off + __popc(heads[p] & ((1u << lane) - 1u))] = (unsigned short)(threadIdx.x + p * kBlock);
+  }
+  for (int q = 0; q < kPPT * (kBlock / 32); ++q) ngrp += sh.seg[q];
+  if (threadIdx.x == 0) sh.gstart[ngrp] = (unsigned short)count;
+  __syncthreads();
+  const float dx = e.dx;
+  const int nunits = ngrp * 9;
+  for (int u = threadIdx.x; u < nunits; u += kBlock) {
+    const int g = u / 9, bc = u - 9 * g;
+    const int ob = bc % 3, oc = bc / 3;
+    const int q0 = sh.gstart[g], q1 = sh.gstart[g + 1];
+    const unsigned key = sh.key[q0];
+    const int cx = (int)(key & 1023u), cy = (int)((key >> 10) & 1023u), cz = (int)(key >> 20);
+    const float bdx = (float)ob * dx, cdx = (float)oc * dx;
+    float am[3] = {0.f, 0.f, 0.f};
+    float ap[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    for (int q = q0; q < q1; ++q) {
+      const float4* r = sh.rec + q * (kRec / 4);
+      const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
+      const float wyb = ob == 0 ? r2.y : (ob == 1 ? r2.z : r2.w);
+      const float wzc = oc == 0 ? r3.x : (oc == 1 ? r3.y : r3.z);
+      const float ry = bdx - r1.x, rz = cdx - r1.y;
+      const float wyz = wyb * wzc;
+      // A = [r3.w r4.x r4.y; r4.z r4.w r5.x; r5.y r5.z r5.w]
+      const float t0 = r0.x + r4.x * ry + r4.y * rz;
+      const float t1 = r0.y + r4.w * ry + r5.x * rz;
+      const float t2 = r0.z + r5.z * ry + r5.w * rz;
+      const float wxa[3] = {r1.z, r1.w, r2.x};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float rx = (float)a * dx - r0.w;
+        const float wt = wxa[a] * wyz;
+        if (kMass) am[a] += wt;
+        ap[a][0] += wt * (t0 + r3.w * rx);
+        ap[a][1] += wt * (t1 + r4.z * rx);
+        ap[a][2] += wt * (t2 + r5.y * rx);
+      }
+    }
+    if (fits) {
+      const int row = ((cz + oc - bx.lz) * bx.ny + (cy + ob - bx.ly)) * bx.nx + (cx - bx.lx);
+      // components: (m, p) for P2G, (v-bar) for G2P^T
+      constexpr int o = kMass ? 1 : 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (kMass) atomicAdd(&sh.box[row + a], am[a] * pm);
+        atomicAdd(&sh.box[o * kScBox + row + a], ap[a][0]);
+        atomicAdd(&sh.box[(o + 1) * kScBox + row + a], ap[a][1]);
+        atomicAdd(&sh.box[(o + 2) * kScBox + row + a], ap[a][2]);
+      }
+    } else {
+      float4* gp = grid + ((long long)(cz + oc) * e.G + (cy + ob)) * e.G + cx;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        atomicAdd(gp + a, kMass ? make_float4(am[a] * pm, ap[a][0], ap[a][1], ap[a][2])
+                                : make_float4(ap[a][0], ap[a][1], ap[a][2], 0.f));
+    }
+  }
+  if (fits) {
+    __syncthreads();
+    if (kMass)
+      flush_box<true, false, 4>(e, env, bx, sh.box, kScBox, grid, active, active_n);
+    else
+      flush_box<false, true, 3>(e, env, bx, sh.box, kScBox, grid, nullptr, nullptr);
+  }
+}
+
 // ------------------------------------------------------------------ P2G
+//
+// Grouped scatter of mass and APIC momentum (q = m v, A = m C - dt V D^-1 tau).
 
 template <int MAT>
-__global__ void __launch_bounds__(kBlock) k_p2g(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
-                                                int item_off, StateRef src, int use_perm, int k, int rev,
-                                                uint2* active, int* active_n) {
+__global__ void __launch_bounds__(kBlock, 6) k_p2g(const EnvDesc* __restrict__ envs,
+                                                   const WorkItem* __restrict__ items, int item_off, StateRef src,
+                                                   int use_perm, int k, int rev, uint2* active, int* active_n) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   __shared__ int sred[6];
-  __shared__ SBox sb;
+  __shared__ ScatterShared sh;
   const WorkItem it = items[item_off + blockIdx.x];
   load_env(envs, it.env, e, c);
   const float* b = ref_block(e, c, src);
@@ -254,122 +359,49 @@ __global__ void __launch_bounds__(kBlock) k_p2g(const EnvDesc* __restrict__ envs
   const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
   const long long np = e.n_pad;
   const float G = (float)e.G;
-  int base[kPPT][3];
-  bool valid[kPPT];
-  int jj[kPPT];
-  int oob = 0;
-#pragma unroll
-  for (int p = 0; p < kPPT; ++p) {
-    int i = it.start + threadIdx.x + p * kBlock;
-    valid[p] = i < it.start + it.count;
-    int j = valid[p] ? (perm ? (int)perm[i] : i) : 0;
-    jj[p] = j;
-    if (valid[p]) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) base[p][a] = cell_base(b[a * np + j], G, e.G, &oob);
-    }
-  }
-  Box bx = make_box(base, valid, sred);
-  if (bx.fits) {
-    zero_box(sb, bx.nx * bx.ny * bx.nz, 4);
-    __syncthreads();
-  }
   Mat m = env_mat(e);
   m.kind = MAT;  // compile-time material: the other laws' code is folded away
   const float Dinv = 4.0f * G * G;
   const float stress_k = -e.dt * e.p_vol * Dinv;
   const float pm = e.p_mass;
-  const int nxy = bx.nx * bx.ny;
   const float dx = e.dx;
-  // Every lane runs the loop (warp collectives); lanes past the item's end carry zeros in
-  // their own run, which issues no atomics.
-#pragma unroll 1
-  for (int p = 0; p < kPPT; ++p) {
-    const bool vp = valid[p];
-    const int j = jj[p];
-    float s[kComp];
-    if (vp) {
-      load_state(b, np, j, s);
-    } else {
+  int base[kPPT][3];
+  bool valid[kPPT];
+  int oob = 0;
 #pragma unroll
-      for (int q = 0; q < kComp; ++q) s[q] = 0.0f;
-      base[p][0] = bx.lx;
-      base[p][1] = bx.ly;
-      base[p][2] = bx.lz;
-    }
-    const int b0 = base[p][0], b1 = base[p][1], b2 = base[p][2];
-    const Runs run = warp_runs(vp ? cell_pack(b0, b1, b2) : 0xffffffffu);
-    const bool writer = run.head && vp;
-    int rot_x = run.head_lane % 3, rot_y = (run.head_lane / 3) % 3, rot_z = (run.head_lane / 9) % 3;
-    const unsigned meta = vp ? reinterpret_cast<const unsigned*>(b + kComp * np)[j] : 0u;
+  for (int p = 0; p < kPPT; ++p) {
+    const int l = threadIdx.x + p * kBlock;
+    valid[p] = l < it.count;
+    sh.key[l] = 0xffffffffu;
+    if (!valid[p]) continue;
+    const int i = it.start + l;
+    const int j = perm ? (int)perm[i] : i;
+    float s[kComp];
+    load_state(b, np, j, s);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) base[p][a] = cell_base(s[a], G, e.G, &oob);
+    sh.key[l] = cell_pack(base[p][0], base[p][1], base[p][2]);
+    const unsigned meta = reinterpret_cast<const unsigned*>(b + kComp * np)[j];
     const float a_g = MAT == MAT_MUSCLE ? group_act(e, sslot, meta) : 0.0f;
     float tau[9];
     kirchhoff(m, s + 15, s + 6, a_g, tau);
-    const float pmv = vp ? pm : 0.0f;
     float A[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) A[q] = pmv * s[6 + q] + (vp ? stress_k * tau[q] : 0.0f);
-    Axis3 ax, ay, az;
-    {
-      float w[3], dw[3];
-      const float f0 = vp ? __fmul_rn(s[0], G) - (float)b0 : 1.0f;
-      const float f1 = vp ? __fmul_rn(s[1], G) - (float)b1 : 1.0f;
-      const float f2 = vp ? __fmul_rn(s[2], G) - (float)b2 : 1.0f;
-      bspline(f0, w, dw);
-      rot_axis(rot_x, w, dw, f0, dx, ax);
-      bspline(f1, w, dw);
-      rot_axis(rot_y, w, dw, f1, dx, ay);
-      bspline(f2, w, dw);
-      rot_axis(rot_z, w, dw, f2, dx, az);
-    }
-    const float mv0 = pmv * s[3], mv1 = pmv * s[4], mv2 = pmv * s[5];
-    const int bi0 = bx.fits ? bx.idx(b0, b1, b2) : 0;
-#pragma unroll
-    for (int jz = 0; jz < 3; ++jz) {
-#pragma unroll
-      for (int jy = 0; jy < 3; ++jy) {
-        const float wyz = ay.w[jy] * az.w[jz];
-        const float ry = ay.r[jy], rz = az.r[jz];
-        const float t0 = mv0 + A[1] * ry + A[2] * rz;
-        const float t1 = mv1 + A[4] * ry + A[5] * rz;
-        const float t2 = mv2 + A[7] * ry + A[8] * rz;
-        const int row = bi0 + az.o[jz] * nxy + ay.o[jy] * bx.nx;
-#pragma unroll
-        for (int jx = 0; jx < 3; ++jx) {
-          const float wt = ax.w[jx] * wyz;
-          const float rx = ax.r[jx];
-          float a0 = wt * pmv;
-          float a1 = wt * (t0 + A[0] * rx);
-          float a2 = wt * (t1 + A[3] * rx);
-          float a3 = wt * (t2 + A[6] * rx);
-          run_sum4(a0, a1, a2, a3, run);
-          if (writer) {
-            if (bx.fits) {
-              const int bi = row + ax.o[jx];
-              atomicAdd(&sb.v[bi], a0);
-              atomicAdd(&sb.v[kBoxNodes + bi], a1);
-              atomicAdd(&sb.v[2 * kBoxNodes + bi], a2);
-              atomicAdd(&sb.v[3 * kBoxNodes + bi], a3);
-            } else {
-              const int ix = b0 + ax.o[jx], iy = b1 + ay.o[jy], iz = b2 + az.o[jz];
-              atomicAdd(e.grid_mp + ((long long)iz * e.G + iy) * e.G + ix, make_float4(a0, a1, a2, a3));
-            }
-          }
-        }
-      }
-    }
-    if (!bx.fits && vp) {
-      for (int cz = 0; cz < 3; cz += 2)
-        for (int cy = 0; cy < 3; cy += 2)
-          for (int cx = 0; cx < 3; cx += 2)
-            mark_tile(e, it.env, b0 + cx, b1 + cy, b2 + cz, active, active_n);
-    }
+    for (int q = 0; q < 9; ++q) A[q] = pm * s[6 + q] + stress_k * tau[q];
+    float wx[3], wy[3], wz[3], dw[3];
+    const float f0 = __fmul_rn(s[0], G) - (float)base[p][0];
+    const float f1 = __fmul_rn(s[1], G) - (float)base[p][1];
+    const float f2 = __fmul_rn(s[2], G) - (float)base[p][2];
+    bspline(f0, wx, dw);
+    bspline(f1, wy, dw);
+    bspline(f2, wz, dw);
+    const float mv[3] = {pm * s[3], pm * s[4], pm * s[5]};
+    const float g[3] = {f0 * dx, f1 * dx, f2 * dx};
+    write_record(sh.rec + l * (kRec / 4), mv, g, wx, wy, wz, A);
   }
   if (oob) atomicOr(&e.ctr->status, 1);
-  if (bx.fits) {
-    __syncthreads();
-    flush_box<true, false>(e, it.env, bx, sb, e.grid_mp, active, active_n);
-  }
+  const Box bx = make_box(base, valid, sred);
+  scatter_groups<true>(sh, e, it.env, it.count, valid, base, sred, bx, pm, e.grid_mp, active, active_n);
 }
 
 // ------------------------------------------------------------------ grid update
@@ -713,13 +745,13 @@ __global__ void __launch_bounds__(256) k_reward_end(const EnvDesc* __restrict__ 
 // ------------------------------------------------------------------ adjoint: G2P^T
 
 template <int MAT>
-__global__ void __launch_bounds__(kBlock, 4) k_g2p_adj(const EnvDesc* __restrict__ envs,
+__global__ void __launch_bounds__(kBlock, 5) k_g2p_adj(const EnvDesc* __restrict__ envs,
                                                        const WorkItem* __restrict__ items, int item_off, StateRef src,
                                                        StateRef nxt, int use_perm, int k) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   __shared__ int sred[6];
-  __shared__ SBox sb;
+  __shared__ ScatterShared sh;
   const WorkItem it = items[item_off + blockIdx.x];
   load_env(envs, it.env, e, c);
   const float* b = ref_block(e, c, src);
@@ -729,64 +761,48 @@ __global__ void __launch_bounds__(kBlock, 4) k_g2p_adj(const EnvDesc* __restrict
   const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
   const long long np = e.n_pad;
   const float G = (float)e.G;
-  int base[kPPT][3];
-  bool valid[kPPT];
-  int jj[kPPT];
-  int oob = 0;
-#pragma unroll
-  for (int p = 0; p < kPPT; ++p) {
-    int i = it.start + threadIdx.x + p * kBlock;
-    valid[p] = i < it.start + it.count;
-    int j = valid[p] ? (perm ? (int)perm[i] : i) : 0;
-    jj[p] = j;
-    if (valid[p]) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) base[p][a] = cell_base(b[a * np + j], G, e.G, &oob);
-    }
-  }
-  Box bx = make_box(base, valid, sred);
-  if (bx.fits) {
-    zero_box(sb, bx.nx * bx.ny * bx.nz, 3);
-    __syncthreads();
-  }
   Mat m = env_mat(e);
   m.kind = MAT;  // compile-time material: the other laws' code is folded away
   const float Dinv = 4.0f * G * G, dt = e.dt, dx = e.dx;
-  const int nxy = bx.nx * bx.ny;
   // reference = mean of v-bar + dt x-bar over the env's particles at this substep's end
   // (summed by P2G^T of the next substep, or by k_adj_ref for the step's last substep)
   const float inv_n = 1.0f / (float)e.n;
   const float* vs = e.acc + ACC_VSUM + 4 * (k & 1);
   const float vref[3] = {vs[0] * inv_n, vs[1] * inv_n, vs[2] * inv_n};
   if (it.start == 0 && threadIdx.x < 4) e.acc[ACC_VSUM + 4 * ((k + 1) & 1) + threadIdx.x] = 0.0f;
+  int base[kPPT][3];
+  bool valid[kPPT];
+  int oob = 0;
 #pragma unroll 1
   for (int p = 0; p < kPPT; ++p) {
-    // every lane runs the loop (warp collectives); lanes past the item's end carry zeros
-    const bool vp = valid[p];
-    const int i = vp ? it.start + threadIdx.x + p * kBlock : it.start;
-    const int j = jj[p];
-    if (!vp) {
-      base[p][0] = bx.lx;
-      base[p][1] = bx.ly;
-      base[p][2] = bx.lz;
-    }
+    const int l = threadIdx.x + p * kBlock;
+    valid[p] = l < it.count;
+    sh.key[l] = 0xffffffffu;
+    if (!valid[p]) continue;
+    const int i = it.start + l;
+    const int j = perm ? (int)perm[i] : i;
     float x[3], F[9];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] = vp ? b[a * np + j] : (float)base[p][a] * dx + dx;
+    for (int a = 0; a < 3; ++a) x[a] = b[a * np + j];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) F[a] = vp ? b[(15 + a) * np + j] : 0.0f;
-    float fx[3], w[3][3], dwv[3][3];
+    for (int a = 0; a < 9; ++a) F[a] = b[(15 + a) * np + j];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) base[p][a] = cell_base(x[a], G, e.G, &oob);
+    const int b0 = base[p][0], b1 = base[p][1], b2 = base[p][2];
+    sh.key[l] = cell_pack(b0, b1, b2);
+    float fx[3], w[3][3], dw[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       fx[a] = __fmul_rn(x[a], G) - (float)base[p][a];
-      bspline(fx[a], w[a], dwv[a]);
+      bspline(fx[a], w[a], dw[a]);
+#pragma unroll
+      for (int o = 0; o < 3; ++o) dw[a][o] *= G;
     }
     // v' and C' as the forward G2P stored them in the substep's end state
     float Cn[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) Cn[a] = vp ? bn[(6 + a) * np + i] : 0.0f;
-    const float4 vc =
-        __ldg(e.grid_v + ((long long)(base[p][2] + 1) * e.G + (base[p][1] + 1)) * e.G + base[p][0] + 1);
+    for (int a = 0; a < 9; ++a) Cn[a] = bn[(6 + a) * np + i];
+    const float4 vc = __ldg(e.grid_v + ((long long)(b2 + 1) * e.G + (b1 + 1)) * e.G + b0 + 1);
     // trial H_t = H + dt (C' + C' H)   (F here holds H = F - I)
     float CH[9], Ft[9];
     matmul3(Cn, F, CH);
@@ -796,98 +812,75 @@ __global__ void __launch_bounds__(kBlock, 4) k_g2p_adj(const EnvDesc* __restrict
     float xb[3], vb[3], Cb[9], Fob[9];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      xb[a] = vp ? adj[a * np + i] : 0.0f;
-      vb[a] = vp ? adj[(3 + a) * np + i] : 0.0f;
+      xb[a] = adj[a * np + i];
+      vb[a] = adj[(3 + a) * np + i];
     }
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      Cb[a] = vp ? adj[(6 + a) * np + i] : 0.0f;
-      Fob[a] = vp ? adj[(15 + a) * np + i] : 0.0f;
+      Cb[a] = adj[(6 + a) * np + i];
+      Fob[a] = adj[(15 + a) * np + i];
     }
     float Ftb[9];
     project_vjp(m, Ft, Fob, Ftb);
     // F_t = (I + dt C') F:  Cb += dt Ftb F^T = dt (Ftb + Ftb H^T);  Fb_partial = Ftb + dt C'^T Ftb
-    float Fbp[9];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int bb = 0; bb < 3; ++bb) {
         Cb[3 * a + bb] += dt * (Ftb[3 * a + bb] + Ftb[3 * a] * F[3 * bb] + Ftb[3 * a + 1] * F[3 * bb + 1] +
                                 Ftb[3 * a + 2] * F[3 * bb + 2]);
-        Fbp[3 * a + bb] = Ftb[3 * a + bb] + dt * (Cn[a] * Ftb[bb] + Cn[3 + a] * Ftb[3 + bb] + Cn[6 + a] * Ftb[6 + bb]);
+        adj[(15 + 3 * a + bb) * np + i] =
+            Ftb[3 * a + bb] + dt * (Cn[a] * Ftb[bb] + Cn[3 + a] * Ftb[3 + bb] + Cn[6 + a] * Ftb[6 + bb]);
       }
-    // x' = x + dt v'
-    float vnb[3] = {vb[0] + dt * xb[0], vb[1] + dt * xb[1], vb[2] + dt * xb[2]};
+    // x' = x + dt v';  A' = D^-1 C-bar
+    const float vnb[3] = {vb[0] + dt * xb[0], vb[1] + dt * xb[1], vb[2] + dt * xb[2]};
+    float Ab[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Ab[a] = Dinv * Cb[a];
+    // scatter record: the grid receives sum w (v-bar' - V_ref + A' r); V_ref m_i / m_p is
+    // restored in the grid adjoint
+    {
+      const float q[3] = {vnb[0] - vref[0], vnb[1] - vref[1], vnb[2] - vref[2]};
+      const float g[3] = {fx[0] * dx, fx[1] * dx, fx[2] * dx};
+      write_record(sh.rec + l * (kRec / 4), q, g, w[0], w[1], w[2], Ab);
+    }
+    // gather: x-bar += sum_i (g_i . (v-bar' + A' r_i)) grad w_i - A'^T sum_i w_i g_i with
+    // g_i = v_i - v_c (the stencil-uniform part of v_i adds nothing: sum grad w = 0 and
+    // sum r grad w^T = I cancel it against the w C-bar^T term)
     float xbp[3] = {xb[0], xb[1], xb[2]};
-    // the grid receives sum w (v-bar' - V_ref); V_ref m_i/m_p is restored in the grid adjoint
-    const float vsh[3] = {vp ? vnb[0] - vref[0] : 0.0f, vp ? vnb[1] - vref[1] : 0.0f, vp ? vnb[2] - vref[2] : 0.0f};
-    // each lane visits its stencil in its own rotated order (lanes of one cell then update
-    // different shared nodes at each step)
-    const int lane = threadIdx.x & 31;
-    const int rot_x = lane % 3, rot_y = (lane / 3) % 3, rot_z = (lane / 9) % 3;
-    Axis3 ax, ay, az;
-    rot_axis(rot_x, w[0], dwv[0], fx[0], dx, ax);
-    rot_axis(rot_y, w[1], dwv[1], fx[1], dx, ay);
-    rot_axis(rot_z, w[2], dwv[2], fx[2], dx, az);
-    const int b0 = base[p][0], b1 = base[p][1], b2 = base[p][2];
-    const int bi0 = bx.fits ? bx.idx(b0, b1, b2) : 0;
+    float swg[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int jz = 0; jz < 3; ++jz) {
+    for (int oc = 0; oc < 3; ++oc) {
 #pragma unroll
-      for (int jy = 0; jy < 3; ++jy) {
-        const float wyz = ay.w[jy] * az.w[jz], dwy_wz = ay.dw[jy] * az.w[jz], wy_dwz = ay.w[jy] * az.dw[jz];
-        const float ry = ay.r[jy], rz = az.r[jz];
-        // C-bar r = C-bar[:,0] rx + (C-bar[:,1] ry + C-bar[:,2] rz)
-        const float c0 = Cb[1] * ry + Cb[2] * rz, c1 = Cb[4] * ry + Cb[5] * rz, c2 = Cb[7] * ry + Cb[8] * rz;
-        const float4* rowp = e.grid_v + ((long long)(b2 + az.o[jz]) * e.G + (b1 + ay.o[jy])) * e.G + b0;
-        const int row = bi0 + az.o[jz] * nxy + ay.o[jy] * bx.nx;
+      for (int ob = 0; ob < 3; ++ob) {
+        const float wyz = w[1][ob] * w[2][oc], dwy_wz = dw[1][ob] * w[2][oc], wy_dwz = w[1][ob] * dw[2][oc];
+        const float ry = ((float)ob - fx[1]) * dx, rz = ((float)oc - fx[2]) * dx;
+        const float q0 = vnb[0] + Ab[1] * ry + Ab[2] * rz;
+        const float q1 = vnb[1] + Ab[4] * ry + Ab[5] * rz;
+        const float q2 = vnb[2] + Ab[7] * ry + Ab[8] * rz;
+        const float4* rowp = e.grid_v + ((long long)(b2 + oc) * e.G + (b1 + ob)) * e.G + b0;
 #pragma unroll
-        for (int jx = 0; jx < 3; ++jx) {
-          const float wt = ax.w[jx] * wyz;
-          const float gw0 = ax.dw[jx] * wyz * G, gw1 = ax.w[jx] * dwy_wz * G, gw2 = ax.w[jx] * wy_dwz * G;
-          const float rx = ax.r[jx];
-          const float Cr0 = c0 + Cb[0] * rx, Cr1 = c1 + Cb[3] * rx, Cr2 = c2 + Cb[6] * rx;
-          const float4 gv = __ldg(rowp + ax.o[jx]);
-          // v_i - v_c: the stencil-uniform part of v_i adds nothing to x-bar (sum grad w = 0,
-          // sum r grad w^T = I), so it is removed before the FP32 sums
+        for (int oa = 0; oa < 3; ++oa) {
+          const float4 gv = __ldg(rowp + oa);
           const float g0 = gv.x - vc.x, g1 = gv.y - vc.y, g2 = gv.z - vc.z;
-          const float CTv0 = Cb[0] * g0 + Cb[3] * g1 + Cb[6] * g2;
-          const float CTv1 = Cb[1] * g0 + Cb[4] * g1 + Cb[7] * g2;
-          const float CTv2 = Cb[2] * g0 + Cb[5] * g1 + Cb[8] * g2;
-          const float dwt = Dinv * wt;
-          float a0 = wt * vsh[0] + dwt * Cr0;
-          float a1 = wt * vsh[1] + dwt * Cr1;
-          float a2 = wt * vsh[2] + dwt * Cr2;
-          const float sdw = vnb[0] * g0 + vnb[1] * g1 + vnb[2] * g2 + Dinv * (g0 * Cr0 + g1 * Cr1 + g2 * Cr2);
-          xbp[0] += sdw * gw0 - dwt * CTv0;
-          xbp[1] += sdw * gw1 - dwt * CTv1;
-          xbp[2] += sdw * gw2 - dwt * CTv2;
-          if (vp) {
-            if (bx.fits) {
-              const int bi = row + ax.o[jx];
-              atomicAdd(&sb.v[bi], a0);
-              atomicAdd(&sb.v[kBoxNodes + bi], a1);
-              atomicAdd(&sb.v[2 * kBoxNodes + bi], a2);
-            } else {
-              const int ix = b0 + ax.o[jx], iy = b1 + ay.o[jy], iz = b2 + az.o[jz];
-              atomicAdd(e.grid_vb + ((long long)iz * e.G + iy) * e.G + ix, make_float4(a0, a1, a2, 0.f));
-            }
-          }
+          const float rx = ((float)oa - fx[0]) * dx;
+          const float sdw = g0 * (q0 + Ab[0] * rx) + g1 * (q1 + Ab[3] * rx) + g2 * (q2 + Ab[6] * rx);
+          xbp[0] += sdw * (dw[0][oa] * wyz);
+          xbp[1] += sdw * (w[0][oa] * dwy_wz);
+          xbp[2] += sdw * (w[0][oa] * wy_dwz);
+          const float wt = w[0][oa] * wyz;
+          swg[0] += wt * g0;
+          swg[1] += wt * g1;
+          swg[2] += wt * g2;
         }
       }
     }
-    // partial adjoint in place: x-bar and F-bar slots
-    if (vp) {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) adj[a * np + i] = xbp[a];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) adj[(15 + a) * np + i] = Fbp[a];
-    }
+    for (int a = 0; a < 3; ++a) adj[a * np + i] = xbp[a] - (Ab[a] * swg[0] + Ab[3 + a] * swg[1] + Ab[6 + a] * swg[2]);
   }
-  if (bx.fits) {
-    __syncthreads();
-    flush_box<false, true>(e, it.env, bx, sb, e.grid_vb, nullptr, nullptr);
-  }
+  (void)oob;
+  const Box bx = make_box(base, valid, sred);
+  scatter_groups<false>(sh, e, it.env, it.count, valid, base, sred, bx, 0.0f, e.grid_vb, nullptr, nullptr);
 }
 
 // ------------------------------------------------------------------ adjoint: grid^T
@@ -1450,8 +1443,28 @@ struct Timed {  // records the hook's events around one launch of class kc
 
 static inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
+// Six scatter CTAs (P2G, G2P^T) per SM need the largest shared-memory carveout.
+static bool scatter_carveout() {
+  const int pct = cudaSharedmemCarveoutMaxShared;
+  cudaFuncSetAttribute(k_p2g<MAT_NEOHOOKEAN>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_p2g<MAT_VONMISES>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_p2g<MAT_FLUID>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_p2g<MAT_MUSCLE>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_g2p_adj<MAT_NEOHOOKEAN>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_g2p_adj<MAT_VONMISES>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_g2p_adj<MAT_FLUID>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_g2p_adj<MAT_MUSCLE>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  return true;
+}
+
+static void ensure_carveout() {
+  static const bool done = scatter_carveout();
+  (void)done;
+}
+
 void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k) {
   if (L.n_items == 0) return;
+  ensure_carveout();
   Timed tm_(KC_P2G, L.stream);
   const int rev = src.kind == REF_RING || src.kind == REF_REV ? 1 : 0;
   switch (L.material) {
@@ -1491,8 +1504,8 @@ void launch_reward_end(const Launch& L, float* reward_out, bool record) {
 }
 
 void launch_g2p_adj(const Launch& L, StateRef src, StateRef nxt, bool use_perm, int k) {
-  (void)k;
   if (L.n_items == 0) return;
+  ensure_carveout();
   Timed tm_(KC_G2P_ADJ, L.stream);
   switch (L.material) {
     case MAT_NEOHOOKEAN: k_g2p_adj<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0, k); break;
