@@ -1061,7 +1061,7 @@ __global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ en
 // ------------------------------------------------------------------ adjoint: P2G^T
 
 template <int MAT>
-__global__ void __launch_bounds__(kBlock, 4) k_p2g_adj(const EnvDesc* __restrict__ envs,
+__global__ void __launch_bounds__(kBlock, 5) k_p2g_adj(const EnvDesc* __restrict__ envs,
                                                        const WorkItem* __restrict__ items, int item_off, StateRef src,
                                                        int use_perm, int k) {
   __shared__ float vsum_s[3];
@@ -1104,44 +1104,66 @@ __global__ void __launch_bounds__(kBlock, 4) k_p2g_adj(const EnvDesc* __restrict
     kirchhoff(m, s + 15, s + 6, a_g, tau);
 #pragma unroll
     for (int q = 0; q < 9; ++q) A[q] = pm * s[6 + q] + stress_k * tau[q];
-    float Ab[9], vbn[3] = {0.f, 0.f, 0.f}, xbn[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < 9; ++q) Ab[q] = 0.f;
     // The stencil-centre node's (m-bar, p-bar) adds nothing to A-bar and x-bar (sum w r = 0,
     // sum grad w = 0, sum r grad w^T = I); subtracting it keeps the FP32 sums from cancelling.
     const float4 gc =
         __ldg(e.grid_mpb + ((long long)(base[2] + 1) * e.G + (base[1] + 1)) * e.G + base[0] + 1);
+    // Per node i (p-bar_i relative to the centre): u = w p-bar;  A-bar += u r^T;  S += u;
+    // x-bar += (m-bar_i m_p + p-bar_i . (m_p v + A r)) grad w.  After the stencil:
+    // v-bar = m_p (S + p-bar_c sum w) and x-bar -= A^T S.
+    float Ab[9], S[3] = {0.f, 0.f, 0.f}, xbn[3] = {0.f, 0.f, 0.f}, sw = 0.f;
 #pragma unroll
-    for (int cz = 0; cz < 3; ++cz)
+    for (int q = 0; q < 9; ++q) Ab[q] = 0.f;
+    float rx[3], gwx[3];
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+      rx[o] = ((float)o - fx[0]) * dx;
+      gwx[o] = dwv[0][o] * G;
+    }
+    const float mv0 = pm * s[3], mv1 = pm * s[4], mv2 = pm * s[5];
+#pragma unroll 1
+    for (int cz = 0; cz < 3; ++cz) {
+      const float wz = cz == 0 ? w[2][0] : (cz == 1 ? w[2][1] : w[2][2]);
+      const float dwz = (cz == 0 ? dwv[2][0] : (cz == 1 ? dwv[2][1] : dwv[2][2])) * G;
+      const float rz = ((float)cz - fx[2]) * dx;
 #pragma unroll
       for (int cy = 0; cy < 3; ++cy) {
+        const float wyz = w[1][cy] * wz, dwy_wz = dwv[1][cy] * G * wz, wy_dwz = w[1][cy] * dwz;
+        const float ry = ((float)cy - fx[1]) * dx;
+        const float q0 = mv0 + A[1] * ry + A[2] * rz;
+        const float q1 = mv1 + A[4] * ry + A[5] * rz;
+        const float q2 = mv2 + A[7] * ry + A[8] * rz;
         const float4* row = e.grid_mpb + ((long long)(base[2] + cz) * e.G + (base[1] + cy)) * e.G + base[0];
 #pragma unroll
         for (int cx = 0; cx < 3; ++cx) {
-          const float wt = w[0][cx] * w[1][cy] * w[2][cz];
-          const float gw[3] = {dwv[0][cx] * w[1][cy] * w[2][cz] * G, w[0][cx] * dwv[1][cy] * w[2][cz] * G,
-                               w[0][cx] * w[1][cy] * dwv[2][cz] * G};
-          const float r[3] = {((float)cx - fx[0]) * dx, ((float)cy - fx[1]) * dx, ((float)cz - fx[2]) * dx};
           const float4 gb = __ldg(row + cx);
-          const float pb[3] = {gb.y - gc.y, gb.z - gc.z, gb.w - gc.w};
-          float qv[3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) qv[a] = pm * s[3 + a] + A[3 * a] * r[0] + A[3 * a + 1] * r[1] + A[3 * a + 2] * r[2];
-          const float coef = (gb.x - gc.x) * pm + pb[0] * qv[0] + pb[1] * qv[1] + pb[2] * qv[2];
-          vbn[0] += pm * wt * gb.y;
-          vbn[1] += pm * wt * gb.z;
-          vbn[2] += pm * wt * gb.w;
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int bb = 0; bb < 3; ++bb) Ab[3 * a + bb] += wt * pb[a] * r[bb];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const float ATp = A[a] * pb[0] + A[3 + a] * pb[1] + A[6 + a] * pb[2];
-            xbn[a] += coef * gw[a] - wt * ATp;
-          }
+          const float wt = w[0][cx] * wyz;
+          const float p0 = gb.y - gc.y, p1 = gb.z - gc.z, p2 = gb.w - gc.w;
+          const float u0 = wt * p0, u1 = wt * p1, u2 = wt * p2;
+          Ab[0] += u0 * rx[cx];
+          Ab[1] += u0 * ry;
+          Ab[2] += u0 * rz;
+          Ab[3] += u1 * rx[cx];
+          Ab[4] += u1 * ry;
+          Ab[5] += u1 * rz;
+          Ab[6] += u2 * rx[cx];
+          Ab[7] += u2 * ry;
+          Ab[8] += u2 * rz;
+          S[0] += u0;
+          S[1] += u1;
+          S[2] += u2;
+          sw += wt;
+          const float coef = (gb.x - gc.x) * pm + p0 * (q0 + A[0] * rx[cx]) + p1 * (q1 + A[3] * rx[cx]) +
+                             p2 * (q2 + A[6] * rx[cx]);
+          xbn[0] += coef * (gwx[cx] * wyz);
+          xbn[1] += coef * (w[0][cx] * dwy_wz);
+          xbn[2] += coef * (w[0][cx] * wy_dwz);
         }
       }
+    }
+    const float vbn[3] = {pm * (S[0] + gc.y * sw), pm * (S[1] + gc.z * sw), pm * (S[2] + gc.w * sw)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) xbn[a] -= A[a] * S[0] + A[3 + a] * S[1] + A[6 + a] * S[2];
     float Cbn[9], taub[9], Fbn[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -1149,8 +1171,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_p2g_adj(const EnvDesc* __restrict
       taub[q] = stress_k * Ab[q];
       Fbn[q] = adj[(15 + q) * np + i];
     }
+    // C and H again (cached): not holding them through the stencil loop saves registers
+    float CH[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) CH[q] = b[(6 + q) * np + j];
     float agb = 0.0f;
-    kirchhoff_vjp(m, s + 15, s + 6, a_g, taub, Fbn, Cbn, &agb);
+    kirchhoff_vjp(m, CH + 9, CH, a_g, taub, Fbn, Cbn, &agb);
     const int o = perm ? j : i;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
