@@ -35,7 +35,7 @@ UNIT = "particle-substeps/s"
 ALGO_BYTES = {
     "p2g": (96, 16),       # read x, v, C, H; write (m, p) once per node
     "g2p": (144, 16),      # read x, H; write x, v, C, H; read grid v once per node
-    "g2p_adj": (192, 32),  # read x, H + adjoint 96 B, write partial x-bar, H-bar; grid v in, v-bar out
+    "g2p_adj": (228, 32),  # read x, H, C' + adjoint 96 B, write partial x-bar, H-bar; grid v in, v-bar out
     "p2g_adj": (240, 16),  # read state 96 + partial 48, write adjoint 96; grid (m-bar, p-bar) in
     "grid": (0, 48),       # read (m, p), write v, clear (m, p)
     "grid_adj": (0, 80),   # read (m, p), v-bar; write (m-bar, p-bar); clear (m, p), v-bar
@@ -117,8 +117,8 @@ class ClockSampler:
 
 
 def cpu_baseline(n_steps_sample=1, seed=0):
-    """The FP64 oracle, as it stands, on one environment of the workload: one control step
-    (25 substeps) forward + reverse, single-threaded."""
+    """The FP64 oracle, as it stands, on one environment of the workload: n_steps_sample
+    control steps (25 substeps each) forward + checkpointed reverse, single-threaded."""
     import numpy as np
 
     from oracle import oracle as orc
@@ -135,6 +135,69 @@ def cpu_baseline(n_steps_sample=1, seed=0):
     ps = s.n_particles * s.substeps * n_steps_sample
     return ps / dt, dt, (f"1 env x {n_steps_sample} control step(s) x {s.substeps} substeps x "
                          f"{s.n_particles} particles, forward + checkpointed reverse, FP64, 1 thread")
+
+
+def serving_leg(n_req, rate, seed):
+    """Continuous batching under a Poisson request stream: rollouts of the three materials
+    (dough, fluid, muscle solid), particle counts log-uniform in [1k, 200k], horizons uniform
+    in [8, 64] control steps, half of them with gradients, admitted by an 80% memory budget.
+    The same stream also runs through a server holding one request at a time (every
+    request's kernels launched on their own), the per-request-launch baseline."""
+    import numpy as np
+
+    from paper_2412_12089_gb300 import mpm
+    from paper_2412_12089_gb300 import workloads as wl
+
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(n_req):
+        kind = int(rng.integers(0, 3))
+        n = int(round(np.exp(rng.uniform(np.log(1000.0), np.log(200000.0)))))
+        T = int(rng.integers(8, 65))
+        grad = bool(rng.integers(0, 2))
+        # grid per material (48 / 64 / 96), coarser for small requests so the body keeps at
+        # least 8 particles per cell (below about one per cell MLS-MPM goes unstable)
+        G = min((48, 64, 96)[kind], max(16, 4 * int(np.cbrt(n / (8.0 * (0.004, 0.004, 0.00504)[kind])) // 4)))
+        if kind == 0:
+            w = wl.dough(n_envs=1, seed=seed + k, n_range=(n, n), T=T, G=G)
+        elif kind == 1:
+            w = wl.fluid(n_envs=1, seed=seed + k, n=n, T=T, G=G)
+        else:
+            w = wl.jumper(n_envs=1, seed=seed + k, n=n, T=T, G=G)
+        sp = w.specs[0]
+        A = sp.action_dim
+        reqs.append((sp, w.inits[0], w.actions[:T, 0, :A] if A else None, T, grad, n * T * sp.substeps))
+    gaps = rng.exponential(1.0 / rate, n_req)
+    work = sum(r[5] for r in reqs)
+    out = {"workload": f"{n_req} requests, dough/fluid/muscle, n logU[1k,200k], T U[8,64], 50% grad, "
+                       f"grid 48/64/96 capped at 8 particles per cell, Poisson {rate:g}/s, 80% memory budget",
+           "unit_latency": "ms", "unit_throughput": "particle-substeps/s (forward substeps of all requests)"}
+    for mode, resident in (("batched", 64), ("per_request", 1)):
+        srv = mpm.mpm_server_create(mem_fraction=0.8, max_resident=resident)
+        try:
+            t0 = time.perf_counter()
+            tnext = t0
+            tickets = []
+            for (sp, init, acts, T, grad, _), gap in zip(reqs, gaps):
+                tnext += gap
+                while True:
+                    now = time.perf_counter()
+                    if now >= tnext:
+                        break
+                    time.sleep(min(1e-3, tnext - now))
+                tickets.append(mpm.mpm_submit(srv, sp, init, acts, T, want_grad=grad))
+            res = [mpm.mpm_wait(srv, t, 1.8e6) for t in tickets]
+            wall = time.perf_counter() - t0
+            for t in tickets:
+                mpm.mpm_release(srv, t)
+        finally:
+            mpm.mpm_server_destroy(srv)
+        lat = np.array([r["finish_ms"] - r["submit_ms"] for r in res])
+        out[mode] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "throughput": work / wall, "wall_s": wall,
+                     "failed": [(i, int(r["status"])) for i, r in enumerate(res) if r["status"] != 0]}
+    out["speedup_throughput"] = out["batched"]["throughput"] / out["per_request"]["throughput"]
+    return out
 
 
 def run_reference(args):
@@ -173,6 +236,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--per-env-sample", type=int, default=32, help="envs in the per-env-launch comparison")
+    ap.add_argument("--control-steps", type=int, default=16, help="control steps per rollout (small cases)")
+    ap.add_argument("--substeps", type=int, default=25, help="substeps per control step (small cases)")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests in the serving leg (0 = off)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate of the serving leg (1/s)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -198,7 +265,7 @@ def main():
     torch.cuda.set_device(dev)
 
     # ---- workload: env shard of this rank (weak scaling: every rank runs a full batch)
-    w = wl.fluid(n_envs=args.envs, n=args.particles, seed=1000 * rank)
+    w = wl.fluid(n_envs=args.envs, n=args.particles, seed=1000 * rank, T=args.control_steps, substeps=args.substeps)
     T, S, P = w.T, w.specs[0].substeps, w.n_particles
     b = Batch(w.specs, max_steps=T, use_graphs=False, device=local)
     xs = {k: torch.as_tensor(np.concatenate([getattr(i, k) for i in w.inits])).to(dev) for k in ("x", "v", "C", "F")}
@@ -324,9 +391,13 @@ def main():
         e2e = {"value": world * P * T * S * reps / wall, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "reps": reps}
 
+    serve = None
+    if args.serve_requests > 0 and rank == 0:
+        serve = serving_leg(args.serve_requests, args.serve_rate, seed=11)
+
     cpu = None
     if not args.no_cpu and rank == 0:
-        v, dt, sample = cpu_baseline(1)
+        v, dt, sample = cpu_baseline(T)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": dt}
 
     if rank == 0:
@@ -335,12 +406,14 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"fluid-{args.envs}env-{args.particles}p-64grid-{T}x{S}-fwd+adjoint",
+                       "serving_workload": serve["workload"] if serve else None,
                        "envs_per_gpu": args.envs, "particles_per_env": args.particles, "grid": 64,
                        "control_steps": T, "substeps": S, "parallelism": f"env-shard x{world}",
                        "l2": "inputs larger than L2 (state and grids > 129 MB per pass)",
                        "launch": "direct (per-class CUDA-event timing on)"},
             "rollout_ms": {"p50": step_ms[len(step_ms) // 2], "p99": step_ms[-1], "what": "one batched fwd+adjoint rollout"},
             "per_env_launch": per_env,
+            "serving": serve,
             "clocks": clk, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "status": int(code),
         }

@@ -7,6 +7,7 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 namespace mpm {
@@ -144,7 +145,7 @@ void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base,
 
 void Group::release() {
   void* ptrs[] = {d_desc, d_items, d_items_env, active, active_n, sort.keys[0], sort.keys[1], sort.vals[0],
-                  sort.vals[1], sort.hist};
+                  sort.vals[1], sort.hist, store_mp, store_list, store_n};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d_desc = nullptr;
@@ -154,6 +155,16 @@ void Group::release() {
   sort = SortScratch{};
   desc_cap = items_cap = 0;
   active_cap = hist_cap = 0;
+  store_mp = nullptr;
+  store_list = nullptr;
+  store_n = nullptr;
+  store_mp_cap = store_list_cap = store_n_cap = 0;
+  store_tiles = 0;
+}
+
+GridStore Group::store_slot(int k) const {
+  return GridStore{store_mp + (size_t)k * store_tiles * 64, store_list + (size_t)k * store_tiles, store_n + k,
+                   store_tiles};
 }
 
 namespace {
@@ -255,6 +266,25 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
   size_t hcap = (size_t)g.hist_cap;
   if ((e = ensure(g.sort.hist, hcap, 256 * ((P + 4095) / 4096)))) return e;
   g.hist_cap = (long long)hcap;
+  g.store_tiles = 0;
+  if (g.want_store && g.S_max > 1) {
+    // room for P/16 active tiles per substep (a few particles per touched tile); a substep
+    // whose active list is longer is re-run by P2G in the adjoint pass instead
+    long long per = std::max<long long>(1, std::min<long long>(g.tiles, (long long)g.P / 16 + 4096));
+    // MPM_GRID_STORE_TILES caps it (tests use it to make every slot overflow)
+    if (const char* cap = std::getenv("MPM_GRID_STORE_TILES")) {
+      const long long c = std::atoll(cap);
+      if (c > 0) per = std::min(per, c);
+    }
+    const size_t slots = (size_t)(g.S_max - 1);
+    if (ensure(g.store_mp, g.store_mp_cap, slots * (size_t)per * 64) == cudaSuccess &&
+        ensure(g.store_list, g.store_list_cap, slots * (size_t)per) == cudaSuccess &&
+        ensure(g.store_n, g.store_n_cap, slots) == cudaSuccess) {
+      g.store_tiles = per;
+    } else {
+      cudaGetLastError();  // the store is an optimisation: run without it
+    }
+  }
   return cudaSuccess;
 }
 
@@ -308,8 +338,9 @@ void substeps_forward(Group& g, const Launch& L, const std::vector<MatGroup>& ma
   }
 }
 
+// store: the group's grid store (recomputed substeps keep their grids there), or NULL.
 void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, const float* rbar, float* agrad,
-                  int n_tot, int a_max) {
+                  int n_tot, int a_max, const Group* store) {
   launch_rev_begin(L);
   launch_reward_adj(L, rbar, n_tot);
   launch_adj_ref(L);
@@ -319,14 +350,23 @@ void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, con
     const StateRef src{k == 0 ? REF_REV : REF_RING, k};
     const StateRef dst{REF_RING, k + 1};
     for (auto& m : mats) launch_p2g(mat_launch(L, m, k + 1), src, k == 0, k);
-    launch_grid(L, k, GRID_FWD, true);
+    if (store) {
+      const GridStore slot = store->store_slot(k);
+      launch_grid(L, k, GRID_FWD, true, &slot);
+    } else {
+      launch_grid(L, k, GRID_FWD, true);
+    }
     for (auto& m : mats) launch_g2p(mat_launch(L, m, k + 1), src, dst, k == 0, k);
   }
   // adjoint substeps, last to first (envs with S > k)
   for (int k = S - 1; k >= 0; --k) {
     cudaMemsetAsync(L.active_n, 0, sizeof(int), L.stream);
     const StateRef src{k == 0 ? REF_REV : REF_RING, k};
-    for (auto& m : mats) launch_p2g(mat_launch(L, m, k), src, k == 0, k);
+    // the grid of substep k: restored from the store for envs the recompute kept it for,
+    // rebuilt by P2G for the others (and for all when the store slot overflowed)
+    const bool stored = store && k + 1 < S;
+    if (stored) launch_restore(L, store->store_slot(k));
+    for (auto& m : mats) launch_p2g(mat_launch(L, m, k), src, k == 0, k, stored ? store->store_n + k : nullptr);
     launch_grid(L, k, GRID_KEEP, true);
     // the end state of substep k: ring block k+1 for envs with S > k+1 (a prefix of the
     // material's items), the step's end checkpoint for envs whose last substep is k
@@ -380,14 +420,14 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
 void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env) {
   if (g.n_envs == 0) return;
   if (!per_env) {
-    reverse_step(group_launch(g, st), g.mats, g.S_max, rbar, agrad, n_tot, a_max);
+    reverse_step(group_launch(g, st), g.mats, g.S_max, rbar, agrad, n_tot, a_max, g.store_tiles > 0 ? &g : nullptr);
     return;
   }
   for (int e = 0; e < g.n_envs; ++e) {
     const int S = g.spec[e].substeps;
     std::vector<MatGroup> one{{g.spec[e].material, g.env_item0[e], std::vector<int>(S + 1, g.env_nitems[e])}};
     one[0].n_gt[S] = 0;
-    reverse_step(env_launch(g, e, st), one, S, rbar, agrad, n_tot, a_max);
+    reverse_step(env_launch(g, e, st), one, S, rbar, agrad, n_tot, a_max, nullptr);
   }
 }
 

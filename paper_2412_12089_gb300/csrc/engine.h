@@ -60,6 +60,15 @@ struct Group {
   long long active_cap = 0;
   SortScratch sort{};
   long long hist_cap = 0;
+  // Reverse passes keep the grid of every recomputed substep (S_max - 1 slots of
+  // store_tiles tiles) so the adjoint substeps restore it instead of re-running P2G.
+  bool want_store = false;  // set by the owner before group_build
+  float4* store_mp = nullptr;
+  uint2* store_list = nullptr;
+  int* store_n = nullptr;
+  size_t store_mp_cap = 0, store_list_cap = 0, store_n_cap = 0;
+  long long store_tiles = 0;  // tiles per slot (0: no store)
+  GridStore store_slot(int k) const;
   void release();
 };
 

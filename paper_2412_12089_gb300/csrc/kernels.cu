@@ -347,12 +347,15 @@ __device__ __forceinline__ void scatter_groups(ScatterShared& sh, const EnvDesc&
 template <int MAT>
 __global__ void __launch_bounds__(kBlock, 6) k_p2g(const EnvDesc* __restrict__ envs,
                                                    const WorkItem* __restrict__ items, int item_off, StateRef src,
-                                                   int use_perm, int k, int rev, uint2* active, int* active_n) {
+                                                   int use_perm, int k, int rev, uint2* active, int* active_n,
+                                                   const int* __restrict__ skip_stored) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   __shared__ int sred[6];
   __shared__ ScatterShared sh;
   const WorkItem it = items[item_off + blockIdx.x];
+  // the reverse pass restores this substep's grid of envs the recompute stored it for
+  if (skip_stored != nullptr && *skip_stored >= 0 && envs[it.env].S > k + 1) return;
   load_env(envs, it.env, e, c);
   const float* b = ref_block(e, c, src);
   const int sslot = step_slot(c, rev);
@@ -506,14 +509,19 @@ __device__ __forceinline__ void step_pose(const EnvDesc& e, const EnvCtr& c, int
 }
 
 // Persistent warps over the active-tile list; one warp per 4^3 tile, two nodes per lane.
+// With a store slot, the active tiles' (m, p) are also copied there in list order.
 __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, const uint2* __restrict__ active,
-                                              const int* __restrict__ active_n, int k, int mode, int rev) {
+                                              const int* __restrict__ active_n, int k, int mode, int rev,
+                                              GridStore store) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n = *active_n;
+  const bool keep = store.mp != nullptr && n <= store.cap;
+  if (store.n != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *store.n = keep ? n : -1;
   for (int w = warp; w < n; w += nwarps) {
     const uint2 at = active[w];
+    if (keep && lane == 0) store.list[w] = at;
     const EnvDesc& e = envs[at.x];
     const EnvCtr c = *e.ctr;
     float q[4], u[4];
@@ -526,6 +534,7 @@ __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, 
       const int ix = tx * 4 + (l & 3), iy = ty * 4 + ((l >> 2) & 3), iz = tz * 4 + (l >> 4);
       const long long id = ((long long)iz * e.G + iy) * e.G + ix;
       const float4 mp = e.grid_mp[id];
+      if (keep) store.mp[(long long)w * 64 + l] = mp;
       float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
       if (mp.x > 0.0f) {
         NodeFwd t;
@@ -538,6 +547,31 @@ __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, 
       if (mode == GRID_FWD) e.grid_mp[id] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (mode == GRID_FWD && lane == 0) e.tile[at.y] = 0u;
+  }
+}
+
+// Persistent warps over a store slot: (m, p) back into the dense grid, tiles into the
+// active list (which then holds exactly them).
+__global__ void __launch_bounds__(256) k_restore(const EnvDesc* __restrict__ envs, GridStore store, uint2* active,
+                                                 int* active_n) {
+  const int n = *store.n;
+  if (n < 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *active_n = n;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int w = warp; w < n; w += nwarps) {
+    const uint2 at = store.list[w];
+    if (lane == 0) active[w] = at;
+    const EnvDesc& e = envs[at.x];
+    const int TG = e.G >> 2;
+    const int tz = at.y / (TG * TG), ty = (at.y / TG) % TG, tx = at.y % TG;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int l = lane + 32 * h;
+      const int ix = tx * 4 + (l & 3), iy = ty * 4 + ((l >> 2) & 3), iz = tz * 4 + (l >> 4);
+      e.grid_mp[((long long)iz * e.G + iy) * e.G + ix] = store.mp[(long long)w * 64 + l];
+    }
   }
 }
 
@@ -1485,22 +1519,30 @@ static void ensure_carveout() {
   (void)done;
 }
 
-void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k) {
+void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k, const int* skip_stored) {
   if (L.n_items == 0) return;
   ensure_carveout();
-  Timed tm_(KC_P2G, L.stream);
+  // a conditional rebuild (most of its CTAs exit at once) is timed as "other", so the P2G
+  // class holds only full scatters
+  Timed tm_(skip_stored ? KC_OTHER : KC_P2G, L.stream);
   const int rev = src.kind == REF_RING || src.kind == REF_REV ? 1 : 0;
   switch (L.material) {
-    case MAT_NEOHOOKEAN: k_p2g<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n); break;
-    case MAT_VONMISES: k_p2g<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n); break;
-    case MAT_FLUID: k_p2g<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n); break;
-    default: k_p2g<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n); break;
+    case MAT_NEOHOOKEAN: k_p2g<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n, skip_stored); break;
+    case MAT_VONMISES: k_p2g<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n, skip_stored); break;
+    case MAT_FLUID: k_p2g<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n, skip_stored); break;
+    default: k_p2g<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n, skip_stored); break;
   }
 }
 
-void launch_grid(const Launch& L, int k, GridMode mode, bool rev) {
+void launch_grid(const Launch& L, int k, GridMode mode, bool rev, const GridStore* store) {
   Timed tm_(KC_GRID, L.stream);
-  k_grid<<<L.grid_blocks, 256, 0, L.stream>>>(L.envs, L.active, L.active_n, k, (int)mode, rev ? 1 : 0);
+  const GridStore st = store ? *store : GridStore{nullptr, nullptr, nullptr, 0};
+  k_grid<<<L.grid_blocks, 256, 0, L.stream>>>(L.envs, L.active, L.active_n, k, (int)mode, rev ? 1 : 0, st);
+}
+
+void launch_restore(const Launch& L, const GridStore& store) {
+  Timed tm_(KC_GRID, L.stream);
+  k_restore<<<L.grid_blocks, 256, 0, L.stream>>>(L.envs, store, L.active, L.active_n);
 }
 
 void launch_g2p(const Launch& L, StateRef src, StateRef dst, bool use_perm, int k) {

@@ -40,8 +40,23 @@ struct Launch {
 
 enum GridMode { GRID_FWD = 0, GRID_KEEP = 1 };
 
-void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k);
-void launch_grid(const Launch& L, int k, GridMode mode, bool rev);
+// One substep's slot of the reverse pass's grid store: (m, p) of every node of the active
+// tiles, tile by tile in active-list order, and the list itself.  n = tiles stored, or -1
+// when the active list did not fit (cap tiles).
+struct GridStore {
+  float4* mp;
+  uint2* list;
+  int* n;
+  long long cap;
+};
+
+// skip_stored: envs whose grid of this substep is in a valid store (*skip_stored >= 0 and
+// more than k + 1 substeps) are skipped; NULL = none.
+void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k, const int* skip_stored = nullptr);
+// store: also copy the active tiles' (m, p) into the store slot (before they are cleared).
+void launch_grid(const Launch& L, int k, GridMode mode, bool rev, const GridStore* store = nullptr);
+// Write a store slot back into the dense grids and make its tiles the active list.
+void launch_restore(const Launch& L, const GridStore& store);
 void launch_g2p(const Launch& L, StateRef src, StateRef dst, bool use_perm, int k);
 
 void launch_step_begin(const Launch& L, const float* act_in, int a_max, bool record);

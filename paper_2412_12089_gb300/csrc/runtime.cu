@@ -246,6 +246,7 @@ mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* 
     if (cudaMemcpy(desc[e].pose, ctx->specs[e].pose0, 16, cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(ctx, MPM_ERR_CUDA, "pose upload"));
   }
+  ctx->g.want_store = o.max_steps > 0 && !o.per_env_launch;  // grid store for batched reverse passes
   cudaError_t ge = group_build(ctx->g, desc, ctx->specs);
   if (ge != cudaSuccess)
     return bail(fail(ctx, ge == cudaErrorMemoryAllocation ? MPM_ERR_OOM : MPM_ERR_CUDA, "group: %s", cudaGetErrorString(ge)));
