@@ -21,7 +21,9 @@ namespace {
 
 constexpr int kBinStaticMax = 1 << 18;     // particles per call
 constexpr int kSortTileKeys = 4096;        // keys per sort CTA (radix_sort's tile)
-constexpr int kHistEntries = 256 * ((kBinStaticMax + kSortTileKeys - 1) / kSortTileKeys);
+constexpr int kScanTileCounters = 4096;    // counters per scan CTA (radix_sort's scan)
+constexpr int kDigitCounters = 256 * ((kBinStaticMax + kSortTileKeys - 1) / kSortTileKeys);
+constexpr int kHistEntries = kDigitCounters + (kDigitCounters + kScanTileCounters - 1) / kScanTileCounters;
 constexpr size_t kScratchWords = 4 * (size_t)kBinStaticMax + kHistEntries;
 
 static __device__ __align__(256) unsigned g_bin_scratch[kScratchWords];
@@ -58,6 +60,7 @@ mpm_status mpm_bin_static(const float* x, int32_t n, int32_t grid_res, uint32_t*
   if (!x || !keys || !perm || n < 0 || grid_res < 8 || grid_res > 128 || grid_res % 4) return MPM_ERR_INVALID_ARG;
   if (n > kBinStaticMax) return MPM_ERR_INVALID_ARG;  // beyond the fixed scratch
   if (n == 0) return MPM_OK;
+  if (mpm::radix_hist_entries(n) > kHistEntries) return MPM_ERR_INVALID_ARG;  // scratch layout check
   unsigned* base = nullptr;
   if (scratch_for_current_device(&base) != cudaSuccess) return MPM_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;

@@ -264,7 +264,7 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
     return e;
   g.sort.cap = (long long)std::min(std::min(c0, c1), std::min(c2, c3));
   size_t hcap = (size_t)g.hist_cap;
-  if ((e = ensure(g.sort.hist, hcap, 256 * ((P + 4095) / 4096)))) return e;
+  if ((e = ensure(g.sort.hist, hcap, (size_t)radix_hist_entries((long long)P)))) return e;
   g.hist_cap = (long long)hcap;
   g.store_tiles = 0;
   if (g.want_store && g.S_max > 1) {

@@ -95,7 +95,9 @@ struct SortScratch {
 void bin_envs(const Launch& L, long long poff0, long long n_total, int cell_bits, int key_bits, SortScratch& s);
 // Stable LSD radix sort of (keys, vals) on the low key_bits bits; returns the buffer index
 // (0 or 1) holding the result.
+// hist: radix_hist_entries(n) counters of scratch.
 int radix_sort(unsigned** keys, unsigned** vals, long long n, int key_bits, unsigned* hist, cudaStream_t st);
+long long radix_hist_entries(long long n);
 void launch_bin_keys_plain(const float* x, int n, int G, unsigned* keys, unsigned* vals, cudaStream_t st);
 
 }  // namespace mpm

@@ -496,11 +496,10 @@ mpm_status mpm_bin(const float* x, int32_t n, int32_t grid_res, uint32_t* keys, 
   if (!x || !keys || !perm || n < 0 || grid_res < 8 || grid_res > 128 || grid_res % 4) return MPM_ERR_INVALID_ARG;
   if (n == 0) return MPM_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  const long long nb = ((long long)n + 4095) / 4096;
   unsigned *k1 = nullptr, *k2 = nullptr, *v1 = nullptr, *v2 = nullptr, *hist = nullptr;
   bool ok = cudaMalloc(&k1, sizeof(unsigned) * n) == cudaSuccess && cudaMalloc(&k2, sizeof(unsigned) * n) == cudaSuccess &&
             cudaMalloc(&v1, sizeof(unsigned) * n) == cudaSuccess && cudaMalloc(&v2, sizeof(unsigned) * n) == cudaSuccess &&
-            cudaMalloc(&hist, sizeof(unsigned) * 256 * nb) == cudaSuccess;
+            cudaMalloc(&hist, sizeof(unsigned) * radix_hist_entries(n)) == cudaSuccess;
   mpm_status res = MPM_OK;
   if (!ok) {
     res = MPM_ERR_OOM;

@@ -114,6 +114,58 @@ __global__ void __launch_bounds__(1024) k_scan_excl(unsigned* a, long long m) {
   }
 }
 
+// Multi-CTA exclusive scan: each CTA scans a tile of kScanTile counters in place and
+// writes the tile's total; the totals are scanned by k_scan_excl; k_scan_add adds them.
+constexpr int kScanTile = 4096;  // counters per scan CTA (1024 threads x 4)
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(unsigned* a, long long m, unsigned* tile_sums) {
+  __shared__ unsigned warp_sums[32];
+  const long long t0 = (long long)blockIdx.x * kScanTile + threadIdx.x * 4;
+  unsigned v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = t0 + q < m ? a[t0 + q] : 0u;
+  const unsigned loc = v[0] + v[1] + v[2] + v[3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned incl = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned ws = warp_sums[lane], wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    warp_sums[lane] = wi - ws;  // exclusive
+    if (lane == 31) tile_sums[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  unsigned run = warp_sums[warp] + incl - loc;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (t0 + q < m) a[t0 + q] = run;
+    run += v[q];
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_add(unsigned* a, long long m, const unsigned* __restrict__ tile_sums) {
+  const unsigned off = tile_sums[blockIdx.x];
+  const long long t0 = (long long)blockIdx.x * kScanTile + threadIdx.x * 4;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (t0 + q < m) a[t0 + q] += off;
+}
+
+long long radix_hist_entries(long long n) {
+  const long long m = 256 * ((n + kSortTile - 1) / kSortTile);
+  return m + (m + kScanTile - 1) / kScanTile;
+}
+
 // Stable scatter.  Warp w of a CTA owns a contiguous run of kSortItems*32 keys of the
 // tile and ranks them in order with warp match; warps are then ranked in order, so the
 // position of every key is its digit's global offset + its rank in key order.
@@ -169,11 +221,22 @@ int radix_sort(unsigned** keys, unsigned** vals, long long n, int key_bits, unsi
   int cur = 0;
   if (n <= 1) return cur;
   const int nb = (int)((n + kSortTile - 1) / kSortTile);
+  const long long m = (long long)nb * kRadix;
+  const int ntiles = (int)((m + kScanTile - 1) / kScanTile);
+  unsigned* tile_sums = hist + m;  // radix_hist_entries(n) counters in all
   for (int shift = 0; shift < key_bits; shift += 8) {
     k_radix_hist<<<nb, kSortThreads, 0, st>>>(keys[cur], n, shift, hist);
-    k_scan_excl<<<1, 1024, 0, st>>>(hist, (long long)nb * kRadix);
+    if (ntiles == 1) {
+      k_scan_excl<<<1, 1024, 0, st>>>(hist, m);
+      count_launches(1);
+    } else {
+      k_scan_tiles<<<ntiles, 1024, 0, st>>>(hist, m, tile_sums);
+      k_scan_excl<<<1, 1024, 0, st>>>(tile_sums, ntiles);
+      k_scan_add<<<ntiles, 1024, 0, st>>>(hist, m, tile_sums);
+      count_launches(3);
+    }
     k_radix_scatter<<<nb, kSortThreads, 0, st>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, hist);
-    count_launches(3);
+    count_launches(2);
     cur ^= 1;
   }
   return cur;
