@@ -1,0 +1,91 @@
+"""Parity at full benchmark sizes, in the launch configuration the benchmark times (batched
+direct launches, no graphs): every environment of the batch is stepped on the GPU, and
+sampled environments (the smallest, the largest and one in between) are recomputed one by
+one by the FP64 oracle.  Environments are independent, so a sampled environment's oracle
+run is its exact reference even inside the full batch.
+
+Tolerances: horizon 1e-3 on x and v, rewards 1e-3 relative, gradients 1e-3 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2412_12089_gb300 import workloads as wl
+
+from gpu_helpers import rel_err, split
+
+pytestmark = pytest.mark.gpu
+
+
+def run_batch(w, T, grad):
+    import torch
+
+    from paper_2412_12089_gb300.batch import Batch
+
+    b = Batch(w.specs, max_steps=T if grad else 0, use_graphs=False)
+    b.set_inits(w.inits)
+    rews = []
+    for t in range(T):
+        rews.append(b.step(torch.as_tensor(w.actions[t]).cuda(), record=grad).clone())
+    st = b.get_state()
+    out = {k: v.cpu().numpy() for k, v in st.items()}
+    g = None
+    if grad:
+        g = b.backward(reward_adj=np.ones((T, w.n_envs), np.float32))
+        g = {k: v.cpu().numpy() for k, v in g.items()}
+    code, _ = b.check_status()
+    rew = torch.stack(rews).cpu().numpy()
+    b.close()
+    return out, rew, g, code
+
+
+def sampled(w):
+    n = np.array([s.n_particles for s in w.specs])
+    return sorted({int(n.argmin()), int(n.argmax()), w.n_envs // 2})
+
+
+def check_env(w, e, T, out, rew, g):
+    s = w.specs[e]
+    sp = orc.make_spec(s)
+    st = orc.State.from_init(w.inits[e])
+    A = s.action_dim
+    acts = w.actions[:T, e, :max(A, 1)].astype(np.float64)
+    o, q, r, status = orc.rollout(sp, st, np.array(s.pose0, np.float64), acts)
+    assert status == 0
+    assert rel_err(split(w, out["x"])[e], o.x) < 1e-3, (e, "x", rel_err(split(w, out["x"])[e], o.x))
+    assert rel_err(split(w, out["v"])[e], o.v) < 1e-3, (e, "v", rel_err(split(w, out["v"])[e], o.v))
+    assert np.allclose(rew[:, e], r, rtol=1e-3, atol=1e-6), (e, rew[:, e], r)
+    if g is not None and A:
+        ag, (xb, vb, Cb, Fb), qb = orc.rollout_adj(sp, st, np.array(s.pose0, np.float64), acts[:, :A],
+                                                   rbar=np.ones(T))
+        assert rel_err(g["action_grad"][:, e, :A], ag) < 1e-3, (e, rel_err(g["action_grad"][:, e, :A], ag))
+        assert rel_err(split(w, g["xb0"])[e], xb) < 1e-3, (e, "xb0")
+
+
+def test_fullsize_fluid_1024_envs_fwd_adjoint():
+    """1024 fluid envs x 8192 particles, 64^3 grids, one control step of 25 substeps forward
+    and reversed, as in the benchmark."""
+    w = wl.fluid(n_envs=1024, seed=0, T=1)
+    out, rew, g, code = run_batch(w, 1, grad=True)
+    assert code == 0
+    for e in sampled(w) + [1023]:
+        check_env(w, e, 1, out, rew, g)
+
+
+def test_fullsize_dough_512_envs_forward():
+    """512 dough envs of 2k-16k particles, 48^3 grids, two control steps of 20 substeps."""
+    w = wl.dough(n_envs=512, seed=0, T=2)
+    out, rew, _, code = run_batch(w, 2, grad=False)
+    assert code == 0
+    for e in sampled(w):
+        check_env(w, e, 2, out, rew, None)
+
+
+def test_fullsize_jumper_64_envs_fwd_adjoint():
+    """64 soft jumpers x 100k particles, 96^3 grids, one control step of 20 substeps forward
+    and reversed (222 actuator groups)."""
+    w = wl.jumper(n_envs=64, seed=0, T=1)
+    out, rew, g, code = run_batch(w, 1, grad=True)
+    assert code == 0
+    check_env(w, 0, 1, out, rew, g)
+    check_env(w, 63, 1, out, rew, None)
