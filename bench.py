@@ -255,6 +255,7 @@ def main():
     from paper_2412_12089_gb300 import mpm
     from paper_2412_12089_gb300 import workloads as wl
     from paper_2412_12089_gb300.batch import Batch
+    from paper_2412_12089_gb300.sharding import max_over_ranks, sum_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -322,12 +323,9 @@ def main():
     dom_ms, dom_n = mpm.mpm_kernel_time(b.ctx)
     mpm.mpm_time_kernel(b.ctx, 0)
     step_ms = sorted(step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps))
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device=dev)  # the job ends when the slowest rank does
     code, flags = b.check_status()
-    value = world * P * T * S * args.steps / (ms / 1e3)
+    value = sum_over_ranks(P * T * S * args.steps, device=dev) / (ms / 1e3)
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
@@ -392,7 +390,8 @@ def main():
         wall = time.perf_counter() - t0
         h2d = P * 24 * 4 + b.n_envs * 4 * 4 + acts.numel() * 4 + T * b.n_envs * 4
         d2h = T * b.n_envs * 4 + T * b.n_envs * b.A * 4
-        e2e = {"value": world * P * T * S * reps / wall, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        wall = max_over_ranks(wall, device=dev)
+        e2e = {"value": sum_over_ranks(P * T * S * reps, device=dev) / wall, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "reps": reps}
 
     serve = None
