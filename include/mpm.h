@@ -209,6 +209,20 @@ mpm_status mpm_bin(const float* x, int32_t n, int32_t grid_res, uint32_t* keys, 
 mpm_status mpm_bin_static(const float* x, int32_t n, int32_t grid_res, uint32_t* keys, uint32_t* perm, void* stream);
 int32_t mpm_bin_static_max(void);
 
+/*
+ * Autotuner for the scatter kernels (P2G and its adjoint's scatter half; the batching
+ * scheme these shapes belong to has no counterpart in the paper).  On the context's
+ * current state, times P2G of every material present with each shared-box capacity the
+ * kernels are built for (512 and 1024 nodes), `trials` timed launches each after one
+ * warm-up, and keeps the fastest per material for every later step (captured graphs are
+ * dropped and captured again).  The state is not changed.  Call it after mpm_set_state,
+ * between steps.
+ *   box_out: [4] host, chosen capacity by material (MPM_MAT_*), 0 for absent materials;
+ *   ms_out:  [4][2] host, mean P2G time (ms) per material with 512 and 1024 nodes;
+ *   either may be NULL.  trials in [1, 1000], else MPM_ERR_INVALID_ARG.  Synchronises.
+ */
+mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* ms_out);
+
 /* ------------------------------------------------------------------ instrumentation */
 
 /* Kernel classes for mpm_time_kernel. */

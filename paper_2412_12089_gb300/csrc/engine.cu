@@ -223,11 +223,18 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
     if (sa.material != sb.material) return sa.material < sb.material;
     return sa.substeps > sb.substeps;
   });
+  // scatter-box capacity until autotuned; MPM_SCATTER_BOX=512|1024 sets it (tests use it
+  // to run both kernel builds)
+  int box0 = 512;
+  if (const char* b = std::getenv("MPM_SCATTER_BOX")) {
+    const int v = std::atoi(b);
+    if (v == kScatterBoxes[0] || v == kScatterBoxes[1]) box0 = v;
+  }
   g.mats.clear();
   for (size_t i = 0; i < g.items.size(); ++i) {
     const int mat = specs[g.items[i].env].material;
     if (g.mats.empty() || g.mats.back().material != mat)
-      g.mats.push_back({mat, (int)i, std::vector<int>(g.S_max + 1, 0)});
+      g.mats.push_back({mat, (int)i, std::vector<int>(g.S_max + 1, 0), box0});
     auto& m = g.mats.back();
     for (int k = 0; k <= g.S_max; ++k)
       if (specs[g.items[i].env].substeps > k) m.n_gt[k] += 1;
@@ -322,6 +329,7 @@ namespace {
 Launch mat_launch(const Launch& L, const MatGroup& m, int k) {
   Launch Lm = L;
   Lm.material = m.material;
+  Lm.sc_box = m.sc_box;
   Lm.item_offset = m.item0;
   Lm.n_items = m.n_gt[std::min(k, (int)m.n_gt.size() - 1)];
   return Lm;
@@ -392,6 +400,49 @@ void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, con
 }
 
 }  // namespace
+
+cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, std::vector<std::vector<float>>* ms) {
+  if (g.n_envs == 0) return cudaSuccess;
+  trials = std::max(trials, 1);
+  Launch L = group_launch(g, st);
+  bin_envs(L, 0, g.P, g.cell_bits, g.key_bits, g.sort);  // permutation of the live state
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  if (ms) ms->assign(g.mats.size(), std::vector<float>());
+  for (size_t mi = 0; mi < g.mats.size() && err == cudaSuccess; ++mi) {
+    MatGroup& m = g.mats[mi];
+    float best = 0.0f;
+    int best_box = m.sc_box;
+    for (int bi = 0; bi < 2 && err == cudaSuccess; ++bi) {
+      const int box = kScatterBoxes[bi];
+      float sum = 0.0f;
+      for (int t = 0; t <= trials && err == cudaSuccess; ++t) {
+        cudaMemsetAsync(L.active_n, 0, sizeof(int), st);
+        Launch Lm = mat_launch(L, m, 0);
+        Lm.sc_box = box;
+        cudaEventRecord(e0, st);
+        launch_p2g(Lm, StateRef{REF_LIVE, 0}, true, 0);
+        cudaEventRecord(e1, st);
+        launch_grid(L, 0, GRID_FWD, false);  // consumes and clears the grid and tile flags
+        err = cudaEventSynchronize(e1);
+        float t_ms = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&t_ms, e0, e1);
+        if (t > 0) sum += t_ms;
+      }
+      const float mean = sum / (float)trials;
+      if (ms) (*ms)[mi].push_back(mean);
+      if (bi == 0 || mean < best) {
+        best = mean;
+        best_box = box;
+      }
+    }
+    if (err == cudaSuccess) m.sc_box = best_box;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return err;
+}
 
 void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in, int a_max, float* rew,
                      bool per_env) {

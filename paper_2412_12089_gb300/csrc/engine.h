@@ -40,6 +40,7 @@ struct MatGroup {
   int material;
   int item0;               // first item of the material in the group's item list
   std::vector<int> n_gt;   // [k] = items of the material whose env runs more than k substeps
+  int sc_box = 512;        // shared-box capacity of its scatter kernels (autotuned)
 };
 
 struct Group {
@@ -83,6 +84,11 @@ Launch env_launch(const Group& g, int e, cudaStream_t st);
 // launch per stage per environment when per_env).
 void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in, int a_max, float* rew,
                      bool per_env);
+// Autotuner: time P2G of each material on the group's live state (binned first) with every
+// scatter-box capacity the kernels are built for, `trials` timed launches each after one
+// warm-up, and keep the fastest per material.  The grid is cleared after every trial, so
+// the state is unchanged.  ms[m][b]: mean time of material group m with capacity b.
+cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, std::vector<std::vector<float>>* ms);
 // One reverse control step of every environment (step index from the device counters).
 void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env);
 

@@ -208,12 +208,16 @@ __device__ __forceinline__ unsigned cell_pack(int b0, int b1, int b2) {
 // node), or, when the chunk's box is too large, straight into the grid with float4 atomics.
 // (3) The box is flushed to the grid with float4 atomics.
 
-constexpr int kScBox = 512;  // nodes of the shared box (a 256-particle chunk spans 150-400)
-constexpr int kRec = 24;     // floats per particle record
+// Box capacities the scatter kernels are built for (nodes); the autotuner picks one per
+// material.  A 256-particle chunk of a dense body spans 150-400 nodes.
+constexpr int kScBoxSmall = 512;
+constexpr int kScBoxLarge = 1024;
+constexpr int kRec = 24;  // floats per particle record
 
+template <int kScBox>
 struct ScatterShared {
   float4 rec[kBlock * kPPT * kRec / 4];      // particle records in chunk order (24 KB)
-  float box[4 * kScBox];                     // box nodes, component-major (8 KB)
+  float box[4 * kScBox];                     // box nodes, component-major (8 or 16 KB)
   unsigned key[kBlock * kPPT];               // packed cell base per particle (~0u: none)
   unsigned short gstart[kBlock * kPPT + 1];  // first particle of each group, then the end
   int seg[kPPT * kBlock / 32];               // group heads per (particle slot, warp)
@@ -233,8 +237,8 @@ __device__ __forceinline__ void write_record(float4* r, const float* q, const fl
 
 // Steps (2) and (3), after make_box (whose barriers publish the records and keys).
 // kMass: P2G (mass component m w, tiles marked active); else G2P^T (three components).
-template <bool kMass>
-__device__ __forceinline__ void scatter_groups(ScatterShared& sh, const EnvDesc& e, int env, int count,
+template <bool kMass, int kScBox>
+__device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const EnvDesc& e, int env, int count,
                                                const bool* valid, const int (*base)[3], const int* sred,
                                                const Box& bx, float pm, float4* grid, uint2* active,
                                                int* active_n) {
@@ -344,15 +348,15 @@ __device__ __forceinline__ void scatter_groups(ScatterShared& sh, const EnvDesc&
 //
 // Grouped scatter of mass and APIC momentum (q = m v, A = m C - dt V D^-1 tau).
 
-template <int MAT>
-__global__ void __launch_bounds__(kBlock, 6) k_p2g(const EnvDesc* __restrict__ envs,
+template <int MAT, int BOX>
+__global__ void __launch_bounds__(kBlock, BOX == kScBoxSmall ? 6 : 5) k_p2g(const EnvDesc* __restrict__ envs,
                                                    const WorkItem* __restrict__ items, int item_off, StateRef src,
                                                    int use_perm, int k, int rev, uint2* active, int* active_n,
                                                    const int* __restrict__ skip_stored) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   __shared__ int sred[6];
-  __shared__ ScatterShared sh;
+  __shared__ ScatterShared<BOX> sh;
   const WorkItem it = items[item_off + blockIdx.x];
   // the reverse pass restores this substep's grid of envs the recompute stored it for
   if (skip_stored != nullptr && *skip_stored >= 0 && envs[it.env].S > k + 1) return;
@@ -404,7 +408,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_p2g(const EnvDesc* __restrict__ e
   }
   if (oob) atomicOr(&e.ctr->status, 1);
   const Box bx = make_box(base, valid, sred);
-  scatter_groups<true>(sh, e, it.env, it.count, valid, base, sred, bx, pm, e.grid_mp, active, active_n);
+  scatter_groups<true, BOX>(sh, e, it.env, it.count, valid, base, sred, bx, pm, e.grid_mp, active, active_n);
 }
 
 // ------------------------------------------------------------------ grid update
@@ -778,14 +782,14 @@ __global__ void __launch_bounds__(256) k_reward_end(const EnvDesc* __restrict__ 
 
 // ------------------------------------------------------------------ adjoint: G2P^T
 
-template <int MAT>
+template <int MAT, int BOX>
 __global__ void __launch_bounds__(kBlock, 5) k_g2p_adj(const EnvDesc* __restrict__ envs,
                                                        const WorkItem* __restrict__ items, int item_off, StateRef src,
                                                        StateRef nxt, int use_perm, int k) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   __shared__ int sred[6];
-  __shared__ ScatterShared sh;
+  __shared__ ScatterShared<BOX> sh;
   const WorkItem it = items[item_off + blockIdx.x];
   load_env(envs, it.env, e, c);
   const float* b = ref_block(e, c, src);
@@ -914,7 +918,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_g2p_adj(const EnvDesc* __restrict
   }
   (void)oob;
   const Box bx = make_box(base, valid, sred);
-  scatter_groups<false>(sh, e, it.env, it.count, valid, base, sred, bx, 0.0f, e.grid_vb, nullptr, nullptr);
+  scatter_groups<false, BOX>(sh, e, it.env, it.count, valid, base, sred, bx, 0.0f, e.grid_vb, nullptr, nullptr);
 }
 
 // ------------------------------------------------------------------ adjoint: grid^T
@@ -1505,13 +1509,40 @@ static inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
 // Six P2G CTAs per SM need the largest shared-memory carveout (the gather-heavy kernels keep
 // the default, which leaves more L1 for their grid reads).
+template <int BOX>
+static void p2g_carveout(int pct) {
+  cudaFuncSetAttribute(k_p2g<MAT_NEOHOOKEAN, BOX>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_p2g<MAT_VONMISES, BOX>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_p2g<MAT_FLUID, BOX>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_p2g<MAT_MUSCLE, BOX>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+}
+
 static bool scatter_carveout() {
-  const int pct = cudaSharedmemCarveoutMaxShared;
-  cudaFuncSetAttribute(k_p2g<MAT_NEOHOOKEAN>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  cudaFuncSetAttribute(k_p2g<MAT_VONMISES>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  cudaFuncSetAttribute(k_p2g<MAT_FLUID>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  cudaFuncSetAttribute(k_p2g<MAT_MUSCLE>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  p2g_carveout<kScBoxSmall>(cudaSharedmemCarveoutMaxShared);
+  p2g_carveout<kScBoxLarge>(cudaSharedmemCarveoutMaxShared);
   return true;
+}
+
+template <int BOX>
+static void p2g_dispatch(const Launch& L, StateRef src, bool use_perm, int k, int rev, const int* skip_stored) {
+  const int pm = use_perm ? 1 : 0;
+  switch (L.material) {
+    case MAT_NEOHOOKEAN: k_p2g<MAT_NEOHOOKEAN, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_stored); break;
+    case MAT_VONMISES: k_p2g<MAT_VONMISES, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_stored); break;
+    case MAT_FLUID: k_p2g<MAT_FLUID, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_stored); break;
+    default: k_p2g<MAT_MUSCLE, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_stored); break;
+  }
+}
+
+template <int BOX>
+static void g2p_adj_dispatch(const Launch& L, StateRef src, StateRef nxt, bool use_perm, int k) {
+  const int pm = use_perm ? 1 : 0;
+  switch (L.material) {
+    case MAT_NEOHOOKEAN: k_g2p_adj<MAT_NEOHOOKEAN, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
+    case MAT_VONMISES: k_g2p_adj<MAT_VONMISES, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
+    case MAT_FLUID: k_g2p_adj<MAT_FLUID, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
+    default: k_g2p_adj<MAT_MUSCLE, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
+  }
 }
 
 static void ensure_carveout() {
@@ -1526,12 +1557,8 @@ void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k, const int* 
   // class holds only full scatters
   Timed tm_(skip_stored ? KC_OTHER : KC_P2G, L.stream);
   const int rev = src.kind == REF_RING || src.kind == REF_REV ? 1 : 0;
-  switch (L.material) {
-    case MAT_NEOHOOKEAN: k_p2g<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n, skip_stored); break;
-    case MAT_VONMISES: k_p2g<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n, skip_stored); break;
-    case MAT_FLUID: k_p2g<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n, skip_stored); break;
-    default: k_p2g<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k, rev, L.active, L.active_n, skip_stored); break;
-  }
+  if (L.sc_box == kScBoxLarge) p2g_dispatch<kScBoxLarge>(L, src, use_perm, k, rev, skip_stored);
+  else p2g_dispatch<kScBoxSmall>(L, src, use_perm, k, rev, skip_stored);
 }
 
 void launch_grid(const Launch& L, int k, GridMode mode, bool rev, const GridStore* store) {
@@ -1572,12 +1599,8 @@ void launch_g2p_adj(const Launch& L, StateRef src, StateRef nxt, bool use_perm, 
   if (L.n_items == 0) return;
   ensure_carveout();
   Timed tm_(KC_G2P_ADJ, L.stream);
-  switch (L.material) {
-    case MAT_NEOHOOKEAN: k_g2p_adj<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0, k); break;
-    case MAT_VONMISES: k_g2p_adj<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0, k); break;
-    case MAT_FLUID: k_g2p_adj<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0, k); break;
-    default: k_g2p_adj<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, use_perm ? 1 : 0, k); break;
-  }
+  if (L.sc_box == kScBoxLarge) g2p_adj_dispatch<kScBoxLarge>(L, src, nxt, use_perm, k);
+  else g2p_adj_dispatch<kScBoxSmall>(L, src, nxt, use_perm, k);
 }
 
 void launch_grid_adj(const Launch& L, int k) {

@@ -36,7 +36,10 @@ struct Launch {
   int grid_blocks;       // CTAs of the persistent grid kernels
   int env0, n_env;       // environment range of the per-env kernels
   cudaStream_t stream;
+  int sc_box = 512;      // shared-box capacity (nodes) of the scatter kernels: 512 or 1024
 };
+
+constexpr int kScatterBoxes[2] = {512, 1024};  // capacities the scatter kernels are built for
 
 enum GridMode { GRID_FWD = 0, GRID_KEEP = 1 };
 

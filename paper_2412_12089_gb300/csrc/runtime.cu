@@ -492,6 +492,43 @@ int32_t mpm_last_active_tiles(mpm_ctx* ctx) {
   return n;
 }
 
+mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* ms_out) {
+  if (!ctx || trials < 1 || trials > 1000) return MPM_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaDeviceSynchronize());  // the state may still be in flight on the caller's stream
+  std::vector<std::vector<float>> ms;
+  cudaError_t e;
+  {
+    Enqueue q(ctx);
+    e = autotune_scatter(ctx->g, ctx->cap_stream, trials, &ms);
+  }
+  if (e != cudaSuccess) return fail(ctx, MPM_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+  // captured graphs hold the old kernel choice: capture again on the next step
+  for (auto& g : ctx->g_fwd)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  if (ctx->g_rev) {
+    cudaGraphExecDestroy(ctx->g_rev);
+    ctx->g_rev = nullptr;
+  }
+  for (int m = 0; m < 4; ++m) {
+    if (box_out) box_out[m] = 0;
+    if (ms_out) ms_out[2 * m] = ms_out[2 * m + 1] = 0.0f;
+  }
+  for (size_t i = 0; i < ctx->g.mats.size(); ++i) {
+    const int mat = ctx->g.mats[i].material;
+    if (mat < 0 || mat > 3) continue;
+    if (box_out) box_out[mat] = ctx->g.mats[i].sc_box;
+    if (ms_out && ms[i].size() == 2) {
+      ms_out[2 * mat] = ms[i][0];
+      ms_out[2 * mat + 1] = ms[i][1];
+    }
+  }
+  return MPM_OK;
+}
+
 mpm_status mpm_bin(const float* x, int32_t n, int32_t grid_res, uint32_t* keys, uint32_t* perm, void* stream) {
   if (!x || !keys || !perm || n < 0 || grid_res < 8 || grid_res > 128 || grid_res % 4) return MPM_ERR_INVALID_ARG;
   if (n == 0) return MPM_OK;

@@ -97,6 +97,7 @@ def lib():
         "mpm_check_status": (i32, [_P, _P]),
         "mpm_bin": (i32, [_P, i32, i32, _P, _P, _P]),
         "mpm_bin_static": (i32, [_P, i32, i32, _P, _P, _P]),
+        "mpm_autotune": (i32, [_P, i32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_float)]),
         "mpm_bin_static_max": (i32, []),
         "mpm_kernel_launches": (i64, [_P]),
         "mpm_time_kernel": (i32, [_P, i32]),
@@ -267,6 +268,18 @@ def mpm_bin_static(x, n, grid_res, keys, perm, stream=None):
 
 def mpm_bin_static_max():
     return lib().mpm_bin_static_max()
+
+
+def mpm_autotune(ctx, trials=3):
+    """Pick the scatter-box capacity per material on the current state; returns
+    ({material: capacity}, {material: (ms with 512, ms with 1024)}) for materials present."""
+    box = (ct.c_int32 * 4)()
+    ms = (ct.c_float * 8)()
+    check(lib().mpm_autotune(ctx, trials, box, ms), ctx=ctx)
+    names = ("neohookean", "vonmises", "fluid", "muscle")
+    chosen = {names[m]: int(box[m]) for m in range(4) if box[m]}
+    times = {names[m]: (float(ms[2 * m]), float(ms[2 * m + 1])) for m in range(4) if box[m]}
+    return chosen, times
 
 
 def mpm_tape_length(ctx):

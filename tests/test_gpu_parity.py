@@ -235,3 +235,45 @@ def test_gradients_mixed_batch_grid_store(store_tiles, monkeypatch):
         assert rel_err(g["action_grad"][:, e, :Ae], ag) < 1e-3, (e, rel_err(g["action_grad"][:, e, :Ae], ag))
         assert rel_err(split(w, g["xb0"])[e], xb) < 1e-3, (e, "xb0")
         assert rel_err(split(w, g["vb0"])[e], vb) < 1e-3, (e, "vb0")
+
+
+@pytest.mark.parametrize("box", ["512", "1024"])
+def test_scatter_box_builds_match_oracle(box, monkeypatch):
+    """Both shared-box builds of the scatter kernels (P2G forward, G2P^T in reverse) give the
+    oracle's substep and gradients."""
+    monkeypatch.setenv("MPM_SCATTER_BOX", box)
+    T = 1
+    w = small("dough", seed=15, substeps=3, T=T, n_envs=2, n_range=(500, 3000))
+    g, st = _gpu_grads(w, T, rbar=np.ones((T, w.n_envs), np.float32))
+    for e in range(w.n_envs):
+        s = w.specs[e]
+        sp = orc.make_spec(s)
+        so = orc.State.from_init(w.inits[e])
+        A = s.action_dim
+        o, _, _, _ = orc.rollout(sp, so, np.array(s.pose0, np.float64), w.actions[:T, e, :A].astype(np.float64))
+        assert rel_err(split(w, st["x"].cpu().numpy())[e], o.x) < 1e-4  # three substeps
+        ag, (xb, vb, Cb, Fb), qb = orc.rollout_adj(sp, so, np.array(s.pose0, np.float64),
+                                                   w.actions[:T, e, :A].astype(np.float64), rbar=np.ones(T))
+        assert rel_err(g["action_grad"][:, e, :A], ag) < 1e-3
+
+
+def test_autotune_picks_a_box_and_keeps_results():
+    import torch
+
+    from paper_2412_12089_gb300 import mpm
+    from paper_2412_12089_gb300.batch import Batch
+
+    w = small("dough", seed=14, substeps=3, T=2, n_envs=3, n_range=(500, 4000))
+    _, rew0, st0 = gpu_run(w, 2)
+    b = Batch(w.specs, max_steps=0)
+    b.set_inits(w.inits)
+    chosen, times = mpm.mpm_autotune(b.ctx, trials=2)
+    assert set(chosen) == {"vonmises"} and chosen["vonmises"] in (512, 1024)
+    assert all(t > 0 for pair in times.values() for t in pair)
+    assert chosen["vonmises"] == (512 if times["vonmises"][0] <= times["vonmises"][1] else 1024)
+    rews = [b.step(torch.as_tensor(w.actions[t]).cuda()).clone() for t in range(2)]
+    st = {k: v.cpu().numpy() for k, v in b.get_state().items()}
+    assert rel_err(st["x"], st0["x"]) < 1e-5  # the tuning trials left the state unchanged
+    assert np.allclose(torch.stack(rews).cpu().numpy(), rew0, rtol=1e-5, atol=1e-7)
+    with pytest.raises(mpm.MpmError):
+        mpm.mpm_autotune(b.ctx, trials=0)
