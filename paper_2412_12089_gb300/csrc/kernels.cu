@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(256) k_restore(const EnvDesc* __restrict__ env
 // ------------------------------------------------------------------ G2P
 
 template <int MAT>
-__global__ void __launch_bounds__(kBlock) k_g2p(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
                                                 int item_off, StateRef src, StateRef dst, int use_perm, int rev) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
@@ -603,11 +603,9 @@ __global__ void __launch_bounds__(kBlock) k_g2p(const EnvDesc* __restrict__ envs
     const int i = it.start + threadIdx.x + p * kBlock;
     if (i >= it.start + it.count) continue;
     const int j = perm ? (int)perm[i] : i;
-    float x[3], F[9];
+    float x[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) x[a] = b[a * np + j];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) F[a] = b[(15 + a) * np + j];
     int base[3], oob = 0;
     float fx[3], w[3][3], dw[3];
 #pragma unroll
@@ -646,7 +644,11 @@ __global__ void __launch_bounds__(kBlock) k_g2p(const EnvDesc* __restrict__ envs
         }
       }
     }
-    // F <- (I + dt C) F, i.e. H <- H + dt (C + C H); then the plastic projection
+    // F <- (I + dt C) F, i.e. H <- H + dt (C + C H); then the plastic projection.  H is read
+    // only now, so it is not held in registers through the stencil loop.
+    float F[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) F[a] = b[(15 + a) * np + j];
     float CH[9], Ht[9], Fo[9];
     matmul3(C, F, CH);
 #pragma unroll
@@ -1099,7 +1101,7 @@ __global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ en
 // ------------------------------------------------------------------ adjoint: P2G^T
 
 template <int MAT>
-__global__ void __launch_bounds__(kBlock, 5) k_p2g_adj(const EnvDesc* __restrict__ envs,
+__global__ void __launch_bounds__(kBlock, 6) k_p2g_adj(const EnvDesc* __restrict__ envs,
                                                        const WorkItem* __restrict__ items, int item_off, StateRef src,
                                                        int use_perm, int k) {
   __shared__ float vsum_s[3];
