@@ -220,7 +220,9 @@ struct ScatterShared {
   float box[4 * kScBox];                     // box nodes, component-major (8 or 16 KB)
   unsigned key[kBlock * kPPT];               // packed cell base per particle (~0u: none)
   unsigned short gstart[kBlock * kPPT + 1];  // first particle of each group, then the end
+  unsigned short order[kBlock * kPPT];       // groups by decreasing size (balanced warps)
   int seg[kPPT * kBlock / 32];               // group heads per (particle slot, warp)
+  int bucket[32];                            // groups per size class, then class offsets
 };
 
 // Record layout: (q0 q1 q2 gx) (gy gz wx0 wx1) (wx2 wy0 wy1 wy2) (wz0 wz1 wz2 A00)
@@ -282,11 +284,31 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
   }
   for (int q = 0; q < kPPT * (kBlock / 32); ++q) ngrp += sh.seg[q];
   if (threadIdx.x == 0) sh.gstart[ngrp] = (unsigned short)count;
+  if (threadIdx.x < 32) sh.bucket[threadIdx.x] = 0;
+  __syncthreads();
+  // order the groups by decreasing size (classes 1..31, 32+), so the lanes of a warp loop over
+  // groups of about the same length
+  for (int g = threadIdx.x; g < ngrp; g += kBlock) atomicAdd(&sh.bucket[32 - min(sh.gstart[g + 1] - sh.gstart[g], 32)], 1);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int c = sh.bucket[threadIdx.x];
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    sh.bucket[threadIdx.x] = incl - c;
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < ngrp; g += kBlock)
+    sh.order[atomicAdd(&sh.bucket[32 - min(sh.gstart[g + 1] - sh.gstart[g], 32)], 1)] = (unsigned short)g;
   __syncthreads();
   const float dx = e.dx;
   const int nunits = ngrp * 9;
   for (int u = threadIdx.x; u < nunits; u += kBlock) {
-    const int g = u / 9, bc = u - 9 * g;
+    const int gi = u / 9, bc = u - 9 * gi;
+    const int g = sh.order[gi];
     const int ob = bc % 3, oc = bc / 3;
     const int q0 = sh.gstart[g], q1 = sh.gstart[g + 1];
     const unsigned key = sh.key[q0];
