@@ -110,6 +110,9 @@ typedef struct {
     int32_t use_graphs;     /* 1: replay control steps as captured CUDA graphs */
     int32_t chunk;          /* particles per CTA work item, 0 = default */
     int32_t device;         /* CUDA device ordinal */
+    float grid_tape_fraction; /* share of the device's free memory (after the arena) that the
+                                 grid tape may take: recorded steps keep every substep's grid
+                                 so the reverse pass need not rebuild it; 0 = 0.5, < 0 = none */
 } mpm_options;
 
 typedef struct mpm_ctx mpm_ctx;

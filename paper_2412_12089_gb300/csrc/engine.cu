@@ -145,7 +145,7 @@ void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base,
 
 void Group::release() {
   void* ptrs[] = {d_desc, d_items, d_items_env, active, active_n, sort.keys[0], sort.keys[1], sort.vals[0],
-                  sort.vals[1], sort.hist, store_mp, store_list, store_n};
+                  sort.vals[1], sort.hist, tape.mp, tape.list, tape.slot, tape.cursor};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d_desc = nullptr;
@@ -155,16 +155,8 @@ void Group::release() {
   sort = SortScratch{};
   desc_cap = items_cap = 0;
   active_cap = hist_cap = 0;
-  store_mp = nullptr;
-  store_list = nullptr;
-  store_n = nullptr;
-  store_mp_cap = store_list_cap = store_n_cap = 0;
-  store_tiles = 0;
-}
-
-GridStore Group::store_slot(int k) const {
-  return GridStore{store_mp + (size_t)k * store_tiles * 64, store_list + (size_t)k * store_tiles, store_n + k,
-                   store_tiles};
+  tape = GridTape{nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
+  tape_mp_cap = tape_list_cap = tape_slot_cap = tape_cursor_cap = 0;
 }
 
 namespace {
@@ -176,6 +168,16 @@ cudaError_t ensure(T*& p, size_t& cap, size_t n) {
   const size_t want = std::max<size_t>(n + n / 4, 16);
   cudaError_t e = cudaMalloc(&p, want * sizeof(T));
   cap = e == cudaSuccess ? want : 0;
+  return e;
+}
+// As ensure, without headroom (for the large grid-tape pool).
+template <typename T>
+cudaError_t ensure_exact(T*& p, size_t& cap, size_t n) {
+  if (n <= cap && p) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+  cap = e == cudaSuccess ? std::max<size_t>(n, 1) : 0;
   return e;
 }
 }  // namespace
@@ -273,23 +275,30 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
   size_t hcap = (size_t)g.hist_cap;
   if ((e = ensure(g.sort.hist, hcap, (size_t)radix_hist_entries((long long)P)))) return e;
   g.hist_cap = (long long)hcap;
-  g.store_tiles = 0;
-  if (g.want_store && g.S_max > 1) {
-    // room for P/16 active tiles per substep (a few particles per touched tile); a substep
-    // whose active list is longer is re-run by P2G in the adjoint pass instead
-    long long per = std::max<long long>(1, std::min<long long>(g.tiles, (long long)g.P / 16 + 4096));
-    // MPM_GRID_STORE_TILES caps it (tests use it to make every slot overflow)
-    if (const char* cap = std::getenv("MPM_GRID_STORE_TILES")) {
+  g.tape.cap = 0;
+  if (g.want_tape && g.tape_T > 0 && g.tape_budget > 0.0) {
+    // pool: the budget, or 1.5x a generous estimate of the active tiles (P/32 + 1024 per
+    // substep) when that is smaller; MPM_GRID_TAPE_TILES caps it (tests make it overflow)
+    constexpr double kTileBytes = 64.0 * sizeof(float4) + sizeof(uint2);
+    const double est = 1.5 * (double)g.tape_T * g.S_max * ((double)g.P / 32.0 + 1024.0);
+    long long tiles = (long long)std::min(g.tape_budget / kTileBytes, est);
+    if (const char* cap = std::getenv("MPM_GRID_TAPE_TILES")) {
       const long long c = std::atoll(cap);
-      if (c > 0) per = std::min(per, c);
+      if (c > 0) tiles = std::min(tiles, c);
     }
-    const size_t slots = (size_t)(g.S_max - 1);
-    if (ensure(g.store_mp, g.store_mp_cap, slots * (size_t)per * 64) == cudaSuccess &&
-        ensure(g.store_list, g.store_list_cap, slots * (size_t)per) == cudaSuccess &&
-        ensure(g.store_n, g.store_n_cap, slots) == cudaSuccess) {
-      g.store_tiles = per;
+    tiles = std::max(tiles, 1LL);
+    const size_t slots = (size_t)g.tape_T * g.S_max;
+    if (ensure_exact(g.tape.mp, g.tape_mp_cap, (size_t)tiles * 64) == cudaSuccess &&
+        ensure_exact(g.tape.list, g.tape_list_cap, (size_t)tiles) == cudaSuccess &&
+        ensure_exact(g.tape.slot, g.tape_slot_cap, slots) == cudaSuccess &&
+        ensure_exact(g.tape.cursor, g.tape_cursor_cap, 1) == cudaSuccess) {
+      g.tape.cap = tiles;
+      g.tape.T = g.tape_T;
+      g.tape.S = g.S_max;
+      // no slot is kept until a recorded step writes it
+      cudaMemset(g.tape.slot, 0xff, sizeof(int2) * slots);
     } else {
-      cudaGetLastError();  // the store is an optimisation: run without it
+      cudaGetLastError();  // the tape is an optimisation: run without it
     }
   }
   return cudaSuccess;
@@ -335,46 +344,42 @@ Launch mat_launch(const Launch& L, const MatGroup& m, int k) {
   return Lm;
 }
 
-void substeps_forward(Group& g, const Launch& L, const std::vector<MatGroup>& mats, int S) {
+// tape: record every substep's grid into the grid tape (recorded steps), or NULL.
+void substeps_forward(Group& g, const Launch& L, const std::vector<MatGroup>& mats, int S, const GridTape* tape) {
   for (int k = 0; k < S; ++k) {
     cudaMemsetAsync(L.active_n, 0, sizeof(int), L.stream);
     const StateRef src{k == 0 ? REF_LIVE : REF_NEXT, k};
     const StateRef dst{REF_NEXT, k};
     for (auto& m : mats) launch_p2g(mat_launch(L, m, k), src, k == 0, k);
-    launch_grid(L, k, GRID_FWD, false);
+    if (tape) launch_tape_alloc(L, *tape, k);
+    launch_grid(L, k, GRID_FWD, false, tape);
     for (auto& m : mats) launch_g2p(mat_launch(L, m, k), src, dst, k == 0, k);
   }
 }
 
-// store: the group's grid store (recomputed substeps keep their grids there), or NULL.
+// tape: the group's grid tape (the recorded steps kept their grids there), or NULL.
 void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, const float* rbar, float* agrad,
-                  int n_tot, int a_max, const Group* store) {
+                  int n_tot, int a_max, const GridTape* tape) {
   launch_rev_begin(L);
   launch_reward_adj(L, rbar, n_tot);
   launch_adj_ref(L);
-  // recompute substep states 1..S-1 into the ring (envs with S > k + 1)
+  // recompute substep states 1..S-1 into the ring (envs with S > k + 1); the grid of each
+  // substep comes from the tape when it was kept, else P2G rebuilds it
   for (int k = 0; k + 1 < S; ++k) {
     cudaMemsetAsync(L.active_n, 0, sizeof(int), L.stream);
     const StateRef src{k == 0 ? REF_REV : REF_RING, k};
     const StateRef dst{REF_RING, k + 1};
-    for (auto& m : mats) launch_p2g(mat_launch(L, m, k + 1), src, k == 0, k);
-    if (store) {
-      const GridStore slot = store->store_slot(k);
-      launch_grid(L, k, GRID_FWD, true, &slot);
-    } else {
-      launch_grid(L, k, GRID_FWD, true);
-    }
+    if (tape) launch_restore(L, *tape, k);
+    for (auto& m : mats) launch_p2g(mat_launch(L, m, k + 1), src, k == 0, k, tape);
+    launch_grid(L, k, GRID_FWD, true);
     for (auto& m : mats) launch_g2p(mat_launch(L, m, k + 1), src, dst, k == 0, k);
   }
   // adjoint substeps, last to first (envs with S > k)
   for (int k = S - 1; k >= 0; --k) {
     cudaMemsetAsync(L.active_n, 0, sizeof(int), L.stream);
     const StateRef src{k == 0 ? REF_REV : REF_RING, k};
-    // the grid of substep k: restored from the store for envs the recompute kept it for,
-    // rebuilt by P2G for the others (and for all when the store slot overflowed)
-    const bool stored = store && k + 1 < S;
-    if (stored) launch_restore(L, store->store_slot(k));
-    for (auto& m : mats) launch_p2g(mat_launch(L, m, k), src, k == 0, k, stored ? store->store_n + k : nullptr);
+    if (tape) launch_restore(L, *tape, k);
+    for (auto& m : mats) launch_p2g(mat_launch(L, m, k), src, k == 0, k, tape);
     launch_grid(L, k, GRID_KEEP, true);
     // the end state of substep k: ring block k+1 for envs with S > k+1 (a prefix of the
     // material's items), the step's end checkpoint for envs whose last substep is k
@@ -451,7 +456,7 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
     Launch L = group_launch(g, st);
     launch_step_begin(L, act_in, a_max, record);
     bin_envs(L, 0, g.P, g.cell_bits, g.key_bits, g.sort);
-    substeps_forward(g, L, g.mats, g.S_max);
+    substeps_forward(g, L, g.mats, g.S_max, record && g.tape.cap > 0 ? &g.tape : nullptr);
     launch_reward_end(L, rew, record);
     return;
   }
@@ -463,7 +468,7 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
     one[0].n_gt[S] = 0;
     launch_step_begin(L, act_in, a_max, record);
     bin_envs(L, g.desc[e].poff, g.spec[e].n_particles, g.cell_bits, g.cell_bits, g.sort);
-    substeps_forward(g, L, one, S);
+    substeps_forward(g, L, one, S, nullptr);
     launch_reward_end(L, rew, record);
   }
 }
@@ -471,7 +476,7 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
 void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env) {
   if (g.n_envs == 0) return;
   if (!per_env) {
-    reverse_step(group_launch(g, st), g.mats, g.S_max, rbar, agrad, n_tot, a_max, g.store_tiles > 0 ? &g : nullptr);
+    reverse_step(group_launch(g, st), g.mats, g.S_max, rbar, agrad, n_tot, a_max, g.tape.cap > 0 ? &g.tape : nullptr);
     return;
   }
   for (int e = 0; e < g.n_envs; ++e) {

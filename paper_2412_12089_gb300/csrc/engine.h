@@ -61,15 +61,14 @@ struct Group {
   long long active_cap = 0;
   SortScratch sort{};
   long long hist_cap = 0;
-  // Reverse passes keep the grid of every recomputed substep (S_max - 1 slots of
-  // store_tiles tiles) so the adjoint substeps restore it instead of re-running P2G.
-  bool want_store = false;  // set by the owner before group_build
-  float4* store_mp = nullptr;
-  uint2* store_list = nullptr;
-  int* store_n = nullptr;
-  size_t store_mp_cap = 0, store_list_cap = 0, store_n_cap = 0;
-  long long store_tiles = 0;  // tiles per slot (0: no store)
-  GridStore store_slot(int k) const;
+  // Grid tape: recorded forward steps keep every substep's grid so the reverse pass restores
+  // it instead of re-running P2G (recompute and adjoint substeps alike).  The owner sets
+  // want_tape, tape_T (recorded steps) and tape_budget (bytes) before group_build.
+  bool want_tape = false;
+  int tape_T = 0;
+  double tape_budget = 0.0;
+  GridTape tape{nullptr, nullptr, nullptr, nullptr, 0, 0, 0};  // tape.cap == 0: no tape
+  size_t tape_mp_cap = 0, tape_list_cap = 0, tape_slot_cap = 0, tape_cursor_cap = 0;
   void release();
 };
 

@@ -374,14 +374,17 @@ template <int MAT, int BOX>
 __global__ void __launch_bounds__(kBlock, BOX == kScBoxSmall ? 6 : 5) k_p2g(const EnvDesc* __restrict__ envs,
                                                    const WorkItem* __restrict__ items, int item_off, StateRef src,
                                                    int use_perm, int k, int rev, uint2* active, int* active_n,
-                                                   const int* __restrict__ skip_stored) {
+                                                   const int2* __restrict__ skip_slot, int tape_T, int tape_S) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   __shared__ int sred[6];
   __shared__ ScatterShared<BOX> sh;
   const WorkItem it = items[item_off + blockIdx.x];
-  // the reverse pass restores this substep's grid of envs the recompute stored it for
-  if (skip_stored != nullptr && *skip_stored >= 0 && envs[it.env].S > k + 1) return;
+  // in the reverse pass, the grid tape restores this substep's grid when it was kept
+  if (skip_slot != nullptr) {
+    const int t = envs[it.env].ctr->rev;
+    if (t >= 0 && t < tape_T && skip_slot[t * tape_S + k].y >= 0) return;
+  }
   load_env(envs, it.env, e, c);
   const float* b = ref_block(e, c, src);
   const int sslot = step_slot(c, rev);
@@ -535,19 +538,41 @@ __device__ __forceinline__ void step_pose(const EnvDesc& e, const EnvCtr& c, int
 }
 
 // Persistent warps over the active-tile list; one warp per 4^3 tile, two nodes per lane.
-// With a store slot, the active tiles' (m, p) are also copied there in list order.
+// Index of the recorded step running now (tape slot row), or -1 outside the tape.
+__device__ __forceinline__ int tape_step_fwd(const EnvDesc* envs, int env0, const GridTape& tape) {
+  const EnvCtr* c = envs[env0].ctr;
+  const int t = c->live - c->base;
+  return (t >= 0 && t < tape.T) ? t : -1;
+}
+
+// Index of the step being reversed, or -1 outside the tape.
+__device__ __forceinline__ int tape_step_rev(const EnvDesc* envs, int env0, const GridTape& tape) {
+  const int t = envs[env0].ctr->rev;
+  return (t >= 0 && t < tape.T) ? t : -1;
+}
+
+// Recording (rec.mp set): the active tiles' (m, p) are also copied into the tape slot that
+// k_tape_alloc reserved for this substep.
 __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, const uint2* __restrict__ active,
                                               const int* __restrict__ active_n, int k, int mode, int rev,
-                                              GridStore store) {
+                                              GridTape rec, int env0) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n = *active_n;
-  const bool keep = store.mp != nullptr && n <= store.cap;
-  if (store.n != nullptr && blockIdx.x == 0 && threadIdx.x == 0) *store.n = keep ? n : -1;
+  bool keep = false;
+  long long first = 0;
+  if (rec.mp != nullptr) {
+    const int t = tape_step_fwd(envs, env0, rec);
+    if (t >= 0) {
+      const int2 sl = rec.slot[t * rec.S + k];
+      keep = sl.y >= 0;
+      first = sl.x;
+    }
+  }
   for (int w = warp; w < n; w += nwarps) {
     const uint2 at = active[w];
-    if (keep && lane == 0) store.list[w] = at;
+    if (keep && lane == 0) rec.list[first + w] = at;
     const EnvDesc& e = envs[at.x];
     const EnvCtr c = *e.ctr;
     float q[4], u[4];
@@ -560,7 +585,7 @@ __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, 
       const int ix = tx * 4 + (l & 3), iy = ty * 4 + ((l >> 2) & 3), iz = tz * 4 + (l >> 4);
       const long long id = ((long long)iz * e.G + iy) * e.G + ix;
       const float4 mp = e.grid_mp[id];
-      if (keep) store.mp[(long long)w * 64 + l] = mp;
+      if (keep) rec.mp[(first + w) * 64 + l] = mp;
       float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
       if (mp.x > 0.0f) {
         NodeFwd t;
@@ -576,18 +601,38 @@ __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, 
   }
 }
 
-// Persistent warps over a store slot: (m, p) back into the dense grid, tiles into the
-// active list (which then holds exactly them).
-__global__ void __launch_bounds__(256) k_restore(const EnvDesc* __restrict__ envs, GridStore store, uint2* active,
-                                                 int* active_n) {
-  const int n = *store.n;
+// One thread: reserve the pool range of substep k of the recorded step (the first substep
+// of the first recorded step starts the pool over).  A slot that does not fit is marked -1.
+__global__ void k_tape_alloc(const EnvDesc* __restrict__ envs, int env0, GridTape tape, int k,
+                             const int* __restrict__ active_n) {
+  const int t = tape_step_fwd(envs, env0, tape);
+  if (t < 0) return;
+  if (t == 0 && k == 0) *tape.cursor = 0ull;
+  const unsigned long long n = (unsigned long long)*active_n;
+  const unsigned long long off = *tape.cursor;
+  int2 sl = make_int2(0, -1);
+  if (off + n <= (unsigned long long)tape.cap) {
+    sl = make_int2((int)off, (int)n);
+    *tape.cursor = off + n;
+  }
+  tape.slot[t * tape.S + k] = sl;
+}
+
+// Persistent warps over a kept slot of the step being reversed: (m, p) back into the dense
+// grid, its tiles into the active list (which then holds exactly them).
+__global__ void __launch_bounds__(256) k_restore(const EnvDesc* __restrict__ envs, int env0, GridTape tape, int k,
+                                                 uint2* active, int* active_n) {
+  const int t = tape_step_rev(envs, env0, tape);
+  if (t < 0) return;
+  const int2 sl = tape.slot[t * tape.S + k];
+  const int n = sl.y;
   if (n < 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) *active_n = n;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int w = warp; w < n; w += nwarps) {
-    const uint2 at = store.list[w];
+    const uint2 at = tape.list[(long long)sl.x + w];
     if (lane == 0) active[w] = at;
     const EnvDesc& e = envs[at.x];
     const int TG = e.G >> 2;
@@ -596,7 +641,7 @@ __global__ void __launch_bounds__(256) k_restore(const EnvDesc* __restrict__ env
     for (int h = 0; h < 2; ++h) {
       const int l = lane + 32 * h;
       const int ix = tx * 4 + (l & 3), iy = ty * 4 + ((l >> 2) & 3), iz = tz * 4 + (l >> 4);
-      e.grid_mp[((long long)iz * e.G + iy) * e.G + ix] = store.mp[(long long)w * 64 + l];
+      e.grid_mp[((long long)iz * e.G + iy) * e.G + ix] = tape.mp[((long long)sl.x + w) * 64 + l];
     }
   }
 }
@@ -1548,13 +1593,15 @@ static bool scatter_carveout() {
 }
 
 template <int BOX>
-static void p2g_dispatch(const Launch& L, StateRef src, bool use_perm, int k, int rev, const int* skip_stored) {
+static void p2g_dispatch(const Launch& L, StateRef src, bool use_perm, int k, int rev, const GridTape* skip) {
+  const int2* skip_slot = skip ? skip->slot : nullptr;
+  const int tT = skip ? skip->T : 0, tS = skip ? skip->S : 0;
   const int pm = use_perm ? 1 : 0;
   switch (L.material) {
-    case MAT_NEOHOOKEAN: k_p2g<MAT_NEOHOOKEAN, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_stored); break;
-    case MAT_VONMISES: k_p2g<MAT_VONMISES, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_stored); break;
-    case MAT_FLUID: k_p2g<MAT_FLUID, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_stored); break;
-    default: k_p2g<MAT_MUSCLE, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_stored); break;
+    case MAT_NEOHOOKEAN: k_p2g<MAT_NEOHOOKEAN, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
+    case MAT_VONMISES: k_p2g<MAT_VONMISES, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
+    case MAT_FLUID: k_p2g<MAT_FLUID, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
+    default: k_p2g<MAT_MUSCLE, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
   }
 }
 
@@ -1574,26 +1621,31 @@ static void ensure_carveout() {
   (void)done;
 }
 
-void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k, const int* skip_stored) {
+void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k, const GridTape* skip_kept) {
   if (L.n_items == 0) return;
   ensure_carveout();
-  // a conditional rebuild (most of its CTAs exit at once) is timed as "other", so the P2G
-  // class holds only full scatters
-  Timed tm_(skip_stored ? KC_OTHER : KC_P2G, L.stream);
+  // a conditional rebuild (all its CTAs exit at once when the tape kept the grid) is timed
+  // as "other", so the P2G class holds only full scatters
+  Timed tm_(skip_kept ? KC_OTHER : KC_P2G, L.stream);
   const int rev = src.kind == REF_RING || src.kind == REF_REV ? 1 : 0;
-  if (L.sc_box == kScBoxLarge) p2g_dispatch<kScBoxLarge>(L, src, use_perm, k, rev, skip_stored);
-  else p2g_dispatch<kScBoxSmall>(L, src, use_perm, k, rev, skip_stored);
+  if (L.sc_box == kScBoxLarge) p2g_dispatch<kScBoxLarge>(L, src, use_perm, k, rev, skip_kept);
+  else p2g_dispatch<kScBoxSmall>(L, src, use_perm, k, rev, skip_kept);
 }
 
-void launch_grid(const Launch& L, int k, GridMode mode, bool rev, const GridStore* store) {
+void launch_grid(const Launch& L, int k, GridMode mode, bool rev, const GridTape* record) {
   Timed tm_(KC_GRID, L.stream);
-  const GridStore st = store ? *store : GridStore{nullptr, nullptr, nullptr, 0};
-  k_grid<<<L.grid_blocks, 256, 0, L.stream>>>(L.envs, L.active, L.active_n, k, (int)mode, rev ? 1 : 0, st);
+  const GridTape rec = record ? *record : GridTape{nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
+  k_grid<<<L.grid_blocks, 256, 0, L.stream>>>(L.envs, L.active, L.active_n, k, (int)mode, rev ? 1 : 0, rec, L.env0);
 }
 
-void launch_restore(const Launch& L, const GridStore& store) {
+void launch_tape_alloc(const Launch& L, const GridTape& tape, int k) {
+  Timed tm_(KC_OTHER, L.stream);
+  k_tape_alloc<<<1, 1, 0, L.stream>>>(L.envs, L.env0, tape, k, L.active_n);
+}
+
+void launch_restore(const Launch& L, const GridTape& tape, int k) {
   Timed tm_(KC_GRID, L.stream);
-  k_restore<<<L.grid_blocks, 256, 0, L.stream>>>(L.envs, store, L.active, L.active_n);
+  k_restore<<<L.grid_blocks, 256, 0, L.stream>>>(L.envs, L.env0, tape, k, L.active, L.active_n);
 }
 
 void launch_g2p(const Launch& L, StateRef src, StateRef dst, bool use_perm, int k) {

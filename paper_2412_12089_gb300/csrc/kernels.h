@@ -43,23 +43,30 @@ constexpr int kScatterBoxes[2] = {512, 1024};  // capacities the scatter kernels
 
 enum GridMode { GRID_FWD = 0, GRID_KEEP = 1 };
 
-// One substep's slot of the reverse pass's grid store: (m, p) of every node of the active
-// tiles, tile by tile in active-list order, and the list itself.  n = tiles stored, or -1
-// when the active list did not fit (cap tiles).
-struct GridStore {
-  float4* mp;
-  uint2* list;
-  int* n;
-  long long cap;
+// Grid tape: recorded forward steps keep every substep's grid, (m, p) of the 64 nodes of
+// each active tile in active-list order plus the list entries, in one pool; the reverse pass
+// restores them instead of re-running P2G.  slot[t * S + k] = (first tile, tiles) of
+// substep k of recorded step t, tiles = -1 when the pool was full (P2G rebuilds that grid).
+struct GridTape {
+  float4* mp;                  // pool, 64 nodes per tile
+  uint2* list;                 // pool, the tiles' active-list entries
+  int2* slot;                  // [T * S]
+  unsigned long long* cursor;  // tiles taken by the recorded steps so far
+  long long cap;               // pool tiles
+  int T, S;
 };
 
-// skip_stored: envs whose grid of this substep is in a valid store (*skip_stored >= 0 and
-// more than k + 1 substeps) are skipped; NULL = none.
-void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k, const int* skip_stored = nullptr);
-// store: also copy the active tiles' (m, p) into the store slot (before they are cleared).
-void launch_grid(const Launch& L, int k, GridMode mode, bool rev, const GridStore* store = nullptr);
-// Write a store slot back into the dense grids and make its tiles the active list.
-void launch_restore(const Launch& L, const GridStore& store);
+// skip_kept: in the reverse pass, skip every CTA when the tape kept substep k of the step
+// being reversed; NULL = run.
+void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k, const GridTape* skip_kept = nullptr);
+// record: also copy the active tiles' (m, p) into the tape slot of (recorded step, k), which
+// launch_tape_alloc reserved.
+void launch_grid(const Launch& L, int k, GridMode mode, bool rev, const GridTape* record = nullptr);
+// Reserve the pool range of substep k of the recorded step (the active list's length).
+void launch_tape_alloc(const Launch& L, const GridTape& tape, int k);
+// Write substep k of the step being reversed back into the dense grids and make its tiles
+// the active list (nothing when the slot was not kept).
+void launch_restore(const Launch& L, const GridTape& tape, int k);
 void launch_g2p(const Launch& L, StateRef src, StateRef dst, bool use_perm, int k);
 
 void launch_step_begin(const Launch& L, const float* act_in, int a_max, bool record);

@@ -246,7 +246,15 @@ mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* 
     if (cudaMemcpy(desc[e].pose, ctx->specs[e].pose0, 16, cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(ctx, MPM_ERR_CUDA, "pose upload"));
   }
-  ctx->g.want_store = o.max_steps > 0 && !o.per_env_launch;  // grid store for batched reverse passes
+  // grid tape for batched reverse passes: a share of the memory left after the arena
+  ctx->g.want_tape = o.max_steps > 0 && !o.per_env_launch && o.grid_tape_fraction >= 0.0f;
+  ctx->g.tape_T = o.max_steps;
+  if (ctx->g.want_tape) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+    const double frac = o.grid_tape_fraction > 0.0f ? std::min(1.0, (double)o.grid_tape_fraction) : 0.5;
+    ctx->g.tape_budget = frac * (double)free_b;
+  }
   cudaError_t ge = group_build(ctx->g, desc, ctx->specs);
   if (ge != cudaSuccess)
     return bail(fail(ctx, ge == cudaErrorMemoryAllocation ? MPM_ERR_OOM : MPM_ERR_CUDA, "group: %s", cudaGetErrorString(ge)));
@@ -263,7 +271,8 @@ mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* 
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(fail(ctx, MPM_ERR_CUDA, "stream"));
   ctx->total_bytes = ctx->arena_bytes + sizeof(unsigned) * P * 4 + sizeof(float) * P * kComp +
-                     sizeof(uint2) * ctx->g.tiles + (tape ? sizeof(float) * (size_t)ctx->T_cap * n_envs * (A_max + 1) : 0);
+                     sizeof(uint2) * ctx->g.tiles + (tape ? sizeof(float) * (size_t)ctx->T_cap * n_envs * (A_max + 1) : 0) +
+                     (size_t)ctx->g.tape.cap * (64 * sizeof(float4) + sizeof(uint2));
   *out = ctx;
   return MPM_OK;
 }

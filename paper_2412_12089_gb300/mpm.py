@@ -46,7 +46,7 @@ class MpmEnvSpec(ct.Structure):
 
 class MpmOptions(ct.Structure):
     _fields_ = [("max_steps", ct.c_int32), ("per_env_launch", ct.c_int32), ("use_graphs", ct.c_int32),
-                ("chunk", ct.c_int32), ("device", ct.c_int32)]
+                ("chunk", ct.c_int32), ("device", ct.c_int32), ("grid_tape_fraction", ct.c_float)]
 
 
 class MpmServerOptions(ct.Structure):
@@ -206,9 +206,9 @@ def check(code, ctx=None, srv=None):
 
 # ----------------------------------------------------------------------------- same-name wrappers
 
-def mpm_create(specs, max_steps=0, per_env_launch=False, use_graphs=True, chunk=0, device=0):
+def mpm_create(specs, max_steps=0, per_env_launch=False, use_graphs=True, chunk=0, device=0, grid_tape_fraction=0.0):
     arr = (MpmEnvSpec * len(specs))(*[to_c_spec(s) if not isinstance(s, MpmEnvSpec) else s for s in specs])
-    opt = MpmOptions(max_steps, 1 if per_env_launch else 0, 1 if use_graphs else 0, chunk, device)
+    opt = MpmOptions(max_steps, 1 if per_env_launch else 0, 1 if use_graphs else 0, chunk, device, grid_tape_fraction)
     h = _P()
     code = lib().mpm_create(arr, len(specs), ct.byref(opt), ct.byref(h))
     if code != MPM_OK:

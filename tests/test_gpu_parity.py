@@ -207,14 +207,15 @@ def test_action_gradients(name, S):
         assert rel_err(g["pose_grad0"][e], qb) < 1e-3 or np.abs(qb).max() < 1e-8, (name, e, g["pose_grad0"][e], qb)
 
 
-@pytest.mark.parametrize("store_tiles", [None, "1"])
-def test_gradients_mixed_batch_grid_store(store_tiles, monkeypatch):
+@pytest.mark.parametrize("tape_tiles", [None, "1", "300"])
+def test_gradients_mixed_batch_grid_tape(tape_tiles, monkeypatch):
     """Environments of two materials and different substep counts reversed in one batch.
-    The adjoint substeps restore the grids the recompute kept for the environments that have
-    them and rebuild the rest with P2G; with a store of one tile every slot overflows and P2G
-    rebuilds every grid.  Either way each environment's gradients match its FP64 oracle."""
-    if store_tiles is not None:
-        monkeypatch.setenv("MPM_GRID_STORE_TILES", store_tiles)
+    The reverse pass restores the grids the recorded steps kept on the grid tape; with a
+    one-tile pool no slot is kept and P2G rebuilds every grid, with a 300-tile pool the first
+    substeps are kept and the rest rebuilt.  Either way each environment's gradients match its
+    FP64 oracle."""
+    if tape_tiles is not None:
+        monkeypatch.setenv("MPM_GRID_TAPE_TILES", tape_tiles)
     T = 2
     d = small("dough", seed=12, substeps=5, T=T, n_envs=2, n_range=(500, 2000))
     f = small("fluid", seed=13, substeps=3, T=T, n_envs=1, n=1000)
