@@ -292,7 +292,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    tiles = None
+    tuned = None
     for i in range(args.warmup):
         if i == args.warmup - 1:
             mpm.mpm_time_kernel(b.ctx, "all")  # survey: which kernel class dominates
@@ -300,7 +300,7 @@ def main():
         if i == 0:
             # autotune the scatter kernels' shared-box capacity on a binned state
             chosen, p2g_ms = mpm.mpm_autotune(b.ctx, trials=3)
-            tiles = {"scatter_box_nodes": chosen, "p2g_trial_ms_512_1024": p2g_ms}
+            tuned = {"scatter_box_nodes": chosen, "p2g_trial_ms_512_1024": p2g_ms}
     torch.cuda.synchronize()
     tot, cnt = mpm.mpm_kernel_time(b.ctx, all_classes=True)
     dominant = max((k for k in ALGO_BYTES), key=lambda k: tot[k])
@@ -418,7 +418,7 @@ def main():
                        "envs_per_gpu": args.envs, "particles_per_env": args.particles, "grid": 64,
                        "control_steps": T, "substeps": S, "parallelism": f"env-shard x{world}",
                        "l2": "inputs larger than L2 (state and grids > 129 MB per pass)",
-                       "launch": "direct (per-class CUDA-event timing on)", "autotuned": tiles},
+                       "launch": "direct (per-class CUDA-event timing on)", "autotuned": tuned},
             "rollout_ms": {"p50": step_ms[len(step_ms) // 2], "p99": step_ms[-1], "what": "one batched fwd+adjoint rollout"},
             "per_env_launch": per_env,
             "serving": serve,
