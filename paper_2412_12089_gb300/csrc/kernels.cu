@@ -203,9 +203,10 @@ __device__ __forceinline__ unsigned cell_pack(int b0, int b1, int b2) {
 // group, a group being a run of consecutive particles with the same cell base (a whole cell
 // right after binning).  (1) Every particle writes a record to shared memory: q, its offsets
 // g = f dx from the base node, the weights of the three axes and A.  (2) Work units (group,
-// y offset b, z offset c) sum the group's contributions to the three nodes base + (0..2, b, c)
-// in registers and add them into a shared-memory box (no two units of a group touch the same
+// z offset c) sum the group's contributions to the nine nodes base + (0..2, 0..2, c) in
+// registers and add them into a shared-memory box (no two units of a group touch the same
 // node), or, when the chunk's box is too large, straight into the grid with float4 atomics.
+// Groups are taken largest first, so the lanes of a warp loop over groups of similar size.
 // (3) The box is flushed to the grid with float4 atomics.
 
 // Box capacities the scatter kernels are built for (nodes); the autotuner picks one per
@@ -305,56 +306,68 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
     sh.order[atomicAdd(&sh.bucket[32 - min(sh.gstart[g + 1] - sh.gstart[g], 32)], 1)] = (unsigned short)g;
   __syncthreads();
   const float dx = e.dx;
-  const int nunits = ngrp * 9;
+  // units: (group, z offset c), each summing the nine nodes base + (0..2, 0..2, c)
+  const int nunits = ngrp * 3;
   for (int u = threadIdx.x; u < nunits; u += kBlock) {
-    const int gi = u / 9, bc = u - 9 * gi;
+    const int gi = u / 3, oc = u - 3 * gi;
     const int g = sh.order[gi];
-    const int ob = bc % 3, oc = bc / 3;
     const int q0 = sh.gstart[g], q1 = sh.gstart[g + 1];
     const unsigned key = sh.key[q0];
     const int cx = (int)(key & 1023u), cy = (int)((key >> 10) & 1023u), cz = (int)(key >> 20);
-    const float bdx = (float)ob * dx, cdx = (float)oc * dx;
-    float am[3] = {0.f, 0.f, 0.f};
-    float ap[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    const float cdx = (float)oc * dx;
+    float am[3][3], ap[3][3][3];
+#pragma unroll
+    for (int ob = 0; ob < 3; ++ob)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        am[ob][a] = 0.f;
+        ap[ob][a][0] = ap[ob][a][1] = ap[ob][a][2] = 0.f;
+      }
     for (int q = q0; q < q1; ++q) {
       const float4* r = sh.rec + q * (kRec / 4);
       const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
-      const float wyb = ob == 0 ? r2.y : (ob == 1 ? r2.z : r2.w);
       const float wzc = oc == 0 ? r3.x : (oc == 1 ? r3.y : r3.z);
-      const float ry = bdx - r1.x, rz = cdx - r1.y;
-      const float wyz = wyb * wzc;
-      // A = [r3.w r4.x r4.y; r4.z r4.w r5.x; r5.y r5.z r5.w]
-      const float t0 = r0.x + r4.x * ry + r4.y * rz;
-      const float t1 = r0.y + r4.w * ry + r5.x * rz;
-      const float t2 = r0.z + r5.z * ry + r5.w * rz;
+      const float rz = cdx - r1.y;
+      const float tz0 = r0.x + r4.y * rz, tz1 = r0.y + r5.x * rz, tz2 = r0.z + r5.w * rz;
+      const float wya[3] = {r2.y, r2.z, r2.w};
       const float wxa[3] = {r1.z, r1.w, r2.x};
+      float rxa[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float rx = (float)a * dx - r0.w;
-        const float wt = wxa[a] * wyz;
-        if (kMass) am[a] += wt;
-        ap[a][0] += wt * (t0 + r3.w * rx);
-        ap[a][1] += wt * (t1 + r4.z * rx);
-        ap[a][2] += wt * (t2 + r5.y * rx);
+      for (int a = 0; a < 3; ++a) rxa[a] = (float)a * dx - r0.w;
+#pragma unroll
+      for (int ob = 0; ob < 3; ++ob) {
+        const float ry = (float)ob * dx - r1.x;
+        const float wyz = wya[ob] * wzc;
+        const float t0 = tz0 + r4.x * ry, t1 = tz1 + r4.w * ry, t2 = tz2 + r5.z * ry;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float wt = wxa[a] * wyz;
+          if (kMass) am[ob][a] += wt;
+          ap[ob][a][0] += wt * (t0 + r3.w * rxa[a]);
+          ap[ob][a][1] += wt * (t1 + r4.z * rxa[a]);
+          ap[ob][a][2] += wt * (t2 + r5.y * rxa[a]);
+        }
       }
     }
-    if (fits) {
-      const int row = ((cz + oc - bx.lz) * bx.ny + (cy + ob - bx.ly)) * bx.nx + (cx - bx.lx);
-      // components: (m, p) for P2G, (v-bar) for G2P^T
-      constexpr int o = kMass ? 1 : 0;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (kMass) atomicAdd(&sh.box[row + a], am[a] * pm);
-        atomicAdd(&sh.box[o * kScBox + row + a], ap[a][0]);
-        atomicAdd(&sh.box[(o + 1) * kScBox + row + a], ap[a][1]);
-        atomicAdd(&sh.box[(o + 2) * kScBox + row + a], ap[a][2]);
+    for (int ob = 0; ob < 3; ++ob) {
+      if (fits) {
+        const int row = ((cz + oc - bx.lz) * bx.ny + (cy + ob - bx.ly)) * bx.nx + (cx - bx.lx);
+        constexpr int o = kMass ? 1 : 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (kMass) atomicAdd(&sh.box[row + a], am[ob][a] * pm);
+          atomicAdd(&sh.box[o * kScBox + row + a], ap[ob][a][0]);
+          atomicAdd(&sh.box[(o + 1) * kScBox + row + a], ap[ob][a][1]);
+          atomicAdd(&sh.box[(o + 2) * kScBox + row + a], ap[ob][a][2]);
+        }
+      } else {
+        float4* gp = grid + ((long long)(cz + oc) * e.G + (cy + ob)) * e.G + cx;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          atomicAdd(gp + a, kMass ? make_float4(am[ob][a] * pm, ap[ob][a][0], ap[ob][a][1], ap[ob][a][2])
+                                  : make_float4(ap[ob][a][0], ap[ob][a][1], ap[ob][a][2], 0.f));
       }
-    } else {
-      float4* gp = grid + ((long long)(cz + oc) * e.G + (cy + ob)) * e.G + cx;
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        atomicAdd(gp + a, kMass ? make_float4(am[a] * pm, ap[a][0], ap[a][1], ap[a][2])
-                                : make_float4(ap[a][0], ap[a][1], ap[a][2], 0.f));
     }
   }
   if (fits) {
