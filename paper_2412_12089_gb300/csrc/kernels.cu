@@ -200,8 +200,8 @@ __device__ __forceinline__ unsigned cell_pack(int b0, int b1, int b2) {
 // P2G and G2P^T both add, for every particle p and every node i of its stencil,
 //     w_ip (q_p + A_p r_ip)            (r_ip = x_i - x_p)
 // (and w_ip m_p for P2G's mass).  A CTA does it for its chunk of binned particles group by
-// group, a group being a run of consecutive particles with the same cell base (a whole cell
-// right after binning).  (1) Every particle writes a record to shared memory: q, its offsets
+// group, a group being the chunk's particles of one cell base (found by a counting sort in
+// shared memory; runs of equal cell base in binned order when the chunk's box is too large).  (1) Every particle writes a record to shared memory: q, its offsets
 // g = f dx from the base node, the weights of the three axes and A.  (2) Work units (group,
 // z offset c) sum the group's contributions to the nine nodes base + (0..2, 0..2, c) in
 // registers and add them into a shared-memory box (no two units of a group touch the same
@@ -222,6 +222,7 @@ struct ScatterShared {
   unsigned key[kBlock * kPPT];               // packed cell base per particle (~0u: none)
   unsigned short gstart[kBlock * kPPT + 1];  // first particle of each group, then the end
   unsigned short order[kBlock * kPPT];       // groups by decreasing size (balanced warps)
+  unsigned short sidx[kBlock * kPPT];        // grouped position -> particle record
   int seg[kPPT * kBlock / 32];               // group heads per (particle slot, warp)
   int bucket[32];                            // groups per size class, then class offsets
 };
@@ -246,14 +247,18 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
                                                const Box& bx, float pm, float4* grid, uint2* active,
                                                int* active_n) {
   const bool fits = sred[3] >= 0 && bx.nx * bx.ny * bx.nz <= kScBox;
+  const int cnx = bx.nx - 2, cny = bx.ny - 2;
+  // per cell of the box: particles, then offsets.  It lives in the box's fourth component,
+  // which G2P^T does not use and P2G clears (for its mass) once the sort is done.
+  unsigned* cnt = reinterpret_cast<unsigned*>(sh.box + 3 * kScBox);
   if (fits) {
-    const int vol = bx.nx * bx.ny * bx.nz;
+    const int vol = bx.nx * bx.ny * bx.nz, cvol = cnx * cny * (bx.nz - 2);
     for (int q = threadIdx.x; q < vol; q += kBlock) {
       sh.box[q] = 0.f;
       sh.box[kScBox + q] = 0.f;
       sh.box[2 * kScBox + q] = 0.f;
-      if (kMass) sh.box[3 * kScBox + q] = 0.f;
     }
+    for (int q = threadIdx.x; q < cvol; q += kBlock) cnt[q] = 0u;
   } else if (kMass) {
 #pragma unroll
     for (int p = 0; p < kPPT; ++p)
@@ -263,33 +268,90 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
             for (int cx = 0; cx < 3; cx += 2)
               mark_tile(e, env, base[p][0] + cx, base[p][1] + cy, base[p][2] + cz, active, active_n);
   }
-  // groups: runs of equal keys in chunk order, numbered by a scan over (slot, warp) segments
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned heads[kPPT];
-#pragma unroll
-  for (int p = 0; p < kPPT; ++p) {
-    const int l = threadIdx.x + p * kBlock;
-    const bool h = valid[p] && (l == 0 || sh.key[l - 1] != sh.key[l]);
-    heads[p] = __ballot_sync(0xffffffffu, h);
-    if (lane == 0) sh.seg[p * (kBlock / 32) + warp] = __popc(heads[p]);
-  }
-  __syncthreads();
   int ngrp = 0;
+  if (fits) {
+    // groups = the cells of the chunk: a counting sort by cell base inside the CTA keeps a
+    // cell's particles together however far the binned order has drifted since the last sort
+    __syncthreads();
+    const int cvol = cnx * cny * (bx.nz - 2);
+    int ci[kPPT], rk[kPPT];
 #pragma unroll
-  for (int p = 0; p < kPPT; ++p) {
-    const int sidx = p * (kBlock / 32) + warp;
-    int off = 0;
-    for (int q = 0; q < sidx; ++q) off += sh.seg[q];
-    if (heads[p] >> lane & 1u)
-      sh.gstart[off + __popc(heads[p] & ((1u << lane) - 1u))] = (unsigned short)(threadIdx.x + p * kBlock);
+    for (int p = 0; p < kPPT; ++p) {
+      ci[p] = 0;
+      rk[p] = 0;
+      if (valid[p]) {
+        ci[p] = ((base[p][2] - bx.lz) * cny + (base[p][1] - bx.ly)) * cnx + (base[p][0] - bx.lx);
+        rk[p] = (int)atomicAdd(&cnt[ci[p]], 1u);
+      }
+    }
+    __syncthreads();
+    // exclusive scan of (particles | non-empty << 16) over the cells: offsets and group numbers
+    const int per = (cvol + kBlock - 1) / kBlock;
+    const int c0 = threadIdx.x * per;
+    unsigned loc = 0;
+    for (int q = 0; q < per && c0 + q < cvol; ++q) {
+      const unsigned n = cnt[c0 + q];
+      loc += n | (n ? 1u << 16 : 0u);
+    }
+    unsigned incl = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) sh.seg[warp] = (int)incl;
+    __syncthreads();
+    unsigned run = incl - loc;
+    unsigned total = 0;
+    for (int w = 0; w < kBlock / 32; ++w) {
+      const unsigned t = (unsigned)sh.seg[w];
+      if (w < warp) run += t;
+      total += t;
+    }
+    for (int q = 0; q < per && c0 + q < cvol; ++q) {
+      const unsigned n = cnt[c0 + q];
+      cnt[c0 + q] = run;
+      if (n) sh.gstart[run >> 16] = (unsigned short)(run & 0xffffu);
+      run += n | (n ? 1u << 16 : 0u);
+    }
+    ngrp = (int)(total >> 16);
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < kPPT; ++p)
+      if (valid[p]) sh.sidx[(cnt[ci[p]] & 0xffffu) + rk[p]] = (unsigned short)(threadIdx.x + p * kBlock);
+  } else {
+    // groups = runs of equal keys in chunk order, numbered by a scan over (slot, warp) segments
+    unsigned heads[kPPT];
+#pragma unroll
+    for (int p = 0; p < kPPT; ++p) {
+      const int l = threadIdx.x + p * kBlock;
+      const bool h = valid[p] && (l == 0 || sh.key[l - 1] != sh.key[l]);
+      heads[p] = __ballot_sync(0xffffffffu, h);
+      if (lane == 0) sh.seg[p * (kBlock / 32) + warp] = __popc(heads[p]);
+      sh.sidx[l] = (unsigned short)l;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < kPPT; ++p) {
+      const int sg = p * (kBlock / 32) + warp;
+      int off = 0;
+      for (int q = 0; q < sg; ++q) off += sh.seg[q];
+      if (heads[p] >> lane & 1u)
+        sh.gstart[off + __popc(heads[p] & ((1u << lane) - 1u))] = (unsigned short)(threadIdx.x + p * kBlock);
+    }
+    for (int q = 0; q < kPPT * (kBlock / 32); ++q) ngrp += sh.seg[q];
   }
-  for (int q = 0; q < kPPT * (kBlock / 32); ++q) ngrp += sh.seg[q];
   if (threadIdx.x == 0) sh.gstart[ngrp] = (unsigned short)count;
   if (threadIdx.x < 32) sh.bucket[threadIdx.x] = 0;
   __syncthreads();
   // order the groups by decreasing size (classes 1..31, 32+), so the lanes of a warp loop over
   // groups of about the same length
   for (int g = threadIdx.x; g < ngrp; g += kBlock) atomicAdd(&sh.bucket[32 - min(sh.gstart[g + 1] - sh.gstart[g], 32)], 1);
+  if (kMass && fits) {  // the cell counts are no longer read: clear the mass component
+    const int vol = bx.nx * bx.ny * bx.nz;
+    for (int q = threadIdx.x; q < vol; q += kBlock) sh.box[3 * kScBox + q] = 0.f;
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
     const int c = sh.bucket[threadIdx.x];
@@ -312,7 +374,7 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
     const int gi = u / 3, oc = u - 3 * gi;
     const int g = sh.order[gi];
     const int q0 = sh.gstart[g], q1 = sh.gstart[g + 1];
-    const unsigned key = sh.key[q0];
+    const unsigned key = sh.key[sh.sidx[q0]];
     const int cx = (int)(key & 1023u), cy = (int)((key >> 10) & 1023u), cz = (int)(key >> 20);
     const float cdx = (float)oc * dx;
     float am[3][3], ap[3][3][3];
@@ -324,7 +386,7 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
         ap[ob][a][0] = ap[ob][a][1] = ap[ob][a][2] = 0.f;
       }
     for (int q = q0; q < q1; ++q) {
-      const float4* r = sh.rec + q * (kRec / 4);
+      const float4* r = sh.rec + sh.sidx[q] * (kRec / 4);
       const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
       const float wzc = oc == 0 ? r3.x : (oc == 1 ? r3.y : r3.z);
       const float rz = cdx - r1.y;
