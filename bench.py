@@ -45,9 +45,10 @@ ALGO_BYTES = {
 # capture (kernel source hash at capture time).  Reported only
 # while the kernel sources are unchanged.
 MEASURED_TRAFFIC = {
-    # ncu capture of one P2G launch over 1,310,720 binned fluid particles (160 envs, 64^3):
-    # 132.6 MB read + 4.1 MB written; scaled by particle count to the timed launch
-    "p2g": (104.3, "e52c353c15d946e1"),
+    # ncu captures of one launch over 1,310,720 binned fluid particles (160 envs, 64^3), in
+    # dram__bytes_read.sum + dram__bytes_write.sum per particle; scaled by particle count
+    "g2p_adj": (202.5, "f22b6a492cd9e738"),  # 216.9 MB read + 48.5 MB written, adjoint substep 3
+    "g2p": (126.8, "f22b6a492cd9e738"),      # 75.7 MB read + 90.5 MB written, recompute substep 1
 }
 
 
