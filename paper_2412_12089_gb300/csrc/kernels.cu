@@ -757,12 +757,18 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
       bspline(fx[a], w[a], dw);
     }
     if (oob) status |= 1;
-    float v[3] = {0.f, 0.f, 0.f}, C[9];
+    // With g_i = v_i - v_c (the stencil-centre velocity v_c adds v_c (sum w r)^T = 0 to C,
+    // and subtracting it keeps the FP32 sums from cancelling):
+    //   v = v_c sum w + sum w g,   C = D^-1 sum w g r^T.
+    // The weights are separable, so each row of three nodes (y offset b, z offset c) is first
+    // summed with w_x and w_x r_x, and the row's w_y w_z, r_y, r_z are applied once per row.
+    const float4 vc = __ldg(e.grid_v + ((long long)(base[2] + 1) * e.G + (base[1] + 1)) * e.G + base[0] + 1);
+    float wxr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) wxr[a] = w[0][a] * (((float)a - fx[0]) * dx);
+    float sg[3] = {0.f, 0.f, 0.f}, C[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) C[a] = 0.f;
-    // C = D^-1 sum w (v_i - v_c) r^T: the stencil-centre velocity v_c contributes
-    // v_c (sum w r)^T = 0, and subtracting it keeps the FP32 sum from cancelling.
-    const float4 vc = __ldg(e.grid_v + ((long long)(base[2] + 1) * e.G + (base[1] + 1)) * e.G + base[0] + 1);
 #pragma unroll
     for (int cz = 0; cz < 3; ++cz) {
       const float rz = ((float)cz - fx[2]) * dx;
@@ -771,21 +777,32 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
         const float ry = ((float)cy - fx[1]) * dx;
         const float wyz = w[1][cy] * w[2][cz];
         const float4* row = e.grid_v + ((long long)(base[2] + cz) * e.G + (base[1] + cy)) * e.G + base[0];
+        float s0[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f};  // sum_a w_x g, sum_a w_x r_x g
 #pragma unroll
         for (int cx = 0; cx < 3; ++cx) {
-          const float rx = ((float)cx - fx[0]) * dx;
-          const float wt = w[0][cx] * wyz;
           const float4 gv = __ldg(row + cx);
-          v[0] += wt * gv.x;
-          v[1] += wt * gv.y;
-          v[2] += wt * gv.z;
-          const float d0 = Dinv * wt * (gv.x - vc.x), d1 = Dinv * wt * (gv.y - vc.y), d2 = Dinv * wt * (gv.z - vc.z);
-          C[0] += d0 * rx; C[1] += d0 * ry; C[2] += d0 * rz;
-          C[3] += d1 * rx; C[4] += d1 * ry; C[5] += d1 * rz;
-          C[6] += d2 * rx; C[7] += d2 * ry; C[8] += d2 * rz;
+          const float g0 = gv.x - vc.x, g1 = gv.y - vc.y, g2 = gv.z - vc.z;
+          s0[0] += w[0][cx] * g0;
+          s0[1] += w[0][cx] * g1;
+          s0[2] += w[0][cx] * g2;
+          s1[0] += wxr[cx] * g0;
+          s1[1] += wxr[cx] * g1;
+          s1[2] += wxr[cx] * g2;
+        }
+        const float wyr = wyz * ry, wzr = wyz * rz;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          sg[q] += wyz * s0[q];
+          C[3 * q] += wyz * s1[q];
+          C[3 * q + 1] += wyr * s0[q];
+          C[3 * q + 2] += wzr * s0[q];
         }
       }
     }
+    const float sw = (w[0][0] + w[0][1] + w[0][2]) * (w[1][0] + w[1][1] + w[1][2]) * (w[2][0] + w[2][1] + w[2][2]);
+    const float v[3] = {vc.x * sw + sg[0], vc.y * sw + sg[1], vc.z * sw + sg[2]};
+#pragma unroll
+    for (int a = 0; a < 9; ++a) C[a] *= Dinv;
     // F <- (I + dt C) F, i.e. H <- H + dt (C + C H); then the plastic projection.  H is read
     // only now, so it is not held in registers through the stencil loop.
     float F[9];
