@@ -1309,16 +1309,20 @@ __global__ void __launch_bounds__(kBlock, 6) k_p2g_adj(const EnvDesc* __restrict
         __ldg(e.grid_mpb + ((long long)(base[2] + 1) * e.G + (base[1] + 1)) * e.G + base[0] + 1);
     // Per node i (p-bar_i relative to the centre): u = w p-bar;  A-bar += u r^T;  S += u;
     // x-bar += (m-bar_i m_p + p-bar_i . (m_p v + A r)) grad w.  After the stencil:
-    // v-bar = m_p (S + p-bar_c sum w) and x-bar -= A^T S.
-    float Ab[9], S[3] = {0.f, 0.f, 0.f}, xbn[3] = {0.f, 0.f, 0.f}, sw = 0.f;
+    // v-bar = m_p (S + p-bar_c sum w) and x-bar -= A^T S.  The weights are separable: each
+    // row of three nodes is summed over x first (with w_x, w_x r_x, dw_x) and the row's y and
+    // z factors are applied once.
+    float Ab[9], S[3] = {0.f, 0.f, 0.f}, xbn[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < 9; ++q) Ab[q] = 0.f;
-    float rx[3], gwx[3];
+    float rx[3], gwx[3], wxr[3];
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
       rx[o] = ((float)o - fx[0]) * dx;
       gwx[o] = dwv[0][o] * G;
+      wxr[o] = w[0][o] * rx[o];
     }
+    const float sw = (w[0][0] + w[0][1] + w[0][2]) * (w[1][0] + w[1][1] + w[1][2]) * (w[2][0] + w[2][1] + w[2][2]);
     const float mv0 = pm * s[3], mv1 = pm * s[4], mv2 = pm * s[5];
 #pragma unroll 1
     for (int cz = 0; cz < 3; ++cz) {
@@ -1333,31 +1337,34 @@ __global__ void __launch_bounds__(kBlock, 6) k_p2g_adj(const EnvDesc* __restrict
         const float q1 = mv1 + A[4] * ry + A[5] * rz;
         const float q2 = mv2 + A[7] * ry + A[8] * rz;
         const float4* row = e.grid_mpb + ((long long)(base[2] + cz) * e.G + (base[1] + cy)) * e.G + base[0];
+        float r0[3] = {0.f, 0.f, 0.f}, r1[3] = {0.f, 0.f, 0.f};  // sum_a w_x p-bar, sum_a w_x r_x p-bar
+        float k0 = 0.f, k1 = 0.f;                                 // sum_a dw_x coef, sum_a w_x coef
 #pragma unroll
         for (int cx = 0; cx < 3; ++cx) {
           const float4 gb = __ldg(row + cx);
-          const float wt = w[0][cx] * wyz;
           const float p0 = gb.y - gc.y, p1 = gb.z - gc.z, p2 = gb.w - gc.w;
-          const float u0 = wt * p0, u1 = wt * p1, u2 = wt * p2;
-          Ab[0] += u0 * rx[cx];
-          Ab[1] += u0 * ry;
-          Ab[2] += u0 * rz;
-          Ab[3] += u1 * rx[cx];
-          Ab[4] += u1 * ry;
-          Ab[5] += u1 * rz;
-          Ab[6] += u2 * rx[cx];
-          Ab[7] += u2 * ry;
-          Ab[8] += u2 * rz;
-          S[0] += u0;
-          S[1] += u1;
-          S[2] += u2;
-          sw += wt;
-          const float coef = (gb.x - gc.x) * pm + p0 * (q0 + A[0] * rx[cx]) + p1 * (q1 + A[3] * rx[cx]) +
-                             p2 * (q2 + A[6] * rx[cx]);
-          xbn[0] += coef * (gwx[cx] * wyz);
-          xbn[1] += coef * (w[0][cx] * dwy_wz);
-          xbn[2] += coef * (w[0][cx] * wy_dwz);
+          r0[0] += w[0][cx] * p0;
+          r0[1] += w[0][cx] * p1;
+          r0[2] += w[0][cx] * p2;
+          r1[0] += wxr[cx] * p0;
+          r1[1] += wxr[cx] * p1;
+          r1[2] += wxr[cx] * p2;
+          const float coef = (gb.x - gc.x) * pm + p0 * q0 + p1 * q1 + p2 * q2 +
+                             rx[cx] * (p0 * A[0] + p1 * A[3] + p2 * A[6]);
+          k0 += gwx[cx] * coef;
+          k1 += w[0][cx] * coef;
         }
+        const float wyr = wyz * ry, wzr = wyz * rz;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          S[q] += wyz * r0[q];
+          Ab[3 * q] += wyz * r1[q];
+          Ab[3 * q + 1] += wyr * r0[q];
+          Ab[3 * q + 2] += wzr * r0[q];
+        }
+        xbn[0] += wyz * k0;
+        xbn[1] += dwy_wz * k1;
+        xbn[2] += wy_dwz * k1;
       }
     }
     const float vbn[3] = {pm * (S[0] + gc.y * sw), pm * (S[1] + gc.z * sw), pm * (S[2] + gc.w * sw)};
