@@ -1198,6 +1198,46 @@ void orc_reward_adj(const orc_spec* s, int n, const double* x, const double* v, 
     }
 }
 
+/* ------------------------------------------------------------------ observations */
+
+/*
+ * Observation of a state (App. E task tables of the MPM tasks): the subsampled particle
+ * positions x' (particles 0..ns-1, ns = min(n_sub, n)), their mean (the CoM of the subsample
+ * for uniform density), then 4 pose entries holding the pose components the actions drive
+ * (in action order, zeros past n_coll_act), then 3 entries holding the reach target p*
+ * (reward REACH, else zeros).  obs[orc_obs_dim(s, n)] = 3 ns + 10.
+ */
+int orc_obs_dim(const orc_spec* s, int n)
+{
+    int ns = s->n_sub < n ? s->n_sub : n;
+    return 3 * ns + 10;
+}
+
+void orc_observe(const orc_spec* s, int n, const double* x, const double* q, double* obs)
+{
+    int ns = s->n_sub < n ? s->n_sub : n;
+    double m[3] = {0, 0, 0};
+    for (int p = 0; p < ns; p++)
+        for (int k = 0; k < 3; k++) {
+            obs[3 * p + k] = x[3 * p + k];
+            m[k] += x[3 * p + k];
+        }
+    double* tail = obs + 3 * ns;
+    for (int k = 0; k < 3; k++) tail[k] = ns ? m[k] / ns : 0.0;
+    for (int j = 0; j < 4; j++) tail[3 + j] = j < s->n_coll_act ? q[s->act_map[j]] : 0.0;
+    for (int k = 0; k < 3; k++) tail[7 + k] = s->reward_kind == ORC_REWARD_REACH ? s->rparam[k] : 0.0;
+}
+
+/* Adjoint of orc_observe for an observation adjoint ob: adds to xb and the pose adjoint qb. */
+static void observe_adj(const orc_spec* s, int n, const double* ob, double* xb, double* qb)
+{
+    int ns = s->n_sub < n ? s->n_sub : n;
+    const double* tail = ob + 3 * ns;
+    for (int p = 0; p < ns; p++)
+        for (int k = 0; k < 3; k++) xb[3 * p + k] += ob[3 * p + k] + tail[k] / ns;
+    for (int j = 0; j < s->n_coll_act; j++) qb[s->act_map[j]] += tail[3 + j];
+}
+
 /* ------------------------------------------------------------------ rollouts */
 
 static void pose_velocity(const orc_spec* s, const double* a, double* u)
@@ -1231,6 +1271,20 @@ int orc_rollout_adj(const orc_spec* s, int n, const double* x0, const double* v0
                     const double* rbar, double* act_grad, double* xb0, double* vb0, double* Cb0,
                     double* Fb0, double* qb0)
 {
+    return orc_rollout_adj_obs(s, n, x0, v0, C0, F0, group, q0, actions, T, xbT, vbT, CbT, FbT, rbar, NULL,
+                               act_grad, xb0, vb0, Cb0, Fb0, qb0);
+}
+
+/* As orc_rollout_adj, with the adjoints of the observations (orc_observe) of the states at
+ * every control-step boundary: obs_adj[(T + 1) * orc_obs_dim], row t for the state before
+ * step t, row T for the final state (NULL: none). */
+int orc_rollout_adj_obs(const orc_spec* s, int n, const double* x0, const double* v0, const double* C0,
+                        const double* F0, const int* group, const double* q0, const double* actions, int T,
+                        const double* xbT, const double* vbT, const double* CbT, const double* FbT,
+                        const double* rbar, const double* obs_adj, double* act_grad, double* xb0, double* vb0,
+                        double* Cb0, double* Fb0, double* qb0)
+{
+    const int od = orc_obs_dim(s, n);
     int A = s->n_coll_act + s->n_groups, S = s->S, status = 0;
     size_t sx = 3 * (size_t)n, sm = 9 * (size_t)n, blk = 2 * sx + 2 * sm;
     /* checkpoints of (x, v, C, F) and pose at every control-step boundary */
@@ -1267,6 +1321,8 @@ int orc_rollout_adj(const orc_spec* s, int n, const double* x0, const double* v0
         /* reward of step t, from the end state and end pose */
         if (rbar && rbar[t] != 0.0)
             orc_reward_adj(s, n, end, end + sx, qs + 4 * (t + 1), a, rbar[t], xb0, vb0, qb, ag);
+        /* observation of the end state */
+        if (obs_adj) observe_adj(s, n, obs_adj + (size_t)(t + 1) * od, xb0, qb);
         /* recompute substep states s_0..s_{S-1} of step t */
         double u[4];
         pose_velocity(s, a, u);
@@ -1297,6 +1353,7 @@ int orc_rollout_adj(const orc_spec* s, int n, const double* x0, const double* v0
         /* u[map[j]] += act_scale[j] a[j] / h */
         for (int j = 0; j < s->n_coll_act; j++) ag[j] += ub[s->act_map[j]] * s->act_scale[j] / h;
     }
+    if (obs_adj) observe_adj(s, n, obs_adj, xb0, qb); /* observation of the initial state */
     memcpy(qb0, qb, sizeof qb);
     free(ck);
     free(qs);

@@ -123,6 +123,20 @@ int    orc_rollout_adj(const orc_spec* s, int n, const double* x0, const double*
                        double* act_grad, double* xb0, double* vb0, double* Cb0, double* Fb0,
                        double* qb0);
 
+/* Observation of a state (App. E task tables): x' of the subsample (particles 0..ns-1),
+ * their mean, 4 entries of the action-driven pose components (action order, zero padded)
+ * and 3 of the reach target (REACH, else zeros); orc_obs_dim = 3 ns + 10. */
+int    orc_obs_dim(const orc_spec* s, int n);
+void   orc_observe(const orc_spec* s, int n, const double* x, const double* q, double* obs);
+/* orc_rollout_adj plus observation adjoints obs_adj[(T + 1) * orc_obs_dim] (row t: the
+ * state before step t; row T: the final state), or NULL. */
+int    orc_rollout_adj_obs(const orc_spec* s, int n, const double* x0, const double* v0,
+                           const double* C0, const double* F0, const int* group, const double* q0,
+                           const double* actions, int T, const double* xbT, const double* vbT,
+                           const double* CbT, const double* FbT, const double* rbar,
+                           const double* obs_adj, double* act_grad, double* xb0, double* vb0,
+                           double* Cb0, double* Fb0, double* qb0);
+
 /* Binning mirror in FP32 (compiled without FMA contraction): per particle, the cell
  * base = floor(x*G - 0.5) per axis as the GPU path computes it, the tile-major key
  * ((tile index)*64 + cell-in-tile) with 4^3-cell tiles, and a stable counting sort. */

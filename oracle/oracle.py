@@ -88,6 +88,12 @@ def lib():
         L.orc_rollout_adj.argtypes = [P, ct.c_int, _D, _D, _D, _D, _I, _D, _D, ct.c_int, _D, _D, _D, _D, _D,
                                       _D, _D, _D, _D, _D, _D]
         L.orc_rollout_adj.restype = ct.c_int
+        L.orc_rollout_adj_obs.argtypes = [P, ct.c_int, _D, _D, _D, _D, _I, _D, _D, ct.c_int, _D, _D, _D, _D, _D,
+                                          _D, _D, _D, _D, _D, _D, _D]
+        L.orc_rollout_adj_obs.restype = ct.c_int
+        L.orc_obs_dim.argtypes = [P, ct.c_int]
+        L.orc_obs_dim.restype = ct.c_int
+        L.orc_observe.argtypes = [P, ct.c_int, _D, _D, _D]
         L.orc_bin_keys_f32.argtypes = [ct.c_int, ct.POINTER(ct.c_float), ct.c_int, ct.POINTER(ct.c_uint)]
         L.orc_stable_sort_u32.argtypes = [ct.c_int, ct.POINTER(ct.c_uint), ct.POINTER(ct.c_uint)]
         _lib = L
@@ -293,9 +299,10 @@ def rollout(spec, st: State, q0, actions):
     return out, q, rew, status
 
 
-def rollout_adj(spec, st: State, q0, actions, adj_final=None, rbar=None):
+def rollout_adj(spec, st: State, q0, actions, adj_final=None, rbar=None, obs_adj=None):
     """Forward + reverse.  adj_final = (xb, vb, Cb, Fb) of the final state or None;
-    rbar (T,) or None.  Returns (act_grad (T, A), (xb0, vb0, Cb0, Fb0), qb0)."""
+    rbar (T,) or None; obs_adj (T + 1, obs_dim) adjoints of the observations of the states at
+    the control-step boundaries, or None.  Returns (act_grad (T, A), (xb0, vb0, Cb0, Fb0), qb0)."""
     actions = _arr(actions)
     T, A = actions.shape
     n = st.n
@@ -317,10 +324,32 @@ def rollout_adj(spec, st: State, q0, actions, adj_final=None, rbar=None):
     ag = np.zeros((T, A))
     xb, vb, Cb, Fb = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3, 3)), np.zeros((n, 3, 3))
     qb = np.zeros(4)
-    lib().orc_rollout_adj(ct.byref(spec), n, _d(st.x), _d(st.v), _d(st.C), _d(st.F), _gp(st.group), _d(q0),
-                          _d(actions), T, fin[0], fin[1], fin[2], fin[3], rb, _d(ag), _d(xb), _d(vb), _d(Cb),
-                          _d(Fb), _d(qb))
+    ob = null
+    if obs_adj is not None:
+        obs_adj = _arr(obs_adj)
+        if obs_adj.shape != (T + 1, obs_dim(spec, n)):
+            raise ValueError(f"obs_adj must be ({T + 1}, {obs_dim(spec, n)})")
+        keep.append(obs_adj)
+        ob = _d(obs_adj)
+    lib().orc_rollout_adj_obs(ct.byref(spec), n, _d(st.x), _d(st.v), _d(st.C), _d(st.F), _gp(st.group), _d(q0),
+                              _d(actions), T, fin[0], fin[1], fin[2], fin[3], rb, ob, _d(ag), _d(xb), _d(vb),
+                              _d(Cb), _d(Fb), _d(qb))
     return ag, (xb, vb, Cb, Fb), qb
+
+
+def obs_dim(spec, n):
+    """Length of one environment's observation (3 n_sub + 10)."""
+    return lib().orc_obs_dim(ct.byref(spec), n)
+
+
+def observe(spec, x, q):
+    """Observation of a state: x' of particles 0..ns-1, their mean, 4 action-driven pose
+    components (zero padded), 3 target entries (reach reward, else zeros)."""
+    x = _arr(x)
+    n = x.shape[0]
+    out = np.zeros(obs_dim(spec, n))
+    lib().orc_observe(ct.byref(spec), n, _d(x), _d(_arr(q, (4,))), _d(out))
+    return out
 
 
 def bin_keys_f32(x32, G):

@@ -606,3 +606,88 @@ def test_binning_keys_and_stable_sort():
     perm = orc.stable_sort(keys)
     assert np.array_equal(np.sort(perm), np.arange(5000))
     assert np.array_equal(perm, np.argsort(keys, kind="stable"))
+
+
+# ------------------------------------------------------------------ observations (App. E)
+
+def test_observation_definition_invariants():
+    """x' is the first n_sub particles, the mean is their centroid (translation moves both by
+    the shift), the pose entries follow the action map, the target fills only REACH."""
+    rng = np.random.default_rng(31)
+    sp = spec_for(collider="capsule", coll_dims=(0.03, 0.1, 0, 0), act_map=(0, 2, 3),
+                  act_scale=(0.01, 0.01, 0.05), reward="flat", n_sub=5, rparam=(0.2, 0, 0, 0))
+    x = rng.random((9, 3))
+    q = np.array([0.1, 0.2, 0.3, 0.4])
+    o = orc.observe(sp, x, q)
+    assert o.shape == (3 * 5 + 10,)
+    assert np.array_equal(o[:15].reshape(5, 3), x[:5])
+    shift = np.array([0.05, -0.02, 0.01])
+    o2 = orc.observe(sp, x + shift, q)
+    assert np.allclose(o2[15:18] - o[15:18], shift, atol=1e-15)
+    assert np.allclose(o[15:18], x[:5].mean(0), atol=1e-15)
+    assert np.array_equal(o[18:22], [0.1, 0.3, 0.4, 0.0])
+    assert np.array_equal(o[22:], [0.0, 0.0, 0.0])
+    reach = spec_for(collider="box", coll_dims=(0.05, 0.05, 0.05, 0), act_map=(0, 1, 2),
+                     act_scale=(0.01, 0.01, 0.01), reward="reach", n_sub=20, rparam=(0.5, 0.45, 0.4, 0))
+    o3 = orc.observe(reach, x, q)  # fewer particles than n_sub: all of them
+    assert o3.shape == (3 * 9 + 10,)
+    assert np.array_equal(o3[-3:], [0.5, 0.45, 0.4])
+
+
+@pytest.mark.parametrize("name", ["capsule", "container"])
+def test_observation_adjoint_fd(name):
+    """Adjoints of the observations at every control-step boundary injected into the
+    checkpointed reverse pass: gradients of L = sum_t <c_t, obs(s_t)> with respect to the
+    actions, the initial state and the initial pose against central differences."""
+    rng = np.random.default_rng(33)
+    kw = dict(CASES[name])
+    kw.update(act_map=(0, 2, 3) if name == "capsule" else (0, 1, 2), act_scale=(0.01, 0.01, 0.05),
+              reward="flat" if name == "capsule" else "reach", n_sub=6,
+              rparam=(0.3, 0, 0, 0) if name == "capsule" else (0.5, 0.45, 0.4, 0), substeps=3)
+    sp = spec_for(G=8, dt=2e-3, bound=2, **kw)
+    st = _rand_state(10, 8, rng, lo=0.3, hi=0.7, vs=0.5)
+    if name == "container":
+        st.F = np.broadcast_to(np.eye(3), st.F.shape).copy()
+    st.group = rng.integers(-1, 4, 10).astype(np.int32)
+    q0 = np.array([0.5031, 0.4967, 0.4043, 0.1])
+    T = 2
+    A = 3 + sp.n_groups
+    acts = rng.uniform(-1, 1, (T, A))
+    od = orc.obs_dim(sp, 10)
+    cw = rng.standard_normal((T + 1, od))
+
+    def loss(s, qq=q0, aa=acts):
+        cur, q = s.copy(), np.array(qq, np.float64)
+        total = (cw[0] * orc.observe(sp, cur.x, q)).sum()
+        for t in range(T):
+            cur, q, _, _ = orc.rollout(sp, cur, q, aa[t:t + 1])
+            total += (cw[t + 1] * orc.observe(sp, cur.x, q)).sum()
+        return total
+
+    ag, (xb, vb, Cb, Fb), qb = orc.rollout_adj(sp, st, q0, acts, obs_adj=cw)
+    h = 1e-6
+    noise = 1e-14 * (abs(loss(st)) + 1.0) / h
+
+    def close(fd, ad, ref):
+        return abs(fd - ad) <= 1e-5 * (abs(fd) + 1e-2 * ref) + noise
+
+    for t in range(T):
+        for j in range(A):
+            ap, am = acts.copy(), acts.copy()
+            ap[t, j] += h
+            am[t, j] -= h
+            fd = (loss(st, aa=ap) - loss(st, aa=am)) / (2 * h)
+            assert close(fd, ag[t, j], np.abs(ag).max()), (t, j, fd, ag[t, j])
+    for k, g in enumerate((xb, vb, Cb, Fb)):
+        for _ in range(4):
+            idx = tuple(rng.integers(0, d) for d in g.shape)
+            sp_, sm_ = st.copy(), st.copy()
+            sp_.arrays()[k][idx] += h
+            sm_.arrays()[k][idx] -= h
+            fd = (loss(sp_) - loss(sm_)) / (2 * h)
+            assert close(fd, g[idx], np.abs(g).max()), (k, idx, fd, g[idx])
+    for i in range(4):
+        e = np.zeros(4)
+        e[i] = h
+        fd = (loss(st, qq=q0 + e) - loss(st, qq=q0 - e)) / (2 * h)
+        assert close(fd, qb[i], np.abs(qb).max()), (i, fd, qb[i])
