@@ -213,6 +213,27 @@ mpm_status mpm_bin_static(const float* x, int32_t n, int32_t grid_res, uint32_t*
 int32_t mpm_bin_static_max(void);
 
 /*
+ * Task observation of every environment's current state, as App. E's task tables define it
+ * for the MPM tasks: the positions x' of the subsampled particles (the caller's particles
+ * 0..ns-1, ns = min(n_sub, n)), their mean (the CoM of the subsample), the pose components
+ * the actions drive (action order) and the reach target p* (REACH reward).
+ *   obs: device [n_envs][mpm_obs_dim(ctx)], one row per env laid out as
+ *        [x' (3 * ns_max, zero padded past ns)][mean (3)][pose (4, zero padded)][p* (3)],
+ *        ns_max = the largest ns of the batch, so mpm_obs_dim = 3 * ns_max + 10.
+ *   Stream-ordered; the context's live state is read, nothing changed.
+ */
+int32_t mpm_obs_dim(const mpm_ctx* ctx);
+mpm_status mpm_observe(mpm_ctx* ctx, float* obs, void* stream);
+/*
+ * Adjoints of the observations of the recorded states, for the next mpm_backward (which
+ * consumes them): obs_adj, device or host, [T + 1][n_envs][mpm_obs_dim] with T the tape
+ * length (row t: the state before recorded step t; row T: the current state).  Copied
+ * before the call returns.  NULL forgets adjoints set earlier.  MPM_ERR_STATE without a
+ * tape (max_steps = 0).
+ */
+mpm_status mpm_set_obs_adjoint(mpm_ctx* ctx, const float* obs_adj, void* stream);
+
+/*
  * Autotuner for the scatter kernels (P2G and its adjoint's scatter half; the batching
  * scheme these shapes belong to has no counterpart in the paper).  On the context's
  * current state, times P2G of every material present with each shared-box capacity the

@@ -94,9 +94,25 @@ class Batch:
         self._keep_a = a
         return r
 
-    def backward(self, xb=None, vb=None, Cb=None, Fb=None, reward_adj=None, want_state=True):
+    @property
+    def obs_dim(self):
+        return mpm.mpm_obs_dim(self.ctx)
+
+    def observe(self):
+        """Task observation of every env's current state: [n_envs, obs_dim] (x' zero padded,
+        then the mean of x', 4 pose entries, 3 target entries)."""
+        torch = _torch()
+        out = torch.empty(self.n_envs, self.obs_dim, device=self.device)
+        mpm.mpm_observe(self.ctx, out)
+        return out
+
+    def backward(self, xb=None, vb=None, Cb=None, Fb=None, reward_adj=None, want_state=True, obs_adj=None):
+        """obs_adj: [T + 1, n_envs, obs_dim] adjoints of the observations of the recorded
+        states (row t before step t, row T the final state), or None."""
         torch = _torch()
         T = mpm.mpm_tape_length(self.ctx)
+        if obs_adj is not None:
+            mpm.mpm_set_obs_adjoint(self.ctx, self._dev(obs_adj).contiguous())
         P = self.P
         out = {"action_grad": torch.empty(T, self.n_envs, self.A, device=self.device)}
         if want_state:

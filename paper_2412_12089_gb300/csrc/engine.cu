@@ -359,9 +359,10 @@ void substeps_forward(Group& g, const Launch& L, const std::vector<MatGroup>& ma
 
 // tape: the group's grid tape (the recorded steps kept their grids there), or NULL.
 void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, const float* rbar, float* agrad,
-                  int n_tot, int a_max, const GridTape* tape) {
+                  int n_tot, int a_max, const GridTape* tape, const ObsAdj* obs) {
   launch_rev_begin(L);
   launch_reward_adj(L, rbar, n_tot);
+  if (obs) launch_obs_adj(L, *obs, 0);  // observation of the step's end state
   launch_adj_ref(L);
   // recompute substep states 1..S-1 into the ring (envs with S > k + 1); the grid of each
   // substep comes from the tape when it was kept, else P2G rebuilds it
@@ -473,17 +474,19 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
   }
 }
 
-void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env) {
+void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env,
+                     const ObsAdj* obs) {
   if (g.n_envs == 0) return;
   if (!per_env) {
-    reverse_step(group_launch(g, st), g.mats, g.S_max, rbar, agrad, n_tot, a_max, g.tape.cap > 0 ? &g.tape : nullptr);
+    reverse_step(group_launch(g, st), g.mats, g.S_max, rbar, agrad, n_tot, a_max, g.tape.cap > 0 ? &g.tape : nullptr,
+                 obs);
     return;
   }
   for (int e = 0; e < g.n_envs; ++e) {
     const int S = g.spec[e].substeps;
     std::vector<MatGroup> one{{g.spec[e].material, g.env_item0[e], std::vector<int>(S + 1, g.env_nitems[e])}};
     one[0].n_gt[S] = 0;
-    reverse_step(env_launch(g, e, st), one, S, rbar, agrad, n_tot, a_max, nullptr);
+    reverse_step(env_launch(g, e, st), one, S, rbar, agrad, n_tot, a_max, nullptr, obs);
   }
 }
 

@@ -89,6 +89,8 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
 // the state is unchanged.  ms[m][b]: mean time of material group m with capacity b.
 cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, std::vector<std::vector<float>>* ms);
 // One reverse control step of every environment (step index from the device counters).
-void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env);
+// obs: adjoints of the task observations at the step boundaries, or NULL.
+void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env,
+                     const ObsAdj* obs = nullptr);
 
 }  // namespace mpm

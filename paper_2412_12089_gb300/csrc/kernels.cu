@@ -1652,6 +1652,77 @@ __global__ void k_adj_out(const EnvDesc* __restrict__ envs, const WorkItem* __re
   }
 }
 
+// ------------------------------------------------------------------ observations
+
+// One CTA per env: the observation of the live state (row layout in kernels.h).
+__global__ void __launch_bounds__(256) k_observe(const EnvDesc* __restrict__ envs, int env0, float* obs, int dim,
+                                                 int nsub_max) {
+  __shared__ float sh[32];
+  const int ei = env0 + blockIdx.x;
+  const EnvDesc& e = envs[ei];
+  const EnvCtr c = *e.ctr;
+  const float* b = e.slots + (long long)c.live * e.block;
+  const long long np = e.n_pad;
+  const unsigned* meta = reinterpret_cast<const unsigned*>(b + kComp * np);
+  const int ns = min(e.n_sub, e.n);
+  float* row = obs + (long long)ei * dim;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  for (int i = threadIdx.x; i < e.n; i += blockDim.x) {
+    const int id = (int)(meta[i] & kIdMask);
+    if (id < ns) {
+      const float x0 = b[i], x1 = b[np + i], x2 = b[2 * np + i];
+      row[3 * id] = x0;
+      row[3 * id + 1] = x1;
+      row[3 * id + 2] = x2;
+      s0 += x0;
+      s1 += x1;
+      s2 += x2;
+    }
+  }
+  for (int q = 3 * ns + threadIdx.x; q < 3 * nsub_max; q += blockDim.x) row[q] = 0.f;
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    float* tail = row + 3 * nsub_max;
+    const float inv = ns > 0 ? 1.0f / (float)ns : 0.0f;
+    tail[0] = s0 * inv;
+    tail[1] = s1 * inv;
+    tail[2] = s2 * inv;
+    for (int j = 0; j < 4; ++j) tail[3 + j] = j < e.n_coll_act ? e.pose[c.live * 4 + e.act_map[j]] : 0.0f;
+    for (int k = 0; k < 3; ++k) tail[7 + k] = e.reward_kind == 2 ? e.rparam[k] : 0.0f;
+  }
+}
+
+// One CTA per env: adds the adjoint of an observation to the state adjoint (x' and its mean)
+// and to the pose adjoint (the action-driven components).
+__global__ void __launch_bounds__(256) k_obs_adj(const EnvDesc* __restrict__ envs, int env0, ObsAdj o, int which) {
+  if (*o.on == 0) return;
+  const int ei = env0 + blockIdx.x;
+  const EnvDesc& e = envs[ei];
+  const EnvCtr c = *e.ctr;
+  const int row_t = which == 0 ? c.rev + 1 : c.rev;
+  const float* b = e.slots + (long long)(c.base + row_t) * e.block;
+  float* adj = c.par ? e.adj1 : e.adj0;
+  const long long np = e.n_pad;
+  const unsigned* meta = reinterpret_cast<const unsigned*>(b + kComp * np);
+  const int ns = min(e.n_sub, e.n);
+  const float* r = o.adj + ((long long)row_t * o.n_tot + ei) * o.dim;
+  const float* tail = r + 3 * o.nsub_max;
+  const float inv = ns > 0 ? 1.0f / (float)ns : 0.0f;
+  const float m0 = tail[0] * inv, m1 = tail[1] * inv, m2 = tail[2] * inv;
+  for (int i = threadIdx.x; i < e.n; i += blockDim.x) {
+    const int id = (int)(meta[i] & kIdMask);
+    if (id < ns) {
+      adj[i] += r[3 * id] + m0;
+      adj[np + i] += r[3 * id + 1] + m1;
+      adj[2 * np + i] += r[3 * id + 2] + m2;
+    }
+  }
+  if (threadIdx.x == 0)
+    for (int j = 0; j < e.n_coll_act; ++j) e.acc[ACC_QB + e.act_map[j]] += tail[3 + j];
+}
+
 // ------------------------------------------------------------------ launchers
 
 static std::atomic<long long> g_launches{0};
@@ -1793,6 +1864,16 @@ void launch_p2g_adj(const Launch& L, StateRef src, bool use_perm, int k) {
     case MAT_FLUID: k_p2g_adj<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k); break;
     default: k_p2g_adj<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, use_perm ? 1 : 0, k); break;
   }
+}
+
+void launch_observe(const Launch& L, float* obs, int dim, int nsub_max) {
+  Timed tm_(KC_OTHER, L.stream);
+  k_observe<<<L.n_env, 256, 0, L.stream>>>(L.envs, L.env0, obs, dim, nsub_max);
+}
+
+void launch_obs_adj(const Launch& L, const ObsAdj& o, int which) {
+  Timed tm_(KC_OTHER, L.stream);
+  k_obs_adj<<<L.n_env, 256, 0, L.stream>>>(L.envs, L.env0, o, which);
 }
 
 void launch_bwd_init(const Launch& L, int T) {

@@ -85,6 +85,18 @@ void launch_reward_adj(const Launch& L, const float* rbar, int n_tot);
 void launch_adj_ref(const Launch& L);
 void launch_rev_end(const Launch& L, float* act_grad, int n_tot, int a_max);
 
+// Task observations (App. E): per env row [x' of caller particles 0..ns-1 (3 nsub_max,
+// zero padded)][their mean 3][action-driven pose components 4][reach target 3].
+struct ObsAdj {
+  const float* adj;  // [T + 1][n_tot][dim] adjoints of the observations at the step boundaries
+  const int* on;     // device flag: inject only when set
+  int dim, nsub_max, n_tot;
+};
+void launch_observe(const Launch& L, float* obs, int dim, int nsub_max);
+// which = 0: the end state of the step being reversed (row rev + 1); 1: the state before it
+// (row rev; used once after the last reverse step, for the initial state).
+void launch_obs_adj(const Launch& L, const ObsAdj& o, int which);
+
 // State I/O: caller order (AoS) <-> arena blocks.
 void launch_set_state(const Launch& L, const float* x, const float* v, const float* C, const float* F,
                       const int* group);

@@ -45,6 +45,9 @@ struct mpm_ctx {
   float* agrad = nullptr;    // [T_cap][n_envs][A_max]
   float* io = nullptr;       // [P][24] staging
   float* posebuf = nullptr;  // [n_envs][4]
+  float* obs_adj = nullptr;  // [T_cap + 1][n_envs][obs_dim] observation adjoints
+  int* obs_on = nullptr;     // device flag: obs_adj holds adjoints for the next backward
+  int obs_dim = 0, nsub_max = 0;
   size_t acc_stride = 0;
   float* acc_all = nullptr;
   EnvCtr* ctr_all = nullptr;
@@ -153,8 +156,11 @@ void body_fwd(mpm_ctx* c, cudaStream_t st, void* arg) {
   enqueue_forward(c->g, st, *(bool*)arg, c->act_in, c->A_max, c->rew, c->per_env);
 }
 
+ObsAdj obs_of(const mpm_ctx* c) { return ObsAdj{c->obs_adj, c->obs_on, c->obs_dim, c->nsub_max, c->n_envs}; }
+
 void body_rev(mpm_ctx* c, cudaStream_t st, void*) {
-  enqueue_reverse(c->g, st, c->rbar, c->agrad, c->n_envs, c->A_max, c->per_env);
+  const ObsAdj o = obs_of(c);
+  enqueue_reverse(c->g, st, c->rbar, c->agrad, c->n_envs, c->A_max, c->per_env, c->obs_adj ? &o : nullptr);
 }
 
 Launch io_launch(mpm_ctx* ctx, cudaStream_t st) {
@@ -266,7 +272,14 @@ mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* 
   if (ok && tape)
     ok = alloc((void**)&ctx->rbar, sizeof(float) * ctx->T_cap * n_envs) &&
          alloc((void**)&ctx->agrad, sizeof(float) * (size_t)ctx->T_cap * n_envs * A_max);
+  ctx->nsub_max = 0;
+  for (const auto& sp : ctx->specs) ctx->nsub_max = std::max(ctx->nsub_max, std::min(sp.n_sub, sp.n_particles));
+  ctx->obs_dim = 3 * ctx->nsub_max + 10;
+  if (ok && tape)
+    ok = alloc((void**)&ctx->obs_adj, sizeof(float) * (size_t)(ctx->T_cap + 1) * n_envs * ctx->obs_dim) &&
+         alloc((void**)&ctx->obs_on, sizeof(int));
   if (!ok) return bail(fail(ctx, MPM_ERR_OOM, "staging buffers"));
+  if (ctx->obs_on) cudaMemset(ctx->obs_on, 0, sizeof(int));
   cudaMemset(ctx->act_in, 0, sizeof(float) * n_envs * A_max);
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(fail(ctx, MPM_ERR_CUDA, "stream"));
@@ -286,7 +299,8 @@ void mpm_destroy(mpm_ctx* ctx) {
   for (auto e : ctx->ev) cudaEventDestroy(e);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   ctx->g.release();
-  void* ptrs[] = {ctx->arena, ctx->act_in, ctx->rew, ctx->rbar, ctx->agrad, ctx->io, ctx->posebuf};
+  void* ptrs[] = {ctx->arena, ctx->act_in, ctx->rew, ctx->rbar, ctx->agrad, ctx->io, ctx->posebuf, ctx->obs_adj,
+                  ctx->obs_on};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete ctx;
@@ -423,6 +437,10 @@ mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const fl
   }
   {
     Enqueue q(ctx);
+    if (ctx->obs_adj) {
+      launch_obs_adj(L, obs_of(ctx), 1);  // observation of the initial state
+      CK(cudaMemsetAsync(ctx->obs_on, 0, sizeof(int), st));  // consumed
+    }
     launch_adj_out(io_launch(ctx, st), StateRef{REF_REV, 0}, io, io + P * 3, io + P * 6, io + P * 15);
   }
   CK(cudaGetLastError());
@@ -499,6 +517,36 @@ int32_t mpm_last_active_tiles(mpm_ctx* ctx) {
   int n = -1;
   if (cudaMemcpy(&n, ctx->g.active_n, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
   return n;
+}
+
+int32_t mpm_obs_dim(const mpm_ctx* ctx) { return ctx ? ctx->obs_dim : 0; }
+
+mpm_status mpm_observe(mpm_ctx* ctx, float* obs, void* stream) {
+  if (!ctx || !obs) return MPM_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  {
+    Enqueue q(ctx);
+    launch_observe(group_launch(ctx->g, st), obs, ctx->obs_dim, ctx->nsub_max);
+  }
+  CK(cudaGetLastError());
+  return MPM_OK;
+}
+
+mpm_status mpm_set_obs_adjoint(mpm_ctx* ctx, const float* obs_adj, void* stream) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (!ctx->obs_adj) return fail(ctx, MPM_ERR_STATE, "observation adjoints need a checkpoint tape (max_steps > 0)");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int T = ctx->h_live - ctx->h_base;
+  if (!obs_adj) {
+    CK(cudaMemsetAsync(ctx->obs_on, 0, sizeof(int), st));
+    return MPM_OK;
+  }
+  CK(cudaMemcpyAsync(ctx->obs_adj, obs_adj, sizeof(float) * (size_t)(T + 1) * ctx->n_envs * ctx->obs_dim,
+                     cudaMemcpyDefault, st));
+  CK(cudaMemsetAsync(ctx->obs_on, 0x01, 1, st));
+  return MPM_OK;
 }
 
 mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* ms_out) {

@@ -98,6 +98,9 @@ def lib():
         "mpm_bin": (i32, [_P, i32, i32, _P, _P, _P]),
         "mpm_bin_static": (i32, [_P, i32, i32, _P, _P, _P]),
         "mpm_autotune": (i32, [_P, i32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_float)]),
+        "mpm_obs_dim": (i32, [_P]),
+        "mpm_observe": (i32, [_P, _P, _P]),
+        "mpm_set_obs_adjoint": (i32, [_P, _P, _P]),
         "mpm_bin_static_max": (i32, []),
         "mpm_kernel_launches": (i64, [_P]),
         "mpm_time_kernel": (i32, [_P, i32]),
@@ -280,6 +283,18 @@ def mpm_autotune(ctx, trials=3):
     chosen = {names[m]: int(box[m]) for m in range(4) if box[m]}
     times = {names[m]: (float(ms[2 * m]), float(ms[2 * m + 1])) for m in range(4) if box[m]}
     return chosen, times
+
+
+def mpm_obs_dim(ctx):
+    return lib().mpm_obs_dim(ctx)
+
+
+def mpm_observe(ctx, obs, stream=None):
+    return check(lib().mpm_observe(ctx, ptr(obs), stream_ptr(stream)), ctx=ctx)
+
+
+def mpm_set_obs_adjoint(ctx, obs_adj, stream=None):
+    return check(lib().mpm_set_obs_adjoint(ctx, ptr(obs_adj), stream_ptr(stream)), ctx=ctx)
 
 
 def mpm_tape_length(ctx):
