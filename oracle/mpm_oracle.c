@@ -569,14 +569,15 @@ static void sdf_container(const double* p, const double* dims, double* d, double
  * signed distance d (> 0 outside), outward normal n = grad d, Hessian H (world frame),
  * and the rigid body's velocity vb at xw.
  */
-void orc_collider(const orc_spec* s, const double* xw, const double* q, const double* u,
-                  double* d, double* n, double* H, double* vb)
+/* One rigid body of shape `kind` at pose q (4 entries), pose velocity u. */
+static void collider_body(const orc_spec* s, int kind, const double* xw, const double* q, const double* u,
+                          double* d, double* n, double* H, double* vb)
 {
     double ct = cos(q[3]), st = sin(q[3]);
     double r[3] = {xw[0] - q[0], xw[1] - q[1], xw[2] - q[2]};
     double p[3] = {ct * r[0] + st * r[1], -st * r[0] + ct * r[1], r[2]}; /* R(-theta) r */
     double nb[3], Hb[9];
-    switch (s->coll_kind) {
+    switch (kind) {
     case ORC_COLL_CAPSULE: sdf_capsule(p, s->coll_dims, d, nb, Hb); break;
     case ORC_COLL_BOX: sdf_box(p, s->coll_dims, d, nb, Hb); break;
     case ORC_COLL_CONTAINER: sdf_container(p, s->coll_dims, d, nb, Hb); break;
@@ -595,15 +596,52 @@ void orc_collider(const orc_spec* s, const double* xw, const double* q, const do
     vb[2] = u[2];
 }
 
-/* dd/dtheta and dn/dtheta at xw (world frame). */
-static void collider_dtheta(const orc_spec* s, const double* xw, const double* q, double* dd_dth,
+int orc_pose_len(const orc_spec* s)
+{
+    return s->coll_kind == ORC_COLL_CAPSULES ? 4 * s->n_caps : 4;
+}
+
+/* The collider at xw: a single body, or for ORC_COLL_CAPSULES the union of the capsules,
+ * i.e. the capsule nearest to xw (smallest signed distance; the first on a tie), whose index
+ * is returned in *which (0 for single bodies). */
+static void collider_pick(const orc_spec* s, const double* xw, const double* q, const double* u, double* d,
+                          double* n, double* H, double* vb, int* which)
+{
+    *which = 0;
+    if (s->coll_kind != ORC_COLL_CAPSULES) {
+        collider_body(s, s->coll_kind, xw, q, u, d, n, H, vb);
+        return;
+    }
+    collider_body(s, ORC_COLL_CAPSULE, xw, q, u, d, n, H, vb);
+    for (int j = 1; j < s->n_caps; j++) {
+        double dj, nj[3], Hj[9], vj[3];
+        collider_body(s, ORC_COLL_CAPSULE, xw, q + 4 * j, u + 4 * j, &dj, nj, Hj, vj);
+        if (dj < *d) {
+            *d = dj;
+            memcpy(n, nj, sizeof nj);
+            memcpy(H, Hj, sizeof Hj);
+            memcpy(vb, vj, sizeof vj);
+            *which = j;
+        }
+    }
+}
+
+void orc_collider(const orc_spec* s, const double* xw, const double* q, const double* u,
+                  double* d, double* n, double* H, double* vb)
+{
+    int which;
+    collider_pick(s, xw, q, u, d, n, H, vb, &which);
+}
+
+/* dd/dtheta and dn/dtheta at xw (world frame) for the body `kind` at pose q. */
+static void collider_dtheta(const orc_spec* s, int kind, const double* xw, const double* q, double* dd_dth,
                             double* dn_dth)
 {
     double ct = cos(q[3]), st = sin(q[3]);
     double r[3] = {xw[0] - q[0], xw[1] - q[1], xw[2] - q[2]};
     double p[3] = {ct * r[0] + st * r[1], -st * r[0] + ct * r[1], r[2]};
     double nb[3], Hb[9], d;
-    switch (s->coll_kind) {
+    switch (kind) {
     case ORC_COLL_CAPSULE: sdf_capsule(p, s->coll_dims, &d, nb, Hb); break;
     case ORC_COLL_BOX: sdf_box(p, s->coll_dims, &d, nb, Hb); break;
     case ORC_COLL_CONTAINER: sdf_container(p, s->coll_dims, &d, nb, Hb); break;
@@ -702,7 +740,8 @@ static void node_update(const orc_spec* s, int ix, int iy, int iz, const double*
     for (int i = 0; i < 3; i++) v[i] = gn[1 + i] / gn[0] + s->dt * s->gravity[i];
     if (s->coll_kind != ORC_COLL_NONE) {
         double xw[3] = {ix * dx, iy * dx, iz * dx}, d, nn[3], H[9], vb[3];
-        orc_collider(s, xw, q, u, &d, nn, H, vb);
+        int which;
+        collider_pick(s, xw, q, u, &d, nn, H, vb, &which);
         double sc = d > 0 ? exp(-s->alpha * d) : 1.0;
         double vr[3] = {v[0] - vb[0], v[1] - vb[1], v[2] - vb[2]};
         double vn = v3_dot(vr, nn);
@@ -830,8 +869,9 @@ static void node_update_adj(const orc_spec* s, int ix, int iy, int iz, const dou
     double xw[3] = {ix * dx, iy * dx, iz * dx}, d = 0, nn[3] = {0, 0, 1}, H[9], vb[3] = {0, 0, 0};
     double sc = 0, vr[3], vn = 0, vt[3] = {0, 0, 0}, L = 0, f = 0, vr2[3];
     int branch = 0; /* 0: separating, 1: friction f>0, 2: stopped */
+    int which = 0;  /* body whose pose the contact depends on */
     if (s->coll_kind != ORC_COLL_NONE) {
-        orc_collider(s, xw, q, u, &d, nn, H, vb);
+        collider_pick(s, xw, q, u, &d, nn, H, vb, &which);
         sc = d > 0 ? exp(-s->alpha * d) : 1.0;
         for (int i = 0; i < 3; i++) vr[i] = v1[i] - vb[i];
         vn = v3_dot(vr, nn);
@@ -934,19 +974,24 @@ static void node_update_adj(const orc_spec* s, int ix, int iy, int iz, const dou
         double db = d > 0 ? scb * (-s->alpha * sc) : 0.0;
         /* pose adjoints: dd/dc = -n, dn/dc = -H, dvb/dc via omega, and theta terms */
         double dd_dth, dn_dth[3];
-        collider_dtheta(s, xw, q, &dd_dth, dn_dth);
-        double r[3] = {xw[0] - q[0], xw[1] - q[1], xw[2] - q[2]};
+        const double* qj = q + 4 * which;
+        const double* uj = u + 4 * which;
+        double* qbj = qb + 4 * which;
+        double* ubj = ub + 4 * which;
+        collider_dtheta(s, s->coll_kind == ORC_COLL_CAPSULES ? ORC_COLL_CAPSULE : s->coll_kind, xw, qj, &dd_dth,
+                        dn_dth);
+        double r[3] = {xw[0] - qj[0], xw[1] - qj[1], xw[2] - qj[2]};
         for (int i = 0; i < 3; i++) {
             double Hn = H[3 * i] * nb[0] + H[3 * i + 1] * nb[1] + H[3 * i + 2] * nb[2];
-            qb[i] += -nn[i] * db - Hn;
+            qbj[i] += -nn[i] * db - Hn;
         }
-        qb[0] += -u[3] * vbb[1];
-        qb[1] += u[3] * vbb[0];
-        qb[3] += dd_dth * db + v3_dot(dn_dth, nb);
-        ub[0] += vbb[0];
-        ub[1] += vbb[1];
-        ub[2] += vbb[2];
-        ub[3] += -r[1] * vbb[0] + r[0] * vbb[1];
+        qbj[0] += -uj[3] * vbb[1];
+        qbj[1] += uj[3] * vbb[0];
+        qbj[3] += dd_dth * db + v3_dot(dn_dth, nb);
+        ubj[0] += vbb[0];
+        ubj[1] += vbb[1];
+        ubj[2] += vbb[2];
+        ubj[3] += -r[1] * vbb[0] + r[0] * vbb[1];
     } else {
         memcpy(v1b, v2b, sizeof v2b);
     }
@@ -1224,7 +1269,8 @@ void orc_observe(const orc_spec* s, int n, const double* x, const double* q, dou
         }
     double* tail = obs + 3 * ns;
     for (int k = 0; k < 3; k++) tail[k] = ns ? m[k] / ns : 0.0;
-    for (int j = 0; j < 4; j++) tail[3 + j] = j < s->n_coll_act ? q[s->act_map[j]] : 0.0;
+    for (int j = 0; j < 4; j++)
+        tail[3 + j] = s->coll_kind == ORC_COLL_CAPSULES ? q[j] : (j < s->n_coll_act ? q[s->act_map[j]] : 0.0);
     for (int k = 0; k < 3; k++) tail[7 + k] = s->reward_kind == ORC_REWARD_REACH ? s->rparam[k] : 0.0;
 }
 
@@ -1235,16 +1281,26 @@ static void observe_adj(const orc_spec* s, int n, const double* ob, double* xb, 
     const double* tail = ob + 3 * ns;
     for (int p = 0; p < ns; p++)
         for (int k = 0; k < 3; k++) xb[3 * p + k] += ob[3 * p + k] + tail[k] / ns;
-    for (int j = 0; j < s->n_coll_act; j++) qb[s->act_map[j]] += tail[3 + j];
+    if (s->coll_kind == ORC_COLL_CAPSULES) {
+        for (int j = 0; j < 4; j++) qb[j] += tail[3 + j];
+    } else {
+        for (int j = 0; j < s->n_coll_act; j++) qb[s->act_map[j]] += tail[3 + j];
+    }
 }
 
 /* ------------------------------------------------------------------ rollouts */
 
+/* Pose velocity over a control step: the step's relative pose change per unit time. */
 static void pose_velocity(const orc_spec* s, const double* a, double* u)
 {
     double h = s->S * s->dt;
-    u[0] = u[1] = u[2] = u[3] = 0.0;
-    for (int j = 0; j < s->n_coll_act; j++) u[s->act_map[j]] += s->act_scale[j] * a[j] / h;
+    int pl = orc_pose_len(s);
+    for (int i = 0; i < pl; i++) u[i] = 0.0;
+    if (s->coll_kind == ORC_COLL_CAPSULES) {
+        for (int j = 0; j < pl; j++) u[j] = s->act_scale[j % 4] * a[j] / h;
+    } else {
+        for (int j = 0; j < s->n_coll_act; j++) u[s->act_map[j]] += s->act_scale[j] * a[j] / h;
+    }
 }
 
 int orc_rollout(const orc_spec* s, int n, double* x, double* v, double* C, double* F, const int* group,
@@ -1253,13 +1309,14 @@ int orc_rollout(const orc_spec* s, int n, double* x, double* v, double* C, doubl
     int A = s->n_coll_act + s->n_groups, status = 0;
     for (int t = 0; t < T; t++) {
         const double* a = actions + (size_t)t * A;
-        double u[4], qk[4];
+        const int pl = orc_pose_len(s);
+        double u[ORC_MAX_POSE], qk[ORC_MAX_POSE];
         pose_velocity(s, a, u);
         for (int k = 0; k < s->S; k++) {
-            for (int i = 0; i < 4; i++) qk[i] = q[i] + k * s->dt * u[i];
+            for (int i = 0; i < pl; i++) qk[i] = q[i] + k * s->dt * u[i];
             status |= orc_substep(s, n, x, v, C, F, group, qk, u, a);
         }
-        for (int i = 0; i < 4; i++) q[i] += s->S * s->dt * u[i];
+        for (int i = 0; i < pl; i++) q[i] += s->S * s->dt * u[i];
         if (rewards) rewards[t] = orc_reward(s, n, x, v, q, a);
     }
     return status;
@@ -1289,18 +1346,19 @@ int orc_rollout_adj_obs(const orc_spec* s, int n, const double* x0, const double
     size_t sx = 3 * (size_t)n, sm = 9 * (size_t)n, blk = 2 * sx + 2 * sm;
     /* checkpoints of (x, v, C, F) and pose at every control-step boundary */
     double* ck = (double*)malloc(blk * (T + 1) * sizeof(double));
-    double* qs = (double*)malloc(4 * (T + 1) * sizeof(double));
+    const int pl = orc_pose_len(s);
+    double* qs = (double*)malloc((size_t)pl * (T + 1) * sizeof(double));
     double* ring = (double*)malloc(blk * S * sizeof(double));
     memcpy(ck, x0, sx * sizeof(double));
     memcpy(ck + sx, v0, sx * sizeof(double));
     memcpy(ck + 2 * sx, C0, sm * sizeof(double));
     memcpy(ck + 2 * sx + sm, F0, sm * sizeof(double));
-    memcpy(qs, q0, 4 * sizeof(double));
+    memcpy(qs, q0, pl * sizeof(double));
     for (int t = 0; t < T; t++) {
         double* cur = ck + blk * (t + 1);
         memcpy(cur, ck + blk * t, blk * sizeof(double));
-        memcpy(qs + 4 * (t + 1), qs + 4 * t, 4 * sizeof(double));
-        status |= orc_rollout(s, n, cur, cur + sx, cur + 2 * sx, cur + 2 * sx + sm, group, qs + 4 * (t + 1),
+        memcpy(qs + pl * (t + 1), qs + pl * t, pl * sizeof(double));
+        status |= orc_rollout(s, n, cur, cur + sx, cur + 2 * sx, cur + 2 * sx + sm, group, qs + pl * (t + 1),
                               actions + (size_t)t * A, 1, NULL);
     }
     /* adjoint state */
@@ -1312,7 +1370,8 @@ int orc_rollout_adj_obs(const orc_spec* s, int n, const double* x0, const double
         Cb0[i] = CbT ? CbT[i] : 0.0;
         Fb0[i] = FbT ? FbT[i] : 0.0;
     }
-    double qb[4] = {0, 0, 0, 0};
+    double qb[ORC_MAX_POSE];
+    for (int i = 0; i < ORC_MAX_POSE; i++) qb[i] = 0.0;
     for (int t = T - 1; t >= 0; t--) {
         const double* a = actions + (size_t)t * A;
         double* ag = act_grad + (size_t)t * A;
@@ -1320,41 +1379,48 @@ int orc_rollout_adj_obs(const orc_spec* s, int n, const double* x0, const double
         double* end = ck + blk * (t + 1);
         /* reward of step t, from the end state and end pose */
         if (rbar && rbar[t] != 0.0)
-            orc_reward_adj(s, n, end, end + sx, qs + 4 * (t + 1), a, rbar[t], xb0, vb0, qb, ag);
+            orc_reward_adj(s, n, end, end + sx, qs + pl * (t + 1), a, rbar[t], xb0, vb0, qb, ag);
         /* observation of the end state */
         if (obs_adj) observe_adj(s, n, obs_adj + (size_t)(t + 1) * od, xb0, qb);
         /* recompute substep states s_0..s_{S-1} of step t */
-        double u[4];
+        double u[ORC_MAX_POSE];
         pose_velocity(s, a, u);
         memcpy(ring, ck + blk * t, blk * sizeof(double));
         for (int k = 0; k + 1 < S; k++) {
             double* nx = ring + blk * (k + 1);
             memcpy(nx, ring + blk * k, blk * sizeof(double));
-            double qk[4];
-            for (int i = 0; i < 4; i++) qk[i] = qs[4 * t + i] + k * s->dt * u[i];
+            double qk[ORC_MAX_POSE];
+            for (int i = 0; i < pl; i++) qk[i] = qs[pl * t + i] + k * s->dt * u[i];
             orc_substep(s, n, nx, nx + sx, nx + 2 * sx, nx + 2 * sx + sm, group, qk, u, a);
         }
         /* q_{t+1} = q_t + h u: dL/du += h qb_{t+1}; dL/dq_t = qb_{t+1} + sum_k dL/dq_k */
         double h = S * s->dt;
-        double ub[4];
-        for (int i = 0; i < 4; i++) ub[i] = h * qb[i];
+        double ub[ORC_MAX_POSE];
+        for (int i = 0; i < pl; i++) ub[i] = h * qb[i];
         for (int k = S - 1; k >= 0; k--) {
             double* st = ring + blk * k;
-            double qk[4], qkb[4] = {0, 0, 0, 0};
-            for (int i = 0; i < 4; i++) qk[i] = qs[4 * t + i] + k * s->dt * u[i];
+            double qk[ORC_MAX_POSE], qkb[ORC_MAX_POSE];
+            for (int i = 0; i < pl; i++) {
+                qk[i] = qs[pl * t + i] + k * s->dt * u[i];
+                qkb[i] = 0.0;
+            }
             orc_substep_adj(s, n, st, st + sx, st + 2 * sx, st + 2 * sx + sm, group, qk, u, a, xb0, vb0, Cb0,
                             Fb0, qkb, ub, ag);
             /* q_k = q_t + k dt u */
-            for (int i = 0; i < 4; i++) {
+            for (int i = 0; i < pl; i++) {
                 qb[i] += qkb[i];
                 ub[i] += k * s->dt * qkb[i];
             }
         }
-        /* u[map[j]] += act_scale[j] a[j] / h */
-        for (int j = 0; j < s->n_coll_act; j++) ag[j] += ub[s->act_map[j]] * s->act_scale[j] / h;
+        /* u[map[j]] += act_scale[j] a[j] / h (capsules: u[j] = act_scale[j % 4] a[j] / h) */
+        if (s->coll_kind == ORC_COLL_CAPSULES) {
+            for (int j = 0; j < pl; j++) ag[j] += ub[j] * s->act_scale[j % 4] / h;
+        } else {
+            for (int j = 0; j < s->n_coll_act; j++) ag[j] += ub[s->act_map[j]] * s->act_scale[j] / h;
+        }
     }
     if (obs_adj) observe_adj(s, n, obs_adj, xb0, qb); /* observation of the initial state */
-    memcpy(qb0, qb, sizeof qb);
+    memcpy(qb0, qb, pl * sizeof(double));
     free(ck);
     free(qs);
     free(ring);

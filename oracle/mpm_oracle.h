@@ -33,7 +33,8 @@ extern "C" {
 #endif
 
 enum { ORC_NEOHOOKEAN = 0, ORC_VONMISES = 1, ORC_FLUID = 2, ORC_MUSCLE = 3 };
-enum { ORC_COLL_NONE = 0, ORC_COLL_CAPSULE = 1, ORC_COLL_BOX = 2, ORC_COLL_CONTAINER = 3 };
+enum { ORC_COLL_NONE = 0, ORC_COLL_CAPSULE = 1, ORC_COLL_BOX = 2, ORC_COLL_CONTAINER = 3, ORC_COLL_CAPSULES = 4 };
+enum { ORC_MAX_CAPS = 8, ORC_MAX_POSE = 4 * ORC_MAX_CAPS };
 enum { ORC_REWARD_NONE = 0, ORC_REWARD_FLAT = 1, ORC_REWARD_REACH = 2, ORC_REWARD_JUMP = 3 };
 enum { ORC_ST_DOMAIN = 1, ORC_ST_NAN = 2, ORC_ST_INVERTED = 4 };
 
@@ -62,6 +63,10 @@ typedef struct {
     double act_scale[4];        /* pose change per unit action per control step */
     double ground_mu;           /* friction of the bottom wall (0: free slip) */
     double rparam[4];           /* reward parameters */
+    int n_caps;                 /* ORC_COLL_CAPSULES: capsules (1..8), all of coll_dims; the
+                                   pose vector holds 4 entries per capsule, capsule j's four
+                                   actions (4j..4j+3) move its (c, theta) by act_scale[0..3] */
+    double cap_offset[3];       /* initial position of capsule j: pose0 + j * cap_offset */
 } orc_spec;
 
 /* ---- building blocks (exported for the pin tests) ---- */
@@ -73,6 +78,8 @@ void   orc_project(const orc_spec* s, const double* Ft, double* Fo);
 void   orc_project_vjp(const orc_spec* s, const double* Ft, const double* Fob, double* Ftb);
 void   orc_collider(const orc_spec* s, const double* xw, const double* q, const double* u,
                     double* d, double* n, double* H, double* vb);
+/* Entries of the pose vector: 4, or 4 per capsule for ORC_COLL_CAPSULES. */
+int    orc_pose_len(const orc_spec* s);
 void   orc_weights(double fx, double* w, double* dw);
 
 /* P2G into a dense grid g[G^3*4] = (m, p_x, p_y, p_z) per node, node index

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libmpm_oracle.so")
 SRC = os.path.join(HERE, "mpm_oracle.c")
 
 MAT = {"neohookean": 0, "vonmises": 1, "fluid": 2, "muscle": 3}
-COLL = {"none": 0, "capsule": 1, "box": 2, "container": 3}
+COLL = {"none": 0, "capsule": 1, "box": 2, "container": 3, "capsules": 4}
 REWARD = {"none": 0, "flat": 1, "reach": 2, "jump": 3}
 
 
@@ -49,7 +49,8 @@ class OrcSpec(ct.Structure):
         ("yield_stress", ct.c_double), ("c_y", ct.c_double), ("bulk", ct.c_double),
         ("visc", ct.c_double), ("act_stress", ct.c_double), ("coll_dims", ct.c_double * 4),
         ("coll_mu", ct.c_double), ("alpha", ct.c_double), ("act_scale", ct.c_double * 4),
-        ("ground_mu", ct.c_double), ("rparam", ct.c_double * 4),
+        ("ground_mu", ct.c_double), ("rparam", ct.c_double * 4), ("n_caps", ct.c_int),
+        ("cap_offset", ct.c_double * 3),
     ]
 
 
@@ -121,7 +122,10 @@ def make_spec(es) -> OrcSpec:
     s.G, s.S, s.bound = es.grid_res, es.substeps, es.bound
     s.material = MAT[es.material]
     s.coll_kind = COLL[es.collider]
-    s.n_coll_act = len(es.act_map)
+    s.n_coll_act = 4 * es.n_caps if es.collider == "capsules" else len(es.act_map)
+    s.n_caps = es.n_caps if es.collider == "capsules" else 0
+    for i in range(3):
+        s.cap_offset[i] = es.cap_offset[i]
     for j in range(4):
         s.act_map[j] = es.act_map[j] if j < len(es.act_map) else 0
         s.act_scale[j] = es.act_scale[j] if j < len(es.act_scale) else 0.0
@@ -141,6 +145,21 @@ def make_spec(es) -> OrcSpec:
     s.bulk, s.visc, s.act_stress = es.bulk, es.visc, es.act_stress
     s.coll_mu, s.alpha, s.ground_mu = es.coll_mu, es.alpha, es.ground_mu
     return s
+
+
+def pose_len(spec):
+    """Entries of the pose vector: 4, or 4 per capsule for the multi-capsule collider."""
+    return 4 * spec.n_caps if spec.coll_kind == COLL["capsules"] else 4
+
+
+def initial_pose(es):
+    """Initial pose vector of an EnvSpec: pose0, or for the multi-capsule collider capsule j
+    at pose0 + j * cap_offset (same angle)."""
+    p0 = np.asarray(es.pose0, np.float64)
+    if es.collider != "capsules":
+        return p0.copy()
+    return np.concatenate([p0 + np.array([*(j * np.asarray(es.cap_offset, np.float64)), 0.0])
+                           for j in range(es.n_caps)])
 
 
 class State:
@@ -212,8 +231,10 @@ def project_vjp(spec, Ft, Fob):
     return out
 
 
-def collider(spec, xw, q, u=(0, 0, 0, 0)):
-    xw, q, u = _arr(xw, (3,)), _arr(q, (4,)), _arr(u, (4,))
+def collider(spec, xw, q, u=None):
+    pl = pose_len(spec)
+    xw, q = _arr(xw, (3,)), _arr(q, (pl,))
+    u = np.zeros(pl) if u is None else _arr(u, (pl,))
     d, n, H, vb = np.zeros(1), np.zeros(3), np.zeros((3, 3)), np.zeros(3)
     lib().orc_collider(ct.byref(spec), _d(xw), _d(q), _d(u), _d(d), _d(n), _d(H), _d(vb))
     return d[0], n, H, vb
@@ -233,10 +254,12 @@ def p2g(spec, st: State, act=None):
     return g, status
 
 
-def grid_update(spec, g, q=(0, 0, 0, 0), u=(0, 0, 0, 0)):
+def grid_update(spec, g, q=None, u=None):
     G = spec.G
+    pl = pose_len(spec)
     g = _arr(g, (G, G, G, 4))
-    q, u = _arr(q, (4,)), _arr(u, (4,))
+    q = np.zeros(pl) if q is None else _arr(q, (pl,))
+    u = np.zeros(pl) if u is None else _arr(u, (pl,))
     gv = np.zeros((G, G, G, 3))
     lib().orc_grid_update(ct.byref(spec), _d(g), _d(q), _d(u), _d(gv))
     return gv
@@ -255,35 +278,41 @@ def g2p(spec, st: State, gv):
 def pose_velocity(es, a):
     """Pose velocity u for one control step (relative-pose actions, held over the step)."""
     h = es.substeps * es.dt
+    if es.collider == "capsules":
+        return np.array([es.act_scale[j % 4] * a[j] / h for j in range(4 * es.n_caps)])
     u = np.zeros(4)
     for j, m in enumerate(es.act_map):
         u[m] += es.act_scale[j] * a[j] / h
     return u
 
 
-def substep(spec, st: State, q=(0, 0, 0, 0), u=(0, 0, 0, 0), act=None):
+def substep(spec, st: State, q=None, u=None, act=None):
     out = st.copy()
-    q, u = _arr(q, (4,)), _arr(u, (4,))
+    pl = pose_len(spec)
+    q = np.zeros(pl) if q is None else _arr(q, (pl,))
+    u = np.zeros(pl) if u is None else _arr(u, (pl,))
     a = _arr(np.zeros(1) if act is None else act)
     status = lib().orc_substep(ct.byref(spec), out.n, _d(out.x), _d(out.v), _d(out.C), _d(out.F), _gp(out.group),
                                _d(q), _d(u), _d(a))
     return out, status
 
 
-def substep_adj(spec, st: State, adj_end, q=(0, 0, 0, 0), u=(0, 0, 0, 0), act=None, n_act=1):
+def substep_adj(spec, st: State, adj_end, q=None, u=None, act=None, n_act=1):
     """Adjoint of one substep.  adj_end = (xb, vb, Cb, Fb) of the end state.  Returns the
-    adjoint of the start state, dL/dq (4), dL/du through the body velocity (4), dL/dact."""
+    adjoint of the start state, dL/dq, dL/du through the body velocity (pose vectors), dL/dact."""
     xb, vb, Cb, Fb = [_arr(a).copy() for a in adj_end]
-    q, u = _arr(q, (4,)), _arr(u, (4,))
+    pl = pose_len(spec)
+    q = np.zeros(pl) if q is None else _arr(q, (pl,))
+    u = np.zeros(pl) if u is None else _arr(u, (pl,))
     a = _arr(np.zeros(max(1, n_act)) if act is None else act)
-    qb, ub, ab = np.zeros(4), np.zeros(4), np.zeros(a.size)
+    qb, ub, ab = np.zeros(pl), np.zeros(pl), np.zeros(a.size)
     lib().orc_substep_adj(ct.byref(spec), st.n, _d(st.x), _d(st.v), _d(st.C), _d(st.F), _gp(st.group), _d(q), _d(u),
                           _d(a), _d(xb), _d(vb), _d(Cb), _d(Fb), _d(qb), _d(ub), _d(ab))
     return (xb.reshape(-1, 3), vb.reshape(-1, 3), Cb.reshape(-1, 3, 3), Fb.reshape(-1, 3, 3)), qb, ub, ab
 
 
 def reward(spec, st: State, q, a):
-    q, a = _arr(q, (4,)), _arr(a)
+    q, a = _arr(q, (pose_len(spec),)), _arr(a)
     return lib().orc_reward(ct.byref(spec), st.n, _d(st.x), _d(st.v), _d(q), _d(a))
 
 
@@ -292,7 +321,7 @@ def rollout(spec, st: State, q0, actions):
     actions = _arr(actions)
     T = actions.shape[0]
     out = st.copy()
-    q = _arr(q0, (4,)).copy()
+    q = _arr(q0, (pose_len(spec),)).copy()
     rew = np.zeros(T)
     status = lib().orc_rollout(ct.byref(spec), out.n, _d(out.x), _d(out.v), _d(out.C), _d(out.F), _gp(out.group),
                                _d(q), _d(actions), T, _d(rew))
@@ -306,7 +335,7 @@ def rollout_adj(spec, st: State, q0, actions, adj_final=None, rbar=None, obs_adj
     actions = _arr(actions)
     T, A = actions.shape
     n = st.n
-    q0 = _arr(q0, (4,))
+    q0 = _arr(q0, (pose_len(spec),))
     null = ct.cast(None, _D)
     fin = [null] * 4
     keep = []
@@ -323,7 +352,7 @@ def rollout_adj(spec, st: State, q0, actions, adj_final=None, rbar=None, obs_adj
         rb = _d(rbar)
     ag = np.zeros((T, A))
     xb, vb, Cb, Fb = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3, 3)), np.zeros((n, 3, 3))
-    qb = np.zeros(4)
+    qb = np.zeros(pose_len(spec))
     ob = null
     if obs_adj is not None:
         obs_adj = _arr(obs_adj)
@@ -348,7 +377,7 @@ def observe(spec, x, q):
     x = _arr(x)
     n = x.shape[0]
     out = np.zeros(obs_dim(spec, n))
-    lib().orc_observe(ct.byref(spec), n, _d(x), _d(_arr(q, (4,))), _d(out))
+    lib().orc_observe(ct.byref(spec), n, _d(x), _d(_arr(q, (pose_len(spec),))), _d(out))
     return out
 
 

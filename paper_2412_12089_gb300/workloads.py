@@ -20,7 +20,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 MATERIALS = ("neohookean", "vonmises", "fluid", "muscle")
-COLLIDERS = ("none", "capsule", "box", "container")
+COLLIDERS = ("none", "capsule", "box", "container", "capsules")
 REWARDS = ("none", "flat", "reach", "jump")
 
 
@@ -56,6 +56,8 @@ class EnvSpec:
     n_sub: int = 250
     rparam: tuple = (0.0, 0.0, 0.0, 0.0)
     pose0: tuple = (0.0, 0.0, 0.0, 0.0)
+    n_caps: int = 0                       # collider "capsules": capsules of coll_dims (1..8)
+    cap_offset: tuple = (0.0, 0.0, 0.0)   # initial position of capsule j: pose0 + j * cap_offset
 
     def __post_init__(self):
         # Every real-valued input is made FP32-representable, so the FP32 CUDA path and the
@@ -68,8 +70,13 @@ class EnvSpec:
                 object.__setattr__(self, f.name, tuple(float(np.float32(a)) for a in v))
 
     @property
+    def n_coll_act(self) -> int:
+        """Actions that move the collider (4 per capsule for the multi-capsule collider)."""
+        return 4 * self.n_caps if self.collider == "capsules" else len(self.act_map)
+
+    @property
     def action_dim(self) -> int:
-        return len(self.act_map) + self.n_groups
+        return self.n_coll_act + self.n_groups
 
     def replace(self, **kw) -> "EnvSpec":
         return dataclasses.replace(self, **kw)

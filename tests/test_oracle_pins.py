@@ -691,3 +691,96 @@ def test_observation_adjoint_fd(name):
         e[i] = h
         fd = (loss(st, qq=q0 + e) - loss(st, qq=q0 - e)) / (2 * h)
         assert close(fd, qb[i], np.abs(qb).max()), (i, fd, qb[i])
+
+
+# ------------------------------------------------------------------ multi-capsule collider
+
+def _caps_spec(n_caps=3, **kw):
+    base = dict(G=8, dt=2e-3, bound=2, collider="capsules", n_caps=n_caps, coll_dims=(0.06, 0.1, 0, 0),
+                cap_offset=(0.0, 0.13, 0.0), act_scale=(0.01, 0.01, 0.01, 0.05), coll_mu=0.4, substeps=3,
+                pose0=(0.5031, 0.3667, 0.4043, 0.1))
+    base.update(kw)
+    return base
+
+
+def test_capsule_union_is_nearest_capsule():
+    """The union of capsules answers like the nearest single capsule (distance, normal,
+    Hessian, body velocity), and one capsule is the single-capsule collider."""
+    rng = np.random.default_rng(51)
+    es = wl.EnvSpec(n_particles=1, grid_res=8, substeps=1, dt=1e-4, **{k: v for k, v in _caps_spec().items()
+                                                                        if k not in ("G", "dt", "substeps")})
+    sp = orc.make_spec(es)
+    one = spec_for(collider="capsule", coll_dims=(0.06, 0.1, 0, 0))
+    q = orc.initial_pose(es) + 0.01 * rng.standard_normal(12)
+    u = rng.standard_normal(12)
+    for _ in range(40):
+        xw = 0.3 + 0.4 * rng.random(3)
+        d, n, H, vb = orc.collider(sp, xw, q, u)
+        singles = [orc.collider(one, xw, q[4 * j:4 * j + 4], u[4 * j:4 * j + 4]) for j in range(3)]
+        j = int(np.argmin([t[0] for t in singles]))
+        assert d == singles[j][0]
+        assert np.array_equal(n, singles[j][1]) and np.array_equal(H, singles[j][2])
+        assert np.array_equal(vb, singles[j][3])
+    # n_caps = 1 rollout equals the single-capsule rollout
+    kw = _caps_spec(n_caps=1)
+    es1 = wl.EnvSpec(n_particles=10, grid_res=8, substeps=3, dt=2e-3, **{k: v for k, v in kw.items()
+                                                                         if k not in ("G", "dt", "substeps")})
+    esc = es1.replace(collider="capsule", n_caps=0, act_map=(0, 1, 2, 3))
+    st = _rand_state(10, 8, rng, lo=0.3, hi=0.7, vs=0.5)
+    acts = rng.uniform(-1, 1, (2, 4))
+    a1, q1, r1, _ = orc.rollout(orc.make_spec(es1), st, orc.initial_pose(es1), acts)
+    a2, q2, r2, _ = orc.rollout(orc.make_spec(esc), st, np.array(esc.pose0, np.float64), acts)
+    assert np.array_equal(a1.x, a2.x) and np.array_equal(q1, q2)
+
+
+def test_capsules_rollout_adjoint_fd():
+    """Checkpointed reverse with three independently driven capsules (12 collider actions per
+    step, a 12-entry pose): action, initial-state and initial-pose gradients against central
+    differences."""
+    rng = np.random.default_rng(53)
+    kw = _caps_spec()
+    es = wl.EnvSpec(n_particles=10, grid_res=8, substeps=3, dt=2e-3, material="neohookean", E=1e4, nu=0.3,
+                    rho=1e3, p_vol=1e-6, reward="flat", n_sub=6, rparam=(0.3, 0, 0, 0),
+                    **{k: v for k, v in kw.items() if k not in ("G", "dt", "substeps")})
+    sp = orc.make_spec(es)
+    st = _rand_state(10, 8, rng, lo=0.3, hi=0.7, vs=0.5)
+    q0 = orc.initial_pose(es)
+    T, A = 2, 12
+    acts = rng.uniform(-1, 1, (T, A))
+    rbar = rng.standard_normal(T)
+    xw = rng.standard_normal((10, 3))
+
+    def loss(s, qq=q0, aa=acts):
+        o, _, rw, _ = orc.rollout(sp, s, qq, aa)
+        return (rw * rbar).sum() + (o.x * xw).sum()
+
+    ag, (xb, vb, Cb, Fb), qb = orc.rollout_adj(sp, st, q0, acts, adj_final=(xw, None, None, None), rbar=rbar)
+    assert qb.shape == (12,) and np.abs(ag).max() > 0
+    h = 1e-6
+    noise = 1e-14 * (abs(loss(st)) + 1.0) / h
+
+    def close(fd, ad, ref):
+        return abs(fd - ad) <= 1e-5 * (abs(fd) + 1e-2 * ref) + noise
+
+    for t in range(T):
+        for j in range(A):
+            ap, am = acts.copy(), acts.copy()
+            ap[t, j] += h
+            am[t, j] -= h
+            fd = (loss(st, aa=ap) - loss(st, aa=am)) / (2 * h)
+            assert close(fd, ag[t, j], np.abs(ag).max()), (t, j, fd, ag[t, j])
+    for k, g in enumerate((xb, vb, Cb, Fb)):
+        for _ in range(3):
+            idx = tuple(rng.integers(0, d) for d in g.shape)
+            sp_, sm_ = st.copy(), st.copy()
+            sp_.arrays()[k][idx] += h
+            sm_.arrays()[k][idx] -= h
+            fd = (loss(sp_) - loss(sm_)) / (2 * h)
+            assert close(fd, g[idx], np.abs(g).max()), (k, idx, fd, g[idx])
+    for i in range(12):
+        e = np.zeros(12)
+        e[i] = h
+        fd = (loss(st, qq=q0 + e) - loss(st, qq=q0 - e)) / (2 * h)
+        assert close(fd, qb[i], np.abs(qb).max()), (i, fd, qb[i])
+    # every capsule takes part in the contact
+    assert all(np.abs(qb[4 * j:4 * j + 3]).max() > 0 for j in range(3))
