@@ -70,7 +70,8 @@ enum { MPM_MAT_NEOHOOKEAN = 0, MPM_MAT_VONMISES = 1, MPM_MAT_FLUID = 2, MPM_MAT_
  * theta = yaw about +z).  CAPSULE: axis along body x, coll_dims = (radius, half-length).
  * BOX: coll_dims = half extents.  CONTAINER: open-top box, coll_dims = (inner half-width,
  * wall thickness, inner half-height), origin at the cavity centre. */
-enum { MPM_COLL_NONE = 0, MPM_COLL_CAPSULE = 1, MPM_COLL_BOX = 2, MPM_COLL_CONTAINER = 3 };
+enum { MPM_COLL_NONE = 0, MPM_COLL_CAPSULE = 1, MPM_COLL_BOX = 2, MPM_COLL_CONTAINER = 3,
+       MPM_COLL_CAPSULES = 4 /* union of n_caps capsules of coll_dims, each driven on its own */ };
 
 /* Per-control-step rewards (App. E), on the subsample of the first n_sub particles (in
  * the caller's order).  FLAT: RollingFlat R_d + R_flat, rparam[0] = h_flat.
@@ -85,7 +86,8 @@ typedef struct {
     int32_t bound;        /* wall thickness in nodes (separating slip walls), >= 0 */
     int32_t material;     /* MPM_MAT_* */
     int32_t collider;     /* MPM_COLL_* */
-    int32_t n_coll_act;   /* 0..4 leading action entries that move the collider */
+    int32_t n_coll_act;   /* 0..4 leading action entries that move the collider (4 * n_caps for
+                             MPM_COLL_CAPSULES) */
     int32_t act_map[4];   /* pose component (0..3) that action j moves */
     int32_t n_groups;     /* muscle actuator groups; their actions follow the collider's */
     int32_t reward;       /* MPM_REWARD_* */
@@ -102,6 +104,15 @@ typedef struct {
     float ground_mu;      /* Coulomb friction of the bottom wall (0 = free slip) */
     float rparam[4];
     float pose0[4];       /* initial collider pose */
+    int32_t n_caps;       /* MPM_COLL_CAPSULES: 1..8 capsules.  Capsule j starts at pose0 + j *
+                             cap_offset (same angle); its actions are 4j..4j+3 (dx, dy, dz,
+                             dtheta per control step, scaled by act_scale[0..3]), so n_coll_act
+                             = 4 * n_caps and act_map is not used.  Pose inputs and outputs of
+                             this API stay 4-wide: poses set capsule 0 (the others follow the
+                             offsets), reads return capsule 0, pose gradients sum over capsules
+                             (the gradient with respect to pose0).  The union's contact at a
+                             node is the nearest capsule's. */
+    float cap_offset[3];
 } mpm_env_spec;
 
 typedef struct {

@@ -27,10 +27,16 @@ const char* check_spec(const mpm_env_spec& s) {
   if (s.substeps < 1 || s.substeps > 4096) return "substeps";
   if (s.bound < 0 || 2 * s.bound >= s.grid_res) return "bound";
   if (s.material < 0 || s.material > 3) return "material";
-  if (s.collider < 0 || s.collider > 3) return "collider";
-  if (s.n_coll_act < 0 || s.n_coll_act > 4) return "n_coll_act";
-  for (int j = 0; j < s.n_coll_act; ++j)
-    if (s.act_map[j] < 0 || s.act_map[j] > 3) return "act_map";
+  if (s.collider < 0 || s.collider > 4) return "collider";
+  if (s.collider == MPM_COLL_CAPSULES) {
+    if (s.n_caps < 1 || s.n_caps > kMaxCaps) return "n_caps";
+    if (s.n_coll_act != 4 * s.n_caps) return "n_coll_act";
+    if (!(s.coll_dims[0] > 0.0f) || !(s.coll_dims[1] >= 0.0f)) return "coll_dims";
+  } else {
+    if (s.n_coll_act < 0 || s.n_coll_act > 4) return "n_coll_act";
+    for (int j = 0; j < s.n_coll_act; ++j)
+      if (s.act_map[j] < 0 || s.act_map[j] > 3) return "act_map";
+  }
   if (s.n_groups < 0 || s.n_groups > 4094) return "n_groups";
   if (s.n_coll_act + s.n_groups > kMaxAct) return "action dim";
   if (s.reward < 0 || s.reward > 3) return "reward";
@@ -61,7 +67,7 @@ EnvLayout env_layout(const mpm_env_spec& s, int n_slots, bool tape, bool own, in
   L.perm = cur;  cur = align256(cur + (size_t)n_slots * n_pad * 4);
   L.grid = cur;  cur = align256(cur + (size_t)(tape ? 4 : 2) * G3 * 16);
   L.tile = cur;  cur = align256(cur + (size_t)TG3 * 4);
-  L.pose = cur;  cur = align256(cur + (size_t)n_slots * 4 * 4);
+  L.pose = cur;  cur = align256(cur + (size_t)n_slots * kPose * 4);
   L.act = cur;   cur = align256(cur + (size_t)n_slots * A * 4);
   if (own) {
     L.acc = cur;       cur = align256(cur + (size_t)(ACC_ACT + A) * 4);
@@ -74,6 +80,15 @@ EnvLayout env_layout(const mpm_env_spec& s, int n_slots, bool tape, bool own, in
   }
   L.total = cur;
   return L;
+}
+
+void initial_pose(const mpm_env_spec& s, float* q) {
+  for (int i = 0; i < kPose; ++i) q[i] = 0.0f;
+  const int bodies = s.collider == MPM_COLL_CAPSULES ? s.n_caps : 1;
+  for (int j = 0; j < bodies; ++j) {
+    for (int i = 0; i < 3; ++i) q[4 * j + i] = s.pose0[i] + (float)j * (bodies > 1 ? s.cap_offset[i] : 0.0f);
+    q[4 * j + 3] = s.pose0[3];
+  }
 }
 
 void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base, float* acc, EnvCtr* ctr) {
@@ -115,6 +130,10 @@ void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base,
   d.coll_mu = s.coll_mu;
   d.alpha = s.alpha;
   d.ground_mu = s.ground_mu;
+  if (s.collider == MPM_COLL_CAPSULES) {
+    d.n_caps = s.n_caps;
+    for (int i = 0; i < 3; ++i) d.cap_offset[i] = s.cap_offset[i];
+  }
   d.block = 25 * L.n_pad;
   const long long G3 = (long long)d.G * d.G * d.G;
   d.slots = (float*)(base + L.slots);

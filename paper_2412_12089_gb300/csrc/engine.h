@@ -34,6 +34,9 @@ struct EnvLayout {
 EnvLayout env_layout(const mpm_env_spec& s, int n_slots, bool tape, bool own, int T);
 // Parameters and buffer addresses of one environment; acc/ctr are taken from the layout when
 // it owns them, else from the given pointers.
+// The slot pose vector (kPose floats) of a fresh environment: pose0, and for the capsule union
+// capsule j at pose0 + j * cap_offset.
+void initial_pose(const mpm_env_spec& s, float* q);
 void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base, float* acc, EnvCtr* ctr);
 
 struct MatGroup {

@@ -518,15 +518,56 @@ struct NodeFwd {
   float sc, vn, L, f, gL, gf;
   float vr[3], vt[3], vr2[3];
   float dl[3];  // vr2 - vr, evaluated without cancellation
-  int branch, ground;
+  int branch, ground, which;
   unsigned zero;
   Contact ct;
 };
 
 // Forward node update; records the trace needed by its adjoint.
+// Signed distance from world point (x, y, z) to a capsule (radius R, half length hl along the
+// body x axis) at pose q.
+__device__ __forceinline__ float capsule_distance(float R, float hl, const float* q, float x, float y, float z) {
+  float st, ct;
+  sincosf(q[3], &st, &ct);
+  const float rx = x - q[0], ry = y - q[1], rz = z - q[2];
+  const float px = ct * rx + st * ry, py = -st * rx + ct * ry;
+  const float ex = px - fminf(fmaxf(px, -hl), hl);
+  return sqrtf(ex * ex + py * py + rz * rz) - R;
+}
+
+// Union of capsules: the nearest capsule to the node (smallest signed distance, the first on a
+// tie) decides the contact.  q, u hold capsule 0's pose and velocity on entry and the chosen
+// capsule's on return; ps is the slot's pose vector, kdt the substep's time since the slot.
+__device__ __forceinline__ int nearest_capsule(const EnvDesc& e, const float* ps, float kdt, float x, float y,
+                                               float z, float* q, float* u) {
+  const float R = e.coll_dims[0], hl = e.coll_dims[1];
+  float best = capsule_distance(R, hl, q, x, y, z);
+  int which = 0;
+  for (int j = 1; j < e.n_caps; ++j) {
+    float qj[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) qj[i] = ps[4 * j + i] + kdt * e.acc[ACC_U + 4 * j + i];
+    const float dj = capsule_distance(R, hl, qj, x, y, z);
+    if (dj < best) {
+      best = dj;
+      which = j;
+    }
+  }
+  if (which != 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      u[i] = e.acc[ACC_U + 4 * which + i];
+      q[i] = ps[4 * which + i] + kdt * u[i];
+    }
+  }
+  return which;
+}
+
+// q, u: the collider pose and velocity (capsule 0 for the capsule union, replaced by the
+// nearest capsule's, whose index is t.which); ps, kdt as for nearest_capsule.
 template <bool kAdj>
-__device__ __forceinline__ void node_forward(const EnvDesc& e, int ix, int iy, int iz, float4 mp, const float* q,
-                                             const float* u, NodeFwd& t) {
+__device__ __forceinline__ void node_forward(const EnvDesc& e, int ix, int iy, int iz, float4 mp, float* q, float* u,
+                                             const float* ps, float kdt, NodeFwd& t) {
   const float inv_m = 1.0f / mp.x;
   t.v0[0] = mp.y * inv_m;
   t.v0[1] = mp.z * inv_m;
@@ -536,7 +577,9 @@ __device__ __forceinline__ void node_forward(const EnvDesc& e, int ix, int iy, i
 #pragma unroll
   for (int i = 0; i < 3; ++i) t.v2[i] = t.v1[i];
   t.branch = 0;
+  t.which = 0;
   if (e.coll_kind != COLL_NONE) {
+    if (e.coll_kind == COLL_CAPSULES) t.which = nearest_capsule(e, ps, kdt, ix * e.dx, iy * e.dx, iz * e.dx, q, u);
     Coll cl;
     cl.kind = e.coll_kind;
 #pragma unroll
@@ -603,13 +646,17 @@ __device__ __forceinline__ void node_forward(const EnvDesc& e, int ix, int iy, i
   if (iz >= G - bnd && t.v3[2] > 0.0f) t.zero |= 4u;
 }
 
-__device__ __forceinline__ void step_pose(const EnvDesc& e, const EnvCtr& c, int rev, int k, float* q, float* u) {
-  const int slot = step_slot(c, rev);
+// Pose vector of the running step's slot, and the pose (q, u) of body 0 at substep k.
+__device__ __forceinline__ const float* step_pose(const EnvDesc& e, const EnvCtr& c, int rev, int k, float* q,
+                                                  float* u) {
+  const float* ps = e.pose + step_slot(c, rev) * kPose;
+  const float kdt = (float)k * e.dt;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     u[i] = e.acc[ACC_U + i];
-    q[i] = e.pose[slot * 4 + i] + (float)k * e.dt * u[i];
+    q[i] = ps[i] + kdt * u[i];
   }
+  return ps;
 }
 
 // Persistent warps over the active-tile list; one warp per 4^3 tile, two nodes per lane.
@@ -650,8 +697,9 @@ __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, 
     if (keep && lane == 0) rec.list[first + w] = at;
     const EnvDesc& e = envs[at.x];
     const EnvCtr c = *e.ctr;
-    float q[4], u[4];
-    step_pose(e, c, rev, k, q, u);
+    float q0[4], u0[4];
+    const float* ps = step_pose(e, c, rev, k, q0, u0);
+    const float kdt = (float)k * e.dt;
     const int TG = e.G >> 2;
     const int tz = at.y / (TG * TG), ty = (at.y / TG) % TG, tx = at.y % TG;
 #pragma unroll
@@ -664,7 +712,8 @@ __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, 
       float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
       if (mp.x > 0.0f) {
         NodeFwd t;
-        node_forward<false>(e, ix, iy, iz, mp, q, u, t);
+        float q[4] = {q0[0], q0[1], q0[2], q0[3]}, u[4] = {u0[0], u0[1], u0[2], u0[3]};
+        node_forward<false>(e, ix, iy, iz, mp, q, u, ps, kdt, t);
         out.x = (t.zero & 1u) ? 0.0f : t.v3[0];
         out.y = (t.zero & 2u) ? 0.0f : t.v3[1];
         out.z = (t.zero & 4u) ? 0.0f : t.v3[2];
@@ -835,8 +884,21 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
 
 // ------------------------------------------------------------------ step bookkeeping
 
+// Pose velocity of a control step, u = act_scale * a / h: entry act_map[j] from action j, or
+// for the capsule union entry j of capsule j / 4 from action j (scale act_scale[j % 4]).
+__device__ __forceinline__ void pose_velocity(const EnvDesc& e, const float* a, float* u) {
+  const float h = e.S * e.dt;
+  if (e.coll_kind == COLL_CAPSULES) {
+    for (int j = 0; j < 4 * e.n_caps; ++j) u[j] = e.act_scale[j & 3] * a[j] / h;
+    return;
+  }
+  float w[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int j = 0; j < e.n_coll_act; ++j) w[e.act_map[j]] += e.act_scale[j] * a[j] / h;
+  for (int i = 0; i < 4; ++i) u[i] = w[i];
+}
+
 // One thread per environment: choose the slot the step writes, store the step's actions,
-// compute the collider's pose velocity u = act_scale * a / h.
+// compute the collider's pose velocity.
 __global__ void k_step_begin(const EnvDesc* __restrict__ envs, int env0, int n_env, const float* act_in, int a_max,
                              int record) {
   int ei = env0 + blockIdx.x * blockDim.x + threadIdx.x;
@@ -847,10 +909,7 @@ __global__ void k_step_begin(const EnvDesc* __restrict__ envs, int env0, int n_e
   c->next = record ? live + 1 : (live == 0 ? 1 : 0);
   const float* a = e.act_env ? e.act_env + (long long)c->t * e.A : act_in + (long long)ei * a_max;
   for (int j = 0; j < e.A; ++j) e.act[(long long)live * e.A + j] = a[j];
-  const float h = e.S * e.dt;
-  float u[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int j = 0; j < e.n_coll_act; ++j) u[e.act_map[j]] += e.act_scale[j] * a[j] / h;
-  for (int i = 0; i < 4; ++i) e.acc[ACC_U + i] = u[i];
+  pose_velocity(e, a, e.acc + ACC_U);
 }
 
 __device__ __forceinline__ float block_sum(float v, float* sh) {
@@ -912,9 +971,9 @@ __global__ void __launch_bounds__(256) k_reward_end(const EnvDesc* __restrict__ 
   __syncthreads();
   if (threadIdx.x == 0) {
     const float h = e.S * e.dt;
-    float qn[4];
-    for (int i = 0; i < 4; ++i) qn[i] = e.pose[live * 4 + i] + h * e.acc[ACC_U + i];
-    for (int i = 0; i < 4; ++i) e.pose[next * 4 + i] = qn[i];
+    const int pl = pose_len(e);
+    for (int i = 0; i < pl; ++i) e.pose[next * kPose + i] = e.pose[live * kPose + i] + h * e.acc[ACC_U + i];
+    const float* qn = e.pose + next * kPose;  // body 0
     float r = 0.f;
     if (e.reward_kind == 1) {
       float d = stats[0] / e.rparam[0];
@@ -1187,8 +1246,9 @@ __global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ en
     const uint2 at = active[w];
     const EnvDesc& e = envs[at.x];
     const EnvCtr c = *e.ctr;
-    float q[4], u[4];
-    step_pose(e, c, 1, k, q, u);
+    float q0[4], u0[4];
+    const float* ps = step_pose(e, c, 1, k, q0, u0);
+    const float kdt = (float)k * e.dt;
     const int TG = e.G >> 2;
     const int tz = at.y / (TG * TG), ty = (at.y / TG) % TG, tx = at.y % TG;
     float qb[4] = {0.f, 0.f, 0.f, 0.f}, ub[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1203,11 +1263,15 @@ __global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ en
       const long long id = ((long long)iz * e.G + iy) * e.G + ix;
       const float4 mp = e.grid_mp[id];
       float4 mpb = make_float4(0.f, 0.f, 0.f, 0.f);
+      // pose adjoints of this node (capsule union: of capsule `which`)
+      float qn[4] = {0.f, 0.f, 0.f, 0.f}, un[4] = {0.f, 0.f, 0.f, 0.f};
+      int which = -1;
       if (mp.x > 0.0f) {
         // grid_vb holds sum w (v-bar' - V_ref); the full adjoint is that + V_ref m / m_p
         const float4 vd = e.grid_vb[id];
         NodeFwd t;
-        node_forward<true>(e, ix, iy, iz, mp, q, u, t);
+        float q[4] = {q0[0], q0[1], q0[2], q0[3]}, u[4] = {u0[0], u0[1], u0[2], u0[3]};
+        node_forward<true>(e, ix, iy, iz, mp, q, u, ps, kdt, t);
         const bool ident = t.zero == 0u && !t.ground && (e.coll_kind == COLL_NONE || t.sc == 0.0f);
         if (ident) {
           // the node update is the identity map on velocities here: p-bar = v-bar/m exactly,
@@ -1222,14 +1286,46 @@ __global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ en
         } else {
           const float sc = mp.x * inv_pm;
           const float4 vob = make_float4(vd.x + vref[0] * sc, vd.y + vref[1] * sc, vd.z + vref[2] * sc, 0.f);
-          node_reverse(e, ix, iy, iz, mp, q, u, t, vob, mpb, qb, ub);
+          node_reverse(e, ix, iy, iz, mp, q, u, t, vob, mpb, qn, un);
+          which = t.which;
         }
       }
       e.grid_mpb[id] = mpb;
       e.grid_mp[id] = make_float4(0.f, 0.f, 0.f, 0.f);
       e.grid_vb[id] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e.coll_kind == COLL_CAPSULES) {
+        // the nodes of a warp may touch different capsules: one warp sum per capsule present
+        unsigned present = __reduce_or_sync(0xffffffffu, which >= 0 ? 1u << which : 0u);
+        while (present) {
+          const int j = __ffs(present) - 1;
+          present &= present - 1u;
+          const bool mine = which == j;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            float a = mine ? qn[i] : 0.0f, b2 = mine ? un[i] : 0.0f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              a += __shfl_xor_sync(0xffffffffu, a, o);
+              b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+            }
+            if (lane == 0) {
+              if (a != 0.0f) {
+                atomicAdd(e.acc + ACC_QKB + 4 * j + i, a);
+                atomicAdd(e.acc + ACC_KQKB + 4 * j + i, kdt * a);
+              }
+              if (b2 != 0.0f) atomicAdd(e.acc + ACC_UB + 4 * j + i, b2);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          qb[i] += qn[i];
+          ub[i] += un[i];
+        }
+      }
     }
-    if (e.coll_kind != COLL_NONE) {
+    if (e.coll_kind != COLL_NONE && e.coll_kind != COLL_CAPSULES) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         float a = qb[i], b2 = ub[i];
@@ -1242,7 +1338,6 @@ __global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ en
         ub[i] = b2;
       }
       if (lane == 0) {
-        const float kdt = (float)k * e.dt;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           if (qb[i] != 0.0f) {
@@ -1422,7 +1517,7 @@ __global__ void k_bwd_init(const EnvDesc* __restrict__ envs, int env0, int n_env
   const EnvDesc& e = envs[ei];
   e.ctr->par = 0;
   e.ctr->rev = T;
-  for (int i = 0; i < 4; ++i) e.acc[ACC_QB + i] = 0.f;
+  for (int i = 0; i < kPose; ++i) e.acc[ACC_QB + i] = 0.f;
 }
 
 // Next step of the reverse pass: t = rev - 1; pose velocity of step t; zero accumulators.
@@ -1434,11 +1529,8 @@ __global__ void k_rev_begin(const EnvDesc* __restrict__ envs, int env0, int n_en
   const int t = c->rev - 1;
   c->rev = t;
   const int slot = c->base + t;
-  const float h = e.S * e.dt;
-  float u[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int j = 0; j < e.n_coll_act; ++j) u[e.act_map[j]] += e.act_scale[j] * e.act[(long long)slot * e.A + j] / h;
-  for (int i = 0; i < 4; ++i) {
-    e.acc[ACC_U + i] = u[i];
+  pose_velocity(e, e.act + (long long)slot * e.A, e.acc + ACC_U);
+  for (int i = 0; i < kPose; ++i) {
     e.acc[ACC_QKB + i] = 0.f;
     e.acc[ACC_KQKB + i] = 0.f;
     e.acc[ACC_UB + i] = 0.f;
@@ -1471,7 +1563,7 @@ __global__ void __launch_bounds__(256) k_reward_adj(const EnvDesc* __restrict__ 
         adj[2 * np + i] += rb * (dRd / (e.rparam[0] * ns) - 2.0f * (b[2 * np + i] - st[0]) / ns);
   } else if (e.reward_kind == 2) {
     if (threadIdx.x == 0) {
-      const float* q = e.pose + (slot + 1) * 4;
+      const float* q = e.pose + (slot + 1) * kPose;
       float d = 0.f;
       for (int i = 0; i < 3; ++i) d += (q[i] - e.rparam[i]) * (q[i] - e.rparam[i]);
       const float dRd = -2.0f * rd_factor(d, 0.02f) / ((1.f + d) * (1.f + d) * (1.f + d));
@@ -1522,9 +1614,12 @@ __global__ void k_rev_end(const EnvDesc* __restrict__ envs, int env0, int n_env,
   const EnvDesc& e = envs[ei];
   EnvCtr* c = e.ctr;
   const float h = e.S * e.dt;
-  float ub[4];
-  for (int i = 0; i < 4; ++i) {
-    ub[i] = h * e.acc[ACC_QB + i] + e.acc[ACC_KQKB + i] + e.acc[ACC_UB + i];
+  // q_k = q_t + k dt u for the step's substeps and q_{t+1} = q_t + h u: the adjoint of u is
+  // h qb_{t+1} + sum_k k dt qb_k + (through the body velocity) ub, and qb_t = qb_{t+1} + sum_k qb_k
+  const int pl = pose_len(e);
+  float* ub = e.acc + ACC_UB;
+  for (int i = 0; i < pl; ++i) {
+    ub[i] += h * e.acc[ACC_QB + i] + e.acc[ACC_KQKB + i];
     e.acc[ACC_QB + i] += e.acc[ACC_QKB + i];
   }
   float* out;
@@ -1540,7 +1635,8 @@ __global__ void k_rev_end(const EnvDesc* __restrict__ envs, int env0, int n_env,
     float g = 0.f;
     if (j < e.A) {
       g = e.acc[ACC_ACT + j];
-      if (j < e.n_coll_act) g += ub[e.act_map[j]] * e.act_scale[j] / h;
+      if (j < e.n_coll_act)
+        g += (e.coll_kind == COLL_CAPSULES ? ub[j] * e.act_scale[j & 3] : ub[e.act_map[j]] * e.act_scale[j]) / h;
     }
     out[j] = g;
   }
@@ -1689,7 +1785,9 @@ __global__ void __launch_bounds__(256) k_observe(const EnvDesc* __restrict__ env
     tail[0] = s0 * inv;
     tail[1] = s1 * inv;
     tail[2] = s2 * inv;
-    for (int j = 0; j < 4; ++j) tail[3 + j] = j < e.n_coll_act ? e.pose[c.live * 4 + e.act_map[j]] : 0.0f;
+    const float* q = e.pose + c.live * kPose;
+    for (int j = 0; j < 4; ++j)
+      tail[3 + j] = e.coll_kind == COLL_CAPSULES ? q[j] : (j < e.n_coll_act ? q[e.act_map[j]] : 0.0f);
     for (int k = 0; k < 3; ++k) tail[7 + k] = e.reward_kind == 2 ? e.rparam[k] : 0.0f;
   }
 }
@@ -1719,8 +1817,40 @@ __global__ void __launch_bounds__(256) k_obs_adj(const EnvDesc* __restrict__ env
       adj[2 * np + i] += r[3 * id + 2] + m2;
     }
   }
-  if (threadIdx.x == 0)
-    for (int j = 0; j < e.n_coll_act; ++j) e.acc[ACC_QB + e.act_map[j]] += tail[3 + j];
+  if (threadIdx.x == 0) {
+    if (e.coll_kind == COLL_CAPSULES)
+      for (int j = 0; j < 4; ++j) e.acc[ACC_QB + j] += tail[3 + j];
+    else
+      for (int j = 0; j < e.n_coll_act; ++j) e.acc[ACC_QB + e.act_map[j]] += tail[3 + j];
+  }
+}
+
+// One thread per environment: the caller's 4-wide pose <-> the slot pose vectors.
+// POSE_SET: body 0 of slot 0 from buf, capsule j at buf + j * cap_offset (same angle);
+// POSE_KEEP: slot `slot`'s pose vector to slot 0; POSE_GET: body 0 of slot `slot` to buf;
+// POSE_GRAD: the gradient with respect to the 4-wide pose (the capsules' pose adjoints summed).
+__global__ void k_pose_io(const EnvDesc* __restrict__ envs, int env0, int n_env, int mode, float* buf, int slot) {
+  const int ei = env0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (ei >= env0 + n_env) return;
+  const EnvDesc& e = envs[ei];
+  const int pl = pose_len(e);
+  float* b = buf + 4 * (long long)ei;
+  if (mode == POSE_SET) {
+    for (int j = 0; j < pl / 4; ++j) {
+      for (int i = 0; i < 3; ++i) e.pose[4 * j + i] = b[i] + (float)j * e.cap_offset[i];
+      e.pose[4 * j + 3] = b[3];
+    }
+  } else if (mode == POSE_KEEP) {
+    for (int i = 0; i < pl; ++i) e.pose[i] = e.pose[slot * kPose + i];
+  } else if (mode == POSE_GET) {
+    for (int i = 0; i < 4; ++i) b[i] = e.pose[slot * kPose + i];
+  } else {
+    for (int i = 0; i < 4; ++i) {
+      float g = 0.f;
+      for (int j = i; j < pl; j += 4) g += e.acc[ACC_QB + j];
+      b[i] = g;
+    }
+  }
 }
 
 // ------------------------------------------------------------------ launchers
@@ -1903,6 +2033,12 @@ void launch_set_state(const Launch& L, const float* x, const float* v, const flo
   if (L.n_items == 0) return;
   Timed tm_(KC_OTHER, L.stream);
   k_set_state<<<L.n_items, 256, 0, L.stream>>>(L.envs, L.items, L.item_offset, x, v, C, F, group);
+}
+
+void launch_pose_io(const Launch& L, PoseIo mode, float* buf, int slot) {
+  if (L.n_env == 0) return;
+  Timed tm_(KC_OTHER, L.stream);
+  k_pose_io<<<(L.n_env + 127) / 128, 128, 0, L.stream>>>(L.envs, L.env0, L.n_env, (int)mode, buf, slot);
 }
 
 void launch_get_state(const Launch& L, StateRef src, float* x, float* v, float* C, float* F) {

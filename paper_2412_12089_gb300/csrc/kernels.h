@@ -101,6 +101,11 @@ void launch_obs_adj(const Launch& L, const ObsAdj& o, int which);
 void launch_set_state(const Launch& L, const float* x, const float* v, const float* C, const float* F,
                       const int* group);
 void launch_get_state(const Launch& L, StateRef src, float* x, float* v, float* C, float* F);
+// The caller's pose ([n_envs][4], indexed by global env) <-> the slot pose vectors:
+// POSE_SET buf -> slot 0 (capsule j offset by j * cap_offset), POSE_KEEP slot -> slot 0,
+// POSE_GET slot body 0 -> buf, POSE_GRAD pose adjoint (summed over capsules) -> buf.
+enum PoseIo { POSE_SET = 0, POSE_KEEP = 1, POSE_GET = 2, POSE_GRAD = 3 };
+void launch_pose_io(const Launch& L, PoseIo mode, float* buf, int slot);
 void launch_adj_in(const Launch& L, const float* xb, const float* vb, const float* Cb, const float* Fb);
 void launch_adj_out(const Launch& L, StateRef src, float* xb, float* vb, float* Cb, float* Fb);
 

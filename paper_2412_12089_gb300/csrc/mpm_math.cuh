@@ -469,7 +469,7 @@ MPM_HD void project_vjp(const Mat& m, const float* Ht, const float* Hob, float* 
 
 // ------------------------------------------------------------------ colliders
 
-enum { COLL_NONE = 0, COLL_CAPSULE = 1, COLL_BOX = 2, COLL_CONTAINER = 3 };
+enum { COLL_NONE = 0, COLL_CAPSULE = 1, COLL_BOX = 2, COLL_CONTAINER = 3, COLL_CAPSULES = 4 };
 
 struct Coll {
   int kind;
@@ -505,7 +505,7 @@ MPM_HD void sdf_box(float px, float py, float pz, float hx, float hy, float hz, 
 
 // Signed distance to the collider in its body frame: d, body-frame gradient nb and Hessian Hb.
 MPM_HD void sdf_body(const Coll& c, float px, float py, float pz, float& d, float* nb, float* Hb) {
-  if (c.kind == COLL_CAPSULE) {
+  if (c.kind == COLL_CAPSULE || c.kind == COLL_CAPSULES) {
     float R = c.dims[0], hl = c.dims[1];
     float ex = px - fminf(fmaxf(px, -hl), hl);
     float l = sqrtf(ex * ex + py * py + pz * pz);

@@ -11,7 +11,7 @@
 //   perm    per slot, the binning permutation computed at that slot's step start
 //   grid_*  G^3 float4 nodes each, node (ix, iy, iz) at (iz*G + iy)*G + ix
 //   tile    (G/4)^3 activity flags, one per 4^3-node tile
-//   pose    per slot, collider pose (c, theta); act per slot, the step's actions
+//   pose    per slot, kPose floats: collider pose (c, theta) per body; act per slot, the step's actions
 //   acc     per-env accumulators of the reverse pass
 //   ctr     per-env step counters (EnvCtr)
 #pragma once
@@ -33,18 +33,24 @@ struct EnvCtr {
   int pad;
 };
 
+// Pose vector: 4 entries (c, theta) per rigid body; the multi-capsule collider has up to
+// kMaxCaps bodies.  Every slot stores kPose floats.
+constexpr int kMaxCaps = 8;
+constexpr int kPose = 4 * kMaxCaps;
+
 // Accumulator layout (floats) inside EnvDesc::acc.
 enum {
-  ACC_U = 0,      // pose velocity of the running step (4)
-  ACC_QB = 4,     // adjoint of the pose at the running step's boundary (4)
-  ACC_QKB = 8,    // sum over substeps of dL/dq_k (4)
-  ACC_KQKB = 12,  // sum over substeps of k dt dL/dq_k (4)
-  ACC_UB = 16,    // dL/du through the body velocity (4)
-  ACC_RSTAT = 20, // reward statistics of the running step (4)
-  ACC_VSUM = 24,  // reverse pass: two sums (by substep parity) over the env's particles of
-                  // the particle-velocity adjoint v-bar + dt x-bar; their mean is the reference
-                  // subtracted before the G2P^T scatter and restored node by node (2 x 4)
-  ACC_ACT = 32,   // dL/d(action) accumulated in the reverse step (A)
+  ACC_U = 0,                 // pose velocity of the running step (kPose)
+  ACC_QB = kPose,            // adjoint of the pose at the running step's boundary (kPose)
+  ACC_QKB = 2 * kPose,       // sum over substeps of dL/dq_k (kPose)
+  ACC_KQKB = 3 * kPose,      // sum over substeps of k dt dL/dq_k (kPose)
+  ACC_UB = 4 * kPose,        // dL/du through the body velocity (kPose)
+  ACC_RSTAT = 5 * kPose,     // reward statistics of the running step (4)
+  ACC_VSUM = 5 * kPose + 4,  // reverse pass: two sums (by substep parity) over the env's particles
+                             // of the particle-velocity adjoint v-bar + dt x-bar; their mean is the
+                             // reference subtracted before the G2P^T scatter and restored node by
+                             // node (2 x 4)
+  ACC_ACT = 5 * kPose + 12,  // dL/d(action) accumulated in the reverse step (A)
 };
 
 struct EnvDesc {
@@ -57,6 +63,8 @@ struct EnvDesc {
   float gravity[3];
   float mu, lam, cyl, bulk, visc, act_stress;
   float coll_dims[4], coll_mu, alpha, act_scale[4], ground_mu;
+  int n_caps;           // multi-capsule collider: capsules (pose entries 4 * n_caps), else 0
+  float cap_offset[3];  // initial position of capsule j: pose0 + j * cap_offset
   float rparam[4];
   // buffers
   float* slots;
@@ -84,6 +92,9 @@ struct EnvDesc {
   unsigned key_env;   // environment index placed in the high bits of the binning key
   int pad_;
 };
+
+// Pose entries of an environment: 4 per rigid body.
+__host__ __device__ inline int pose_len(const EnvDesc& e) { return e.coll_kind == 4 ? 4 * e.n_caps : 4; }
 
 struct WorkItem {
   int env;

@@ -249,7 +249,9 @@ mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* 
   std::vector<EnvDesc> desc(n_envs);
   for (int e = 0; e < n_envs; ++e) {
     env_fill(desc[e], ctx->specs[e], lay[e], ctx->arena + off[e], ctx->acc_all + ctx->acc_stride * e, ctx->ctr_all + e);
-    if (cudaMemcpy(desc[e].pose, ctx->specs[e].pose0, 16, cudaMemcpyHostToDevice) != cudaSuccess)
+    float q0[kPose];
+    initial_pose(ctx->specs[e], q0);
+    if (cudaMemcpy(desc[e].pose, q0, sizeof q0, cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(ctx, MPM_ERR_CUDA, "pose upload"));
   }
   // grid tape for batched reverse passes: a share of the memory left after the arena
@@ -325,12 +327,10 @@ mpm_status mpm_set_state(mpm_ctx* ctx, const float* x, const float* v, const flo
   }
   if (pose) {
     CK(cudaMemcpyAsync(ctx->posebuf, pose, sizeof(float) * 4 * ctx->n_envs, cudaMemcpyDefault, st));
-    for (int e = 0; e < ctx->n_envs; ++e)
-      CK(cudaMemcpyAsync(ctx->g.desc[e].pose, ctx->posebuf + 4 * e, 16, cudaMemcpyDeviceToDevice, st));
+    launch_pose_io(io_launch(ctx, st), POSE_SET, ctx->posebuf, 0);
   } else if (ctx->h_live != 0) {
     // keep the current pose: move it to slot 0
-    for (int e = 0; e < ctx->n_envs; ++e)
-      CK(cudaMemcpyAsync(ctx->g.desc[e].pose, ctx->g.desc[e].pose + 4 * ctx->h_live, 16, cudaMemcpyDeviceToDevice, st));
+    launch_pose_io(io_launch(ctx, st), POSE_KEEP, ctx->posebuf, ctx->h_live);
   }
   CK(cudaMemsetAsync(ctx->ctr_all, 0, sizeof(EnvCtr) * ctx->n_envs, st));
   {
@@ -358,8 +358,8 @@ mpm_status mpm_get_state(mpm_ctx* ctx, float* x, float* v, float* C, float* F, f
   if (C) CK(cudaMemcpyAsync(C, io + P * 6, sizeof(float) * P * 9, cudaMemcpyDefault, st));
   if (F) CK(cudaMemcpyAsync(F, io + P * 15, sizeof(float) * P * 9, cudaMemcpyDefault, st));
   if (pose) {
-    for (int e = 0; e < ctx->n_envs; ++e)
-      CK(cudaMemcpyAsync(ctx->posebuf + 4 * e, ctx->g.desc[e].pose + 4 * ctx->h_live, 16, cudaMemcpyDeviceToDevice, st));
+    launch_pose_io(io_launch(ctx, st), POSE_GET, ctx->posebuf, ctx->h_live);
+    CK(cudaGetLastError());
     CK(cudaMemcpyAsync(pose, ctx->posebuf, sizeof(float) * 4 * ctx->n_envs, cudaMemcpyDefault, st));
   }
   return MPM_OK;
@@ -451,9 +451,11 @@ mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const fl
   if (action_grad)
     CK(cudaMemcpyAsync(action_grad, ctx->agrad, sizeof(float) * (size_t)T * ctx->n_envs * ctx->A_max,
                        cudaMemcpyDefault, st));
-  if (pose_grad0)
-    CK(cudaMemcpy2DAsync(pose_grad0, 16, ctx->acc_all + ACC_QB, ctx->acc_stride * 4, 16, ctx->n_envs,
-                         cudaMemcpyDefault, st));
+  if (pose_grad0) {
+    launch_pose_io(io_launch(ctx, st), POSE_GRAD, ctx->posebuf, 0);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(pose_grad0, ctx->posebuf, sizeof(float) * 4 * ctx->n_envs, cudaMemcpyDefault, st));
+  }
   return MPM_OK;
 }
 

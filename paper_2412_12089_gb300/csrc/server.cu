@@ -136,7 +136,11 @@ cudaError_t admit(mpm_server* s, Req& r, Group& scratch) {
     gbuf = (int*)(io + P * kComp);
     cudaMemcpy(gbuf, r.group.data(), P * 4, cudaMemcpyHostToDevice);
   }
-  cudaMemcpy(r.desc.pose, r.spec.pose0, 16, cudaMemcpyHostToDevice);
+  {
+    float q0[kPose];
+    initial_pose(r.spec, q0);
+    cudaMemcpy(r.desc.pose, q0, sizeof q0, cudaMemcpyHostToDevice);
+  }
   if (r.A > 0) cudaMemcpy((void*)r.desc.act_env, r.actions.data(), (size_t)r.T * r.A * 4, cudaMemcpyHostToDevice);
   cudaMemcpy((void*)r.desc.rbar_env, r.rbar.data(), (size_t)r.T * 4, cudaMemcpyHostToDevice);
   // a one-environment group writes the state into slot 0

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmpm_gb300.so")
 
 MAT = {"neohookean": 0, "vonmises": 1, "fluid": 2, "muscle": 3}
-COLL = {"none": 0, "capsule": 1, "box": 2, "container": 3}
+COLL = {"none": 0, "capsule": 1, "box": 2, "container": 3, "capsules": 4}
 REWARD = {"none": 0, "flat": 1, "reach": 2, "jump": 3}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NUMERIC", 5: "DOMAIN", 6: "TIMEOUT",
           7: "NOT_READY", 8: "BUDGET", 9: "STATE"}
@@ -40,7 +40,8 @@ class MpmEnvSpec(ct.Structure):
         ("rho", ct.c_float), ("p_vol", ct.c_float), ("yield_stress", ct.c_float), ("c_y", ct.c_float),
         ("bulk", ct.c_float), ("visc", ct.c_float), ("act_stress", ct.c_float), ("coll_dims", ct.c_float * 4),
         ("coll_mu", ct.c_float), ("alpha", ct.c_float), ("act_scale", ct.c_float * 4), ("ground_mu", ct.c_float),
-        ("rparam", ct.c_float * 4), ("pose0", ct.c_float * 4),
+        ("rparam", ct.c_float * 4), ("pose0", ct.c_float * 4), ("n_caps", ct.c_int32),
+        ("cap_offset", ct.c_float * 3),
     ]
 
 
@@ -178,7 +179,10 @@ def to_c_spec(es) -> MpmEnvSpec:
     s = MpmEnvSpec()
     s.n_particles, s.grid_res, s.substeps, s.bound = es.n_particles, es.grid_res, es.substeps, es.bound
     s.material, s.collider, s.reward = MAT[es.material], COLL[es.collider], REWARD[es.reward]
-    s.n_coll_act = len(es.act_map)
+    s.n_coll_act = es.n_coll_act
+    s.n_caps = es.n_caps if es.collider == "capsules" else 0
+    for i in range(3):
+        s.cap_offset[i] = es.cap_offset[i]
     for j in range(4):
         s.act_map[j] = es.act_map[j] if j < len(es.act_map) else 0
         s.act_scale[j] = es.act_scale[j] if j < len(es.act_scale) else 0.0

@@ -275,6 +275,41 @@ def jumper(n_envs: int = 64, seed: int = 0, n: int = 100_000, G: int = 96, subst
     return Workload("jumper", specs, inits, _pad_actions(acts, T), T)
 
 
+# ----------------------------------------------------------------------------- HandFlip-like
+
+def handflip(n_envs: int = 128, seed: int = 0, n: int = 2500, G: int = 48, substeps: int = 40,
+             T: int = 16, n_caps: int = 6, action_std: float = 0.5) -> Workload:
+    """Elastoplastic slab (von Mises, E=4000, nu=0.2, sigma_y=130, rho=1) resting on a row of
+    n_caps parallel capsule fingers (radius 0.015, half-length 0.1 along x, 0.035 apart in y)
+    just above the floor; each finger is driven on its own by 4-DoF relative-pose actions
+    (dx, dy, dz, dtheta_z) ~ N(0, 0.5), 4 n_caps actions per step (24 for six fingers), with
+    dt=5e-5, 40 substeps, boundary friction 0.5 on a 48^3 grid.  The union of the capsules is
+    a synthetic stand-in for the articulated hand, whose meshes are not available."""
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / G
+    R, hl, gap = 0.015, 0.1, 0.035
+    specs, inits, acts = [], [], []
+    for e in range(n_envs):
+        off = rng.uniform(-0.03, 0.03, 2)
+        zf = 3 * dx + R + 0.37 * dx
+        y0 = 0.5 + off[1] - 0.5 * (n_caps - 1) * gap
+        size = np.array([0.14, max(0.1, (n_caps - 1) * gap), 0.04]) * rng.uniform(0.9, 1.1)
+        lo = np.array([0.5 + off[0] - size[0] / 2, 0.5 + off[1] - size[1] / 2, zf + R + 0.5 * dx])
+        hi = lo + size
+        x = _box_points(rng, n, lo, hi)
+        v = np.zeros((n, 3))
+        spec = EnvSpec(n_particles=n, grid_res=G, substeps=substeps, dt=5e-5, material="vonmises",
+                       E=4000.0, nu=0.2, rho=1.0, p_vol=float(np.prod(size)) / n, yield_stress=130.0,
+                       c_y=2.0, collider="capsules", n_caps=n_caps, coll_dims=(R, hl, 0.0, 0.0),
+                       cap_offset=(0.0, gap, 0.0), coll_mu=0.5, alpha=666.0,
+                       act_scale=(0.005, 0.005, 0.005, 0.05), ground_mu=0.5, reward="none",
+                       n_sub=min(250, n), pose0=(float(0.5 + off[0]), float(y0), float(zf), 0.0))
+        specs.append(spec)
+        inits.append(_rest_state(x, v))
+        acts.append(rng.normal(0.0, action_std, (T, 4 * n_caps)))
+    return Workload("handflip", specs, inits, _pad_actions(acts, T), T)
+
+
 def concat_inits(inits):
     """Concatenate per-env initial states in env order (particle-major arrays)."""
     return EnvInit(np.concatenate([i.x for i in inits]), np.concatenate([i.v for i in inits]),

@@ -61,5 +61,5 @@ def oracle_run(w: wl.Workload, e: int, T: int):
     st = orc.State.from_init(w.inits[e])
     A = s.action_dim
     acts = w.actions[:T, e, :max(A, 1)].astype(np.float64)
-    out, q, rew, status = orc.rollout(sp, st, np.array(s.pose0, np.float64), acts)
+    out, q, rew, status = orc.rollout(sp, st, orc.initial_pose(s), acts)
     return out, q, rew

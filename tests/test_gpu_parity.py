@@ -25,6 +25,9 @@ def small(name, seed=0, substeps=None, T=1, **kw):
                      substeps=substeps or 1, T=T)
     elif name == "fluid":
         w = wl.fluid(n_envs=kw.pop("n_envs", 2), seed=seed, n=kw.pop("n", 1500), substeps=substeps or 1, T=T)
+    elif name == "handflip":
+        w = wl.handflip(n_envs=kw.pop("n_envs", 2), seed=seed, n=kw.pop("n", 1500), substeps=substeps or 1, T=T,
+                        n_caps=kw.pop("n_caps", 6))
     elif name == "jumper":
         w = wl.jumper(n_envs=kw.pop("n_envs", 2), seed=seed, n=kw.pop("n", 3000), G=kw.pop("G", 48),
                       substeps=substeps or 1, T=T)
@@ -59,7 +62,7 @@ def test_bin_bitexact(n, G):
 
 # ------------------------------------------------------------------ one substep
 
-@pytest.mark.parametrize("name", ["cube", "dough", "fluid", "jumper"])
+@pytest.mark.parametrize("name", ["cube", "dough", "fluid", "jumper", "handflip"])
 def test_substep_parity(name):
     w = perturb(small(name, seed=1, substeps=1, T=1), seed=2)
     b, rew, st = gpu_run(w, 1)
@@ -73,7 +76,7 @@ def test_substep_parity(name):
         assert rel_err(vs, o.v) < 1e-5, (name, e, "v", rel_err(vs, o.v))
         assert rel_err(Fs, o.F) < 1e-5, (name, e, "F", rel_err(Fs, o.F))
         assert rel_err(Cs, o.C) < 1e-4, (name, e, "C", rel_err(Cs, o.C))
-        assert np.allclose(st["pose"][e], q, atol=1e-6)
+        assert np.allclose(st["pose"][e], q[:4], atol=1e-6)  # body 0
         if w.specs[e].reward != "none":
             assert abs(rew[0, e] - r[0]) <= 1e-4 * max(1.0, abs(r[0])), (name, e, rew[0, e], r[0])
     code, flags = b.check_status()
@@ -93,7 +96,7 @@ def test_cube_horizon_c1():
         assert rel_err(st[k], getattr(o, k)) < 1e-3, (k, rel_err(st[k], getattr(o, k)))
 
 
-@pytest.mark.parametrize("name,T,S", [("dough", 2, 20), ("fluid", 2, 25), ("jumper", 2, 20)])
+@pytest.mark.parametrize("name,T,S", [("dough", 2, 20), ("fluid", 2, 25), ("jumper", 2, 20), ("handflip", 2, 40)])
 def test_horizon_parity(name, T, S):
     w = small(name, seed=3, substeps=S, T=T)
     b, rew, st = gpu_run(w, T)
@@ -200,11 +203,39 @@ def test_action_gradients(name, S):
         sp = orc.make_spec(s)
         so = orc.State.from_init(w.inits[e])
         A = s.action_dim
-        ag, (xb, vb, Cb, Fb), qb = orc.rollout_adj(sp, so, np.array(s.pose0, np.float64),
+        ag, (xb, vb, Cb, Fb), qb = orc.rollout_adj(sp, so, orc.initial_pose(s),
                                                    w.actions[:T, e, :A].astype(np.float64), rbar=np.ones(T))
         assert rel_err(g["action_grad"][:, e, :A], ag) < 1e-3, (name, e, rel_err(g["action_grad"][:, e, :A], ag))
         assert rel_err(split(w, g["xb0"])[e], xb) < 1e-3, (name, e, "xb0")
+        qb = qb.reshape(-1, 4).sum(0)  # gradient with respect to pose0 (capsule j at pose0 + j offset)
         assert rel_err(g["pose_grad0"][e], qb) < 1e-3 or np.abs(qb).max() < 1e-8, (name, e, g["pose_grad0"][e], qb)
+
+
+def test_capsule_union_gradients():
+    """Six independently driven capsules (24 collider actions per step): gradients of a loss on
+    the final positions with respect to every capsule's actions, the initial state and pose0."""
+    T = 2
+    w = small("handflip", seed=12, substeps=4, T=T, n_envs=2)
+    rng = np.random.default_rng(13)
+    xw = rng.standard_normal((w.n_particles, 3)).astype(np.float32)
+    g, st = _gpu_grads(w, T, xbT=lambda xT: xw)
+    for e in range(w.n_envs):
+        s = w.specs[e]
+        sp = orc.make_spec(s)
+        so = orc.State.from_init(w.inits[e])
+        A = s.action_dim
+        assert A == 24
+        ag, (xb, vb, Cb, Fb), qb = orc.rollout_adj(sp, so, orc.initial_pose(s),
+                                                   w.actions[:T, e, :A].astype(np.float64),
+                                                   adj_final=(split(w, xw)[e].astype(np.float64), None, None, None))
+        got = g["action_grad"][:, e, :A]
+        assert rel_err(got, ag) < 1e-3, (e, rel_err(got, ag))
+        # the contact is spread over the fingers: most capsules carry a gradient
+        assert sum(np.abs(ag[:, 4 * j:4 * j + 4]).max() > 1e-6 * np.abs(ag).max() for j in range(6)) >= 4
+        for name, gg, ref in (("x", g["xb0"], xb), ("v", g["vb0"], vb), ("F", g["Fb0"], Fb)):
+            assert rel_err(split(w, gg)[e], ref) < 1e-3, (e, name, rel_err(split(w, gg)[e], ref))
+        q4 = qb.reshape(-1, 4).sum(0)
+        assert rel_err(g["pose_grad0"][e], q4) < 1e-3, (e, g["pose_grad0"][e], q4)
 
 
 @pytest.mark.parametrize("tape_tiles", [None, "1", "300"])
