@@ -205,6 +205,55 @@ def serving_leg(n_req, rate, seed):
     return out
 
 
+# App. F runtime table (RTX 4090, forward HandFlip, random actions): total env-frames/s.
+HANDFLIP_PAPER_FPS = {(128, 2500): 1569, (32, 30000): 179}
+
+
+def handflip_leg(cases, frames, warm, device):
+    """Forward-only HandFlip-like rollouts with random actions (the paper's runtime-scaling
+    setting): six driven capsule fingers under an elastoplastic slab, 48^3 grid, 40 substeps
+    of 5e-5 s per frame.  Reports total env-frames/s, particle-substeps/s and device memory
+    for (envs, particles per env) cases."""
+    import numpy as np
+    import torch
+
+    from paper_2412_12089_gb300 import mpm
+    from paper_2412_12089_gb300 import workloads as wl
+    from paper_2412_12089_gb300.batch import Batch
+
+    dev = torch.device("cuda", device)
+    out = []
+    for ne, n in cases:
+        w = wl.handflip(n_envs=ne, n=n, T=frames + warm, seed=5)
+        b = Batch(w.specs, max_steps=0, device=device)
+        try:
+            b.set_inits(w.inits)
+            acts = torch.as_tensor(w.actions).to(dev)
+            rew = torch.empty(ne, device=dev)
+            for t in range(warm):
+                b.step(acts[t], reward=rew)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for t in range(warm, warm + frames):
+                b.step(acts[t], reward=rew)
+            e1.record()
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            code, flags = b.check_status()
+            fps = ne * frames / sec
+            out.append({"envs": ne, "particles_per_env": n, "fps": fps,
+                        "particle_substeps_per_s": fps * n * w.specs[0].substeps,
+                        "device_gb": mpm.mpm_device_bytes(b.ctx) / 1e9, "frames": frames,
+                        "status_flags": int(np.count_nonzero(flags)),
+                        "paper_rtx4090_fps": HANDFLIP_PAPER_FPS.get((ne, n))})
+        finally:
+            b.close()
+    return {"workload": "handflip-like: 6 capsule fingers, von Mises slab E=4000 nu=0.2 sigma_y=130, 48^3 grid, "
+                        "40 x 5e-5 s substeps per frame, forward only, random actions N(0,0.5)",
+            "unit": "env-frames/s", "cases": out}
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -245,6 +294,7 @@ def main():
     ap.add_argument("--substeps", type=int, default=25, help="substeps per control step (small cases)")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests in the serving leg (0 = off)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate of the serving leg (1/s)")
+    ap.add_argument("--handflip-frames", type=int, default=30, help="timed frames of the HandFlip-like leg (0 = off)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -404,6 +454,10 @@ def main():
     if args.serve_requests > 0 and rank == 0:
         serve = serving_leg(args.serve_requests, args.serve_rate, seed=11)
 
+    handflip = None
+    if args.handflip_frames > 0 and rank == 0:
+        handflip = handflip_leg([(128, 2500), (32, 30000)], args.handflip_frames, 3, local)
+
     cpu = None
     if not args.no_cpu and rank == 0:
         v, dt, sample = cpu_baseline(T)
@@ -423,6 +477,7 @@ def main():
             "rollout_ms": {"p50": step_ms[len(step_ms) // 2], "p99": step_ms[-1], "what": "one batched fwd+adjoint rollout"},
             "per_env_launch": per_env,
             "serving": serve,
+            "handflip": handflip,
             "clocks": clk, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "status": int(code),
         }
