@@ -188,8 +188,9 @@ mpm_status mpm_reset_tape(mpm_ctx* ctx);
 
 /*
  * Synchronise and read the per-environment status words (bit 1: a particle left the
- * grid, bit 2: NaN/Inf, bit 4: J <= 0), accumulated since the last call, which clears
- * them.  flags: [n_envs] host array or NULL.  Returns DOMAIN / NUMERIC if any bit is set.
+ * grid, bit 2: NaN/Inf, bit 4: J <= 0, bit 8: a bounded wait on an asynchronous copy gave up
+ * and the chunk's work was skipped), accumulated since the last call, which clears them.
+ * flags: [n_envs] host array or NULL.  Returns TIMEOUT / NUMERIC / DOMAIN if a bit is set.
  */
 mpm_status mpm_check_status(mpm_ctx* ctx, int32_t* flags);
 

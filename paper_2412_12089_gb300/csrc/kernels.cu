@@ -30,6 +30,61 @@ constexpr int kBoxNodes = 2048;     // shared-memory box capacity (float4 nodes,
 
 // ------------------------------------------------------------------ common device helpers
 
+// Status bits of EnvCtr::status: 1 domain, 2 NaN/Inf, 4 inverted J, 8 a bounded wait on an
+// asynchronous copy gave up.
+constexpr int kStatusWait = 8;
+
+// ---- bulk-asynchronous staging (TMA bulk copies) of contiguous particle-component runs
+//
+// One thread issues cp.async.bulk copies of a chunk's SoA component runs into shared memory;
+// they complete on an mbarrier (transaction count = bytes), which every thread waits on.
+// A copy needs 16-byte aligned source and destination and a size that is a multiple of 16
+// bytes: chunks start at multiples of four particles, component arrays hold n_pad (a multiple
+// of 32) floats, and a run of `count` particles is rounded up to four, which stays inside the
+// array.  The wait is bounded: after kWaitLimit polls the caller sets kStatusWait and skips
+// the chunk's work.
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// The calling thread's arrival, announcing `bytes` of copies that complete on the barrier.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// Waits for the barrier's phase `parity` to complete; false after kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (int it = 0; it < kWaitLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Issue (one thread) the copies of components comps[0..n) of particles [start, start + count)
+// of block b (component stride np) into stage[q][0..], and arm the barrier with their bytes.
+template <int kN, int kStride>
+__device__ __forceinline__ void stage_components(float (*stage)[kStride], const float* b, long long np,
+                                                 const int* comps, int start, int count, unsigned long long* bar) {
+  const unsigned bytes = (unsigned)((count + 3) & ~3) * 4u;
+  mbar_arrive_expect_tx(bar, bytes * kN);
+#pragma unroll
+  for (int q = 0; q < kN; ++q) bulk_copy_g2s(stage[q], b + comps[q] * np + start, bytes, bar);
+}
+
 __device__ __forceinline__ void load_env(const EnvDesc* envs, int env, EnvDesc& s, EnvCtr& c) {
   const int* src = reinterpret_cast<const int*>(envs + env);
   int* dst = reinterpret_cast<int*>(&s);
@@ -777,13 +832,28 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
                                                 int item_off, StateRef src, StateRef dst, int use_perm, int rev) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
+  // x and H of the chunk's particles, staged by bulk copies when they are read in place
+  __shared__ alignas(16) float stage[12][kBlock * kPPT];
+  __shared__ alignas(8) unsigned long long bar;
   const WorkItem it = items[item_off + blockIdx.x];
-  load_env(envs, it.env, e, c);
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  load_env(envs, it.env, e, c);  // its barriers also publish the mbarrier's initialisation
   const float* b = ref_block(e, c, src);
   float* o = ref_block(e, c, dst);
   const int sslot = step_slot(c, rev);
   const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
   const long long np = e.n_pad;
+  const bool staged = perm == nullptr && (it.start & 3) == 0 && it.count > 0 && it.count <= kBlock * kPPT;
+  if (staged) {
+    if (threadIdx.x == 0) {
+      const int comps[12] = {0, 1, 2, 15, 16, 17, 18, 19, 20, 21, 22, 23};
+      stage_components<12>(stage, b, np, comps, it.start, it.count, &bar);
+    }
+    if (!mbar_wait(&bar, 0)) {
+      if (threadIdx.x == 0) atomicOr(&e.ctr->status, kStatusWait);
+      return;
+    }
+  }
   const float G = (float)e.G;
   Mat m = env_mat(e);
   m.kind = MAT;  // compile-time material: the other laws' code is folded away
@@ -794,9 +864,10 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
     const int i = it.start + threadIdx.x + p * kBlock;
     if (i >= it.start + it.count) continue;
     const int j = perm ? (int)perm[i] : i;
+    const int l = threadIdx.x + p * kBlock;
     float x[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] = b[a * np + j];
+    for (int a = 0; a < 3; ++a) x[a] = staged ? stage[a][l] : b[a * np + j];
     int base[3], oob = 0;
     float fx[3], w[3][3], dw[3];
 #pragma unroll
@@ -856,7 +927,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
     // only now, so it is not held in registers through the stencil loop.
     float F[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) F[a] = b[(15 + a) * np + j];
+    for (int a = 0; a < 9; ++a) F[a] = staged ? stage[3 + a][l] : b[(15 + a) * np + j];
     float CH[9], Ht[9], Fo[9];
     matmul3(C, F, CH);
 #pragma unroll
