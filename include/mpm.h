@@ -183,6 +183,34 @@ mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const fl
                         const float* reward_adj, float* action_grad, float* xb0, float* vb0, float* Cb0,
                         float* Fb0, float* pose_grad0, void* stream);
 
+/*
+ * The same reverse pass one recorded step at a time, for gradient consumers whose actions
+ * depend on observations (a closed-loop policy a_t = pi(o_t), Sec. 4 and App. B): the adjoint
+ * of step t's action is needed before the adjoint of o_t, which goes into the next (earlier)
+ * step.
+ *  mpm_backward_begin: xb..Fb as for mpm_backward.  Observation adjoints set earlier with
+ *    mpm_set_obs_adjoint are dropped.  MPM_ERR_STATE without recorded steps or while a
+ *    step-wise pass is open.
+ *  mpm_backward_step: reverses the latest recorded step t not yet reversed (T - 1 first).
+ *    reward_adj: [n_envs] adjoint of r_t, or NULL (0).  obs_adj: [n_envs][mpm_obs_dim]
+ *    adjoint of the observation of step t's end state (row t + 1 of mpm_set_obs_adjoint's
+ *    layout), or NULL (0).  action_grad: [n_envs][A_max] output, the total adjoint of a_t
+ *    (everything after it included), or NULL.  step: t, or NULL.  MPM_ERR_STATE when no pass
+ *    is open or every step is reversed.
+ *  mpm_backward_end: after all T steps.  obs_adj: [n_envs][mpm_obs_dim] adjoint of the
+ *    observation of the state at the start of the tape, or NULL.  xb0..pose_grad0 as for
+ *    mpm_backward.  Closes the pass.
+ * Pointers are device or host; each call copies its inputs before it returns.  mpm_step,
+ * mpm_set_state and mpm_reset_tape abandon an open pass; mpm_backward refuses to run during
+ * one.  With the same adjoints the results equal mpm_backward's.
+ */
+mpm_status mpm_backward_begin(mpm_ctx* ctx, const float* xb, const float* vb, const float* Cb, const float* Fb,
+                              void* stream);
+mpm_status mpm_backward_step(mpm_ctx* ctx, const float* reward_adj, const float* obs_adj, float* action_grad,
+                             int32_t* step, void* stream);
+mpm_status mpm_backward_end(mpm_ctx* ctx, const float* obs_adj, float* xb0, float* vb0, float* Cb0, float* Fb0,
+                            float* pose_grad0, void* stream);
+
 /* Forget the recorded steps; the current state stays. */
 mpm_status mpm_reset_tape(mpm_ctx* ctx);
 

@@ -127,6 +127,37 @@ class Batch:
         self._keep_b = (ins, rb)
         return out
 
+    # step-wise reverse pass (closed-loop consumers): begin, one call per recorded step from
+    # the last, end
+    def backward_begin(self, xb=None, vb=None, Cb=None, Fb=None):
+        ins = [self._dev(a) for a in (xb, vb, Cb, Fb)]
+        mpm.mpm_backward_begin(self.ctx, *ins)
+        self._keep_b = ins
+
+    def backward_step(self, reward_adj=None, obs_adj=None):
+        """Reverse the next recorded step t (the last first).  reward_adj: [n_envs] adjoint of
+        r_t; obs_adj: [n_envs, obs_dim] adjoint of the observation of step t's end state.
+        Returns (t, action_grad [n_envs, A]): the total adjoint of a_t."""
+        torch = _torch()
+        ag = torch.empty(self.n_envs, self.A, device=self.device)
+        rb, ob = self._dev(reward_adj), self._dev(obs_adj)
+        t = mpm.mpm_backward_step(self.ctx, reward_adj=rb, obs_adj=ob, action_grad=ag)
+        self._keep_s = (rb, ob)
+        return t, ag
+
+    def backward_end(self, obs_adj=None, want_state=False):
+        torch = _torch()
+        P = self.P
+        out = {"pose_grad0": torch.empty(self.n_envs, 4, device=self.device)}
+        if want_state:
+            out.update(xb0=torch.empty(P, 3, device=self.device), vb0=torch.empty(P, 3, device=self.device),
+                       Cb0=torch.empty(P, 3, 3, device=self.device), Fb0=torch.empty(P, 3, 3, device=self.device))
+        ob = self._dev(obs_adj)
+        mpm.mpm_backward_end(self.ctx, obs_adj=ob, xb0=out.get("xb0"), vb0=out.get("vb0"), Cb0=out.get("Cb0"),
+                             Fb0=out.get("Fb0"), pose_grad0=out["pose_grad0"])
+        self._keep_e = ob
+        return out
+
     def check_status(self):
         return mpm.mpm_check_status(self.ctx, self.n_envs)
 

@@ -74,15 +74,22 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   return false;
 }
 
-// Issue (one thread) the copies of components comps[0..n) of particles [start, start + count)
-// of block b (component stride np) into stage[q][0..], and arm the barrier with their bytes.
-template <int kN, int kStride>
-__device__ __forceinline__ void stage_components(float (*stage)[kStride], const float* b, long long np,
-                                                 const int* comps, int start, int count, unsigned long long* bar) {
-  const unsigned bytes = (unsigned)((count + 3) & ~3) * 4u;
-  mbar_arrive_expect_tx(bar, bytes * kN);
-#pragma unroll
-  for (int q = 0; q < kN; ++q) bulk_copy_g2s(stage[q], b + comps[q] * np + start, bytes, bar);
+// Bytes of one staged component run of `count` particles (rounded up to four particles).
+__device__ __forceinline__ unsigned run_bytes(int count) { return (unsigned)((count + 3) & ~3) * 4u; }
+
+// Whether a chunk can be staged: read in place (no permutation), starting on a 16-byte
+// boundary, and no longer than the stage.
+__device__ __forceinline__ bool stageable(const WorkItem& it, const unsigned* perm) {
+  return perm == nullptr && (it.start & 3) == 0 && it.count > 0 && it.count <= kBlock * kPPT;
+}
+
+// One thread: copy components comps[0..n) of particles [start, start + count) of the SoA
+// block src (component stride np) into dst[0..n), completing on bar.  The caller has armed
+// bar with the bytes of all its runs (mbar_arrive_expect_tx).
+template <int kStride>
+__device__ __forceinline__ void copy_runs(float (*dst)[kStride], const float* src, long long np, const int* comps,
+                                          int n, int start, unsigned bytes, unsigned long long* bar) {
+  for (int q = 0; q < n; ++q) bulk_copy_g2s(dst[q], src + comps[q] * np + start, bytes, bar);
 }
 
 __device__ __forceinline__ void load_env(const EnvDesc* envs, int env, EnvDesc& s, EnvCtr& c) {
@@ -843,13 +850,16 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
   const int sslot = step_slot(c, rev);
   const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
   const long long np = e.n_pad;
-  const bool staged = perm == nullptr && (it.start & 3) == 0 && it.count > 0 && it.count <= kBlock * kPPT;
+  const bool staged = stageable(it, perm);
   if (staged) {
     if (threadIdx.x == 0) {
       const int comps[12] = {0, 1, 2, 15, 16, 17, 18, 19, 20, 21, 22, 23};
-      stage_components<12>(stage, b, np, comps, it.start, it.count, &bar);
+      const unsigned bytes = run_bytes(it.count);
+      mbar_arrive_expect_tx(&bar, 12 * bytes);
+      copy_runs(stage, b, np, comps, 12, it.start, bytes, &bar);
     }
-    if (!mbar_wait(&bar, 0)) {
+    // every thread polls on its own; the CTA leaves together if any of them gave up
+    if (!__syncthreads_and(mbar_wait(&bar, 0) ? 1 : 0)) {
       if (threadIdx.x == 0) atomicOr(&e.ctr->status, kStatusWait);
       return;
     }
@@ -900,8 +910,8 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
         float s0[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f};  // sum_a w_x g, sum_a w_x r_x g
 #pragma unroll
         for (int cx = 0; cx < 3; ++cx) {
-          const float4 gv = __ldg(row + cx);
-          const float g0 = gv.x - vc.x, g1 = gv.y - vc.y, g2 = gv.z - vc.z;
+          const float4 nv = __ldg(row + cx);
+          const float g0 = nv.x - vc.x, g1 = nv.y - vc.y, g2 = nv.z - vc.z;
           s0[0] += w[0][cx] * g0;
           s0[1] += w[0][cx] * g1;
           s0[2] += w[0][cx] * g2;

@@ -52,6 +52,10 @@ struct mpm_ctx {
   float* acc_all = nullptr;
   EnvCtr* ctr_all = nullptr;
   int h_live = 0, h_base = 0;  // host mirrors of the device counters (identical in all envs)
+  // step-wise reverse pass (mpm_backward_begin / _step / _end): steps recorded when it began
+  // and the next step to reverse (-1 when all are done); open between begin and end
+  bool bwd_open = false;
+  int bwd_T = 0, bwd_next = -1;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t g_fwd[2] = {nullptr, nullptr};
   cudaGraphExec_t g_rev = nullptr;
@@ -339,6 +343,7 @@ mpm_status mpm_set_state(mpm_ctx* ctx, const float* x, const float* v, const flo
   }
   CK(cudaGetLastError());
   ctx->h_live = ctx->h_base = 0;
+  ctx->bwd_open = false;  // the tape an open step-wise reverse pass ran over is gone
   return MPM_OK;
 }
 
@@ -366,6 +371,7 @@ mpm_status mpm_get_state(mpm_ctx* ctx, float* x, float* v, float* C, float* F, f
 }
 
 mpm_status mpm_step(mpm_ctx* ctx, const float* actions, float* reward, uint32_t flags, void* stream) {
+  if (ctx) ctx->bwd_open = false;  // a new step changes the tape under an open reverse pass
   if (!ctx) return MPM_ERR_INVALID_ARG;
   const bool record = (flags & MPM_STEP_RECORD) != 0;
   if (record && (ctx->T_cap == 0 || ctx->h_live + 1 >= ctx->n_slots))
@@ -394,6 +400,7 @@ mpm_status mpm_reset_tape(mpm_ctx* ctx) {
   if (!ctx) return MPM_ERR_INVALID_ARG;
   // the live slot stays; it becomes the tape's base
   ctx->h_base = ctx->h_live;
+  ctx->bwd_open = false;
   CK(cudaDeviceSynchronize());
   std::vector<EnvCtr> c(ctx->n_envs);
   CK(cudaMemcpy(c.data(), ctx->ctr_all, sizeof(EnvCtr) * ctx->n_envs, cudaMemcpyDeviceToHost));
@@ -402,15 +409,12 @@ mpm_status mpm_reset_tape(mpm_ctx* ctx) {
   return MPM_OK;
 }
 
-mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const float* Cb, const float* Fb,
-                        const float* reward_adj, float* action_grad, float* xb0, float* vb0, float* Cb0, float* Fb0,
-                        float* pose_grad0, void* stream) {
-  if (!ctx) return MPM_ERR_INVALID_ARG;
+// Start of a reverse pass over the T recorded steps: the final state's adjoint in, every
+// accumulator zeroed.
+static mpm_status bwd_begin(mpm_ctx* ctx, const float* xb, const float* vb, const float* Cb, const float* Fb,
+                            cudaStream_t st, int* T_out) {
   const int T = ctx->h_live - ctx->h_base;
   if (T <= 0) return fail(ctx, MPM_ERR_STATE, "no recorded steps");
-  if (!action_grad && !xb0 && !vb0 && !Cb0 && !Fb0 && !pose_grad0)
-    return fail(ctx, MPM_ERR_INVALID_ARG, "no output requested");
-  cudaStream_t st = (cudaStream_t)stream;
   CK(cudaSetDevice(ctx->device));
   const long long P = ctx->P;
   float* io = ctx->io;
@@ -418,28 +422,33 @@ mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const fl
   if (vb) CK(cudaMemcpyAsync(io + P * 3, vb, sizeof(float) * P * 3, cudaMemcpyDefault, st));
   if (Cb) CK(cudaMemcpyAsync(io + P * 6, Cb, sizeof(float) * P * 9, cudaMemcpyDefault, st));
   if (Fb) CK(cudaMemcpyAsync(io + P * 15, Fb, sizeof(float) * P * 9, cudaMemcpyDefault, st));
-  // a NULL reward adjoint is a zero one (keeps a single captured reverse-step graph)
-  if (reward_adj)
-    CK(cudaMemcpyAsync(ctx->rbar, reward_adj, sizeof(float) * T * ctx->n_envs, cudaMemcpyDefault, st));
-  else
-    CK(cudaMemsetAsync(ctx->rbar, 0, sizeof(float) * T * ctx->n_envs, st));
-  const Launch L = group_launch(ctx->g, st);
   {
     Enqueue q(ctx);
-    launch_bwd_init(L, T);
+    launch_bwd_init(group_launch(ctx->g, st), T);
     launch_adj_in(io_launch(ctx, st), xb ? io : nullptr, vb ? io + P * 3 : nullptr, Cb ? io + P * 6 : nullptr,
                   Fb ? io + P * 15 : nullptr);
   }
   CK(cudaGetLastError());
-  for (int t = T - 1; t >= 0; --t) {
-    mpm_status s = run_graph_or_direct(ctx, &ctx->g_rev, &ctx->g_rev_kernels, st, body_rev, nullptr);
-    if (s != MPM_OK) return s;
-  }
+  *T_out = T;
+  return MPM_OK;
+}
+
+// One reverse step (the next one down), through the captured reverse-step graph.
+static mpm_status bwd_step(mpm_ctx* ctx, cudaStream_t st) {
+  return run_graph_or_direct(ctx, &ctx->g_rev, &ctx->g_rev_kernels, st, body_rev, nullptr);
+}
+
+// End of a reverse pass: the initial state's observation adjoint (when set), then the initial
+// state's and pose's adjoints out.
+static mpm_status bwd_end(mpm_ctx* ctx, float* xb0, float* vb0, float* Cb0, float* Fb0, float* pose_grad0,
+                          cudaStream_t st) {
+  const long long P = ctx->P;
+  float* io = ctx->io;
   {
     Enqueue q(ctx);
     if (ctx->obs_adj) {
-      launch_obs_adj(L, obs_of(ctx), 1);  // observation of the initial state
-      CK(cudaMemsetAsync(ctx->obs_on, 0, sizeof(int), st));  // consumed
+      launch_obs_adj(group_launch(ctx->g, st), obs_of(ctx), 1);  // observation of the initial state
+      CK(cudaMemsetAsync(ctx->obs_on, 0, sizeof(int), st));      // consumed
     }
     launch_adj_out(io_launch(ctx, st), StateRef{REF_REV, 0}, io, io + P * 3, io + P * 6, io + P * 15);
   }
@@ -448,15 +457,107 @@ mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const fl
   if (vb0) CK(cudaMemcpyAsync(vb0, io + P * 3, sizeof(float) * P * 3, cudaMemcpyDefault, st));
   if (Cb0) CK(cudaMemcpyAsync(Cb0, io + P * 6, sizeof(float) * P * 9, cudaMemcpyDefault, st));
   if (Fb0) CK(cudaMemcpyAsync(Fb0, io + P * 15, sizeof(float) * P * 9, cudaMemcpyDefault, st));
-  if (action_grad)
-    CK(cudaMemcpyAsync(action_grad, ctx->agrad, sizeof(float) * (size_t)T * ctx->n_envs * ctx->A_max,
-                       cudaMemcpyDefault, st));
   if (pose_grad0) {
     launch_pose_io(io_launch(ctx, st), POSE_GRAD, ctx->posebuf, 0);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(pose_grad0, ctx->posebuf, sizeof(float) * 4 * ctx->n_envs, cudaMemcpyDefault, st));
   }
   return MPM_OK;
+}
+
+mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const float* Cb, const float* Fb,
+                        const float* reward_adj, float* action_grad, float* xb0, float* vb0, float* Cb0, float* Fb0,
+                        float* pose_grad0, void* stream) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (!action_grad && !xb0 && !vb0 && !Cb0 && !Fb0 && !pose_grad0)
+    return fail(ctx, MPM_ERR_INVALID_ARG, "no output requested");
+  if (ctx->bwd_open) return fail(ctx, MPM_ERR_STATE, "a step-wise reverse pass is open");
+  cudaStream_t st = (cudaStream_t)stream;
+  int T = 0;
+  mpm_status s = bwd_begin(ctx, xb, vb, Cb, Fb, st, &T);
+  if (s != MPM_OK) return s;
+  // a NULL reward adjoint is a zero one (keeps a single captured reverse-step graph)
+  if (reward_adj)
+    CK(cudaMemcpyAsync(ctx->rbar, reward_adj, sizeof(float) * T * ctx->n_envs, cudaMemcpyDefault, st));
+  else
+    CK(cudaMemsetAsync(ctx->rbar, 0, sizeof(float) * T * ctx->n_envs, st));
+  for (int t = T - 1; t >= 0; --t)
+    if ((s = bwd_step(ctx, st)) != MPM_OK) return s;
+  if ((s = bwd_end(ctx, xb0, vb0, Cb0, Fb0, pose_grad0, st)) != MPM_OK) return s;
+  if (action_grad)
+    CK(cudaMemcpyAsync(action_grad, ctx->agrad, sizeof(float) * (size_t)T * ctx->n_envs * ctx->A_max,
+                       cudaMemcpyDefault, st));
+  return MPM_OK;
+}
+
+mpm_status mpm_backward_begin(mpm_ctx* ctx, const float* xb, const float* vb, const float* Cb, const float* Fb,
+                              void* stream) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (ctx->bwd_open) return fail(ctx, MPM_ERR_STATE, "a step-wise reverse pass is already open");
+  cudaStream_t st = (cudaStream_t)stream;
+  int T = 0;
+  const mpm_status s = bwd_begin(ctx, xb, vb, Cb, Fb, st, &T);
+  if (s != MPM_OK) return s;
+  // observation adjoints come step by step now: forget any set for a whole-tape backward
+  if (ctx->obs_on) CK(cudaMemsetAsync(ctx->obs_on, 0, sizeof(int), st));
+  ctx->bwd_open = true;
+  ctx->bwd_T = T;
+  ctx->bwd_next = T - 1;
+  return MPM_OK;
+}
+
+mpm_status mpm_backward_step(mpm_ctx* ctx, const float* reward_adj, const float* obs_adj, float* action_grad,
+                             int32_t* step, void* stream) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (!ctx->bwd_open) return fail(ctx, MPM_ERR_STATE, "no step-wise reverse pass is open");
+  if (ctx->bwd_next < 0) return fail(ctx, MPM_ERR_STATE, "every recorded step is reversed");
+  if (obs_adj && !ctx->obs_adj) return fail(ctx, MPM_ERR_STATE, "observation adjoints need a checkpoint tape");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaSetDevice(ctx->device));
+  const int t = ctx->bwd_next;
+  const size_t ne = (size_t)ctx->n_envs;
+  if (reward_adj)
+    CK(cudaMemcpyAsync(ctx->rbar + (size_t)t * ne, reward_adj, sizeof(float) * ne, cudaMemcpyDefault, st));
+  else
+    CK(cudaMemsetAsync(ctx->rbar + (size_t)t * ne, 0, sizeof(float) * ne, st));
+  if (ctx->obs_adj) {
+    // the reverse step adds row t + 1 (its end state) when the flag is set
+    if (obs_adj) {
+      CK(cudaMemcpyAsync(ctx->obs_adj + (size_t)(t + 1) * ne * ctx->obs_dim, obs_adj,
+                         sizeof(float) * ne * ctx->obs_dim, cudaMemcpyDefault, st));
+      CK(cudaMemsetAsync(ctx->obs_on, 0x01, 1, st));
+    } else {
+      CK(cudaMemsetAsync(ctx->obs_on, 0, sizeof(int), st));
+    }
+  }
+  const mpm_status s = bwd_step(ctx, st);
+  if (s != MPM_OK) return s;
+  if (action_grad)
+    CK(cudaMemcpyAsync(action_grad, ctx->agrad + (size_t)t * ne * ctx->A_max, sizeof(float) * ne * ctx->A_max,
+                       cudaMemcpyDefault, st));
+  if (step) *step = t;
+  ctx->bwd_next = t - 1;
+  return MPM_OK;
+}
+
+mpm_status mpm_backward_end(mpm_ctx* ctx, const float* obs_adj, float* xb0, float* vb0, float* Cb0, float* Fb0,
+                            float* pose_grad0, void* stream) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (!ctx->bwd_open) return fail(ctx, MPM_ERR_STATE, "no step-wise reverse pass is open");
+  if (ctx->bwd_next >= 0) return fail(ctx, MPM_ERR_STATE, "%d recorded steps are not reversed yet", ctx->bwd_next + 1);
+  if (obs_adj && !ctx->obs_adj) return fail(ctx, MPM_ERR_STATE, "observation adjoints need a checkpoint tape");
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaSetDevice(ctx->device));
+  if (ctx->obs_adj) {
+    if (obs_adj) {
+      CK(cudaMemcpyAsync(ctx->obs_adj, obs_adj, sizeof(float) * ctx->n_envs * ctx->obs_dim, cudaMemcpyDefault, st));
+      CK(cudaMemsetAsync(ctx->obs_on, 0x01, 1, st));
+    } else {
+      CK(cudaMemsetAsync(ctx->obs_on, 0, sizeof(int), st));
+    }
+  }
+  ctx->bwd_open = false;
+  return bwd_end(ctx, xb0, vb0, Cb0, Fb0, pose_grad0, st);
 }
 
 mpm_status mpm_check_status(mpm_ctx* ctx, int32_t* flags) {

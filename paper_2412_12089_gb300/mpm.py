@@ -94,6 +94,9 @@ def lib():
         "mpm_get_state": (i32, [_P, _P, _P, _P, _P, _P, _P]),
         "mpm_step": (i32, [_P, _P, _P, u32, _P]),
         "mpm_backward": (i32, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+        "mpm_backward_begin": (i32, [_P, _P, _P, _P, _P, _P]),
+        "mpm_backward_step": (i32, [_P, _P, _P, _P, ct.POINTER(ct.c_int32), _P]),
+        "mpm_backward_end": (i32, [_P, _P, _P, _P, _P, _P, _P, _P]),
         "mpm_reset_tape": (i32, [_P]),
         "mpm_check_status": (i32, [_P, _P]),
         "mpm_bin": (i32, [_P, i32, i32, _P, _P, _P]),
@@ -247,6 +250,23 @@ def mpm_backward(ctx, xb=None, vb=None, Cb=None, Fb=None, reward_adj=None, actio
                  Cb0=None, Fb0=None, pose_grad0=None, stream=None):
     return check(lib().mpm_backward(ctx, ptr(xb), ptr(vb), ptr(Cb), ptr(Fb), ptr(reward_adj), ptr(action_grad),
                                     ptr(xb0), ptr(vb0), ptr(Cb0), ptr(Fb0), ptr(pose_grad0), stream_ptr(stream)), ctx)
+
+
+def mpm_backward_begin(ctx, xb=None, vb=None, Cb=None, Fb=None, stream=None):
+    return check(lib().mpm_backward_begin(ctx, ptr(xb), ptr(vb), ptr(Cb), ptr(Fb), stream_ptr(stream)), ctx)
+
+
+def mpm_backward_step(ctx, reward_adj=None, obs_adj=None, action_grad=None, stream=None):
+    """Reverse the next recorded step; returns its index t."""
+    t = ct.c_int32(-1)
+    check(lib().mpm_backward_step(ctx, ptr(reward_adj), ptr(obs_adj), ptr(action_grad), ct.byref(t),
+                                  stream_ptr(stream)), ctx)
+    return t.value
+
+
+def mpm_backward_end(ctx, obs_adj=None, xb0=None, vb0=None, Cb0=None, Fb0=None, pose_grad0=None, stream=None):
+    return check(lib().mpm_backward_end(ctx, ptr(obs_adj), ptr(xb0), ptr(vb0), ptr(Cb0), ptr(Fb0), ptr(pose_grad0),
+                                        stream_ptr(stream)), ctx)
 
 
 def mpm_reset_tape(ctx):
