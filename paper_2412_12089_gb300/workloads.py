@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-MATERIALS = ("neohookean", "vonmises", "fluid", "muscle")
+MATERIALS = ("neohookean", "vonmises", "fluid", "muscle", "fem")
 COLLIDERS = ("none", "capsule", "box", "container", "capsules")
 REWARDS = ("none", "flat", "reach", "jump")
 
@@ -58,6 +58,12 @@ class EnvSpec:
     pose0: tuple = (0.0, 0.0, 0.0, 0.0)
     n_caps: int = 0                       # collider "capsules": capsules of coll_dims (1..8)
     cap_offset: tuple = (0.0, 0.0, 0.0)   # initial position of capsule j: pose0 + j * cap_offset
+    # material "fem": a tetrahedral mesh whose vertices are the environment's particles
+    k_damp: float = 0.0                   # viscous damping stress k_damp dF/dt
+    ground_z: float = 0.0                 # height of the ground plane
+    fem_tets: np.ndarray = None           # (n_t, 4) int32 vertex indices
+    fem_rest: np.ndarray = None           # (n_particles, 3) float32 rest positions
+    fem_group: np.ndarray = None          # (n_t,) int32 action index of each element
 
     def __post_init__(self):
         # Every real-valued input is made FP32-representable, so the FP32 CUDA path and the
@@ -308,6 +314,73 @@ def handflip(n_envs: int = 128, seed: int = 0, n: int = 2500, G: int = 48, subst
         inits.append(_rest_state(x, v))
         acts.append(rng.normal(0.0, action_std, (T, 4 * n_caps)))
     return Workload("handflip", specs, inits, _pad_actions(acts, T), T)
+
+
+# ----------------------------------------------------------------------------- tet meshes
+
+def voxel_mesh(occ, size, origin=(0.0, 0.0, 0.0)):
+    """Tetrahedral mesh of the occupied voxels occ[i, j, k] (edge `size`): shared lattice
+    vertices, five tetrahedra per voxel, the split mirrored on alternate voxels so that
+    neighbouring faces carry the same diagonal.  Returns (rest (n_v, 3) float32, tets
+    (n_t, 4) int32)."""
+    occ = np.asarray(occ, bool)
+    index = {}
+    verts = []
+
+    def vid(p):
+        if p not in index:
+            index[p] = len(verts)
+            verts.append(p)
+        return index[p]
+
+    # corners (dx, dy, dz) of the five tetrahedra of a voxel; the fifth is the central one
+    five = (((0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)), ((1, 1, 0), (0, 1, 0), (1, 0, 0), (1, 1, 1)),
+            ((1, 0, 1), (1, 0, 0), (0, 0, 1), (1, 1, 1)), ((0, 1, 1), (0, 0, 1), (0, 1, 0), (1, 1, 1)),
+            ((1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 1)))
+    tets = []
+    for i, j, k in zip(*np.nonzero(occ)):
+        mirror = (i + j + k) % 2 == 1
+        for tet in five:
+            tets.append([vid((i + (1 - c[0] if mirror else c[0]), j + c[1], k + c[2])) for c in tet])
+    rest = np.asarray(verts, np.float64) * size + np.asarray(origin, np.float64)
+    return rest.astype(np.float32), np.asarray(tets, np.int32)
+
+
+def softjumper(n_envs: int = 256, seed: int = 0, substeps: int = 80, T: int = 16, scale: float = 0.05,
+               act_scale: float = 0.2) -> Workload:
+    """SoftJumper (App. E) as tetrahedral FEM: a quadruped of voxels (a 7 x 4 x 2 torso on four
+    2 x 2 x 2 legs, edge `scale`), 180 vertices and 440 elements, stable neo-Hookean with
+    lambda = mu = 1000 (E = 2500, nu = 0.25), rho = 1, k_damp = 1, h = 1/60 in 80 substeps,
+    ground z = 0 with friction 0.5.  Actions: one activation per pair of elements (220),
+    U(-1, 1), scaled by act_scale into the elements' volume-ratio shift.  Reward: mean forward
+    velocity + 3 (mean height - h0) - 1e-4 |a|^2 over all vertices.  Per env the body is
+    scaled by U(0.9, 1.1) and offset by U(-0.08, 0.08) in x, y and U(0, 0.04) in z."""
+    rng = np.random.default_rng(seed)
+    occ = np.zeros((7, 4, 4), bool)
+    occ[:, :, 2:4] = True
+    for i0 in (0, 5):
+        for j0 in (0, 2):
+            occ[i0:i0 + 2, j0:j0 + 2, 0:2] = True
+    rest0, tets = voxel_mesh(occ, 1.0)
+    n_t = tets.shape[0]
+    n_act = (n_t + 1) // 2
+    group = (np.arange(n_t) // 2).astype(np.int32)
+    specs, inits, acts = [], [], []
+    for e in range(n_envs):
+        sc = scale * rng.uniform(0.9, 1.1)
+        off = np.array([rng.uniform(-0.08, 0.08), rng.uniform(-0.08, 0.08), rng.uniform(0.0, 0.04)])
+        centre = np.array([0.5 - 3.5 * sc, 0.5 - 2.0 * sc, 0.0])
+        rest = (rest0.astype(np.float64) * sc + centre + off).astype(np.float32)
+        n = rest.shape[0]
+        h0 = float(np.float32(rest[:, 2].astype(np.float64).mean()))
+        spec = EnvSpec(n_particles=n, grid_res=8, substeps=substeps, dt=(1.0 / 60.0) / substeps, material="fem",
+                       E=2500.0, nu=0.25, rho=1.0, act_stress=act_scale, n_groups=n_act, ground_mu=0.5,
+                       reward="jump", n_sub=n, rparam=(h0, 3.0, 1e-4, 0.0), k_damp=1.0, ground_z=0.0,
+                       fem_tets=tets, fem_rest=rest, fem_group=group, bound=0)
+        specs.append(spec)
+        inits.append(_rest_state(rest, np.zeros((n, 3))))
+        acts.append(rng.uniform(-1.0, 1.0, (T, n_act)))
+    return Workload("softjumper", specs, inits, _pad_actions(acts, T), T)
 
 
 def concat_inits(inits):
