@@ -64,7 +64,8 @@ typedef enum {
  * FLUID: tau = bulk J (J - 1) I + visc J (C + C^T); projection F <- J^(1/3) I.
  * MUSCLE: neo-Hookean plus a_g * act_stress * (F e_z)(F e_z)^T for particles in actuator
  * group g (a_g = the group's action). */
-enum { MPM_MAT_NEOHOOKEAN = 0, MPM_MAT_VONMISES = 1, MPM_MAT_FLUID = 2, MPM_MAT_MUSCLE = 3 };
+enum { MPM_MAT_NEOHOOKEAN = 0, MPM_MAT_VONMISES = 1, MPM_MAT_FLUID = 2, MPM_MAT_MUSCLE = 3,
+       MPM_MAT_FEM = 4 /* tetrahedral FEM (App. D.2): the particles are the mesh's vertices */ };
 
 /* Kinematic collider shapes, in the body frame (body pose q = (c_x, c_y, c_z, theta),
  * theta = yaw about +z).  CAPSULE: axis along body x, coll_dims = (radius, half-length).
@@ -113,6 +114,25 @@ typedef struct {
                              (the gradient with respect to pose0).  The union's contact at a
                              node is the nearest capsule's. */
     float cap_offset[3];
+    /*
+     * MPM_MAT_FEM (App. D.2 and App. E's SoftJumper): the n_particles particles are the vertices
+     * of a tetrahedral mesh, simulated by the stable neo-Hookean energy
+     *   Psi = mu/2 (I_C - 3) + lam/2 (J - alpha - a)^2 - mu/2 log(I_C + 1),
+     * alpha = 1 + 3 mu / (4 lam), (mu, lam) from (E, nu), with a per-element activation
+     * a = act_stress * action[fem_group[e]] (n_groups actions), a damping stress k_damp dF/dt,
+     * lumped masses rho V0 / 4, gravity, a semi-implicit Euler substep, and the ground z =
+     * ground_z (a vertex at or below it moving down stops, with Coulomb friction ground_mu).
+     * No grid is used (grid_res only sizes an unused minimum arena; 8 is enough), the collider
+     * must be MPM_COLL_NONE, n_particles <= 4096.  C and F of the state are not used (get_state
+     * returns C = 0, F = I).  The mesh arrays are host memory, read during mpm_create (and
+     * mpm_submit), not kept.
+     */
+    int32_t n_tets;
+    const int32_t* fem_tets;   /* [n_tets][4] vertex indices */
+    const float* fem_rest;     /* [n_particles][3] rest positions */
+    const int32_t* fem_group;  /* [n_tets] action index of each element (< n_groups), or NULL */
+    float k_damp;
+    float ground_z;
 } mpm_env_spec;
 
 typedef struct {

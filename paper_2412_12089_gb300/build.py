@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libmpm_gb300.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["kernels.cu", "sort.cu", "engine.cu", "runtime.cu", "server.cu", "bin_static.cu"]
+SOURCES = ["kernels.cu", "fem.cu", "sort.cu", "engine.cu", "runtime.cu", "server.cu", "bin_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -26,7 +26,7 @@ const char* check_spec(const mpm_env_spec& s) {
   if (s.grid_res < 8 || s.grid_res > 128 || s.grid_res % 4) return "grid_res";
   if (s.substeps < 1 || s.substeps > 4096) return "substeps";
   if (s.bound < 0 || 2 * s.bound >= s.grid_res) return "bound";
-  if (s.material < 0 || s.material > 3) return "material";
+  if (s.material < 0 || s.material > kMatFem) return "material";
   if (s.collider < 0 || s.collider > 4) return "collider";
   if (s.collider == MPM_COLL_CAPSULES) {
     if (s.n_caps < 1 || s.n_caps > kMaxCaps) return "n_caps";
@@ -43,9 +43,66 @@ const char* check_spec(const mpm_env_spec& s) {
   if (s.reward != 0 && s.n_sub < 1) return "n_sub";
   if (!(s.dt > 0.f) || !(s.p_vol > 0.f) || !(s.rho > 0.f)) return "dt/p_vol/rho";
   if (s.reward == 1 && !(s.rparam[0] != 0.f)) return "rparam (h_flat)";
-  if ((s.material == 0 || s.material == 1 || s.material == 3) && !(s.E > 0.f && s.nu >= 0.f && s.nu < 0.5f))
+  if ((s.material == 0 || s.material == 1 || s.material == 3 || s.material == kMatFem) &&
+      !(s.E > 0.f && s.nu >= 0.f && s.nu < 0.5f))
     return "E/nu";
+  if (s.material == kMatFem) {
+    if (s.n_particles > kFemMaxVerts) return "n_particles (FEM meshes hold at most 2048 vertices)";
+    if (s.collider != MPM_COLL_NONE || s.n_coll_act != 0) return "collider (FEM has none)";
+    if (!(s.nu > 0.f)) return "nu (FEM needs lambda > 0)";
+    if (s.n_tets < 1 || s.n_tets > (1 << 20) || !s.fem_tets || !s.fem_rest) return "fem mesh";
+    if (!(s.k_damp >= 0.f)) return "k_damp";
+    for (long long e = 0; e < s.n_tets; ++e) {
+      for (int c = 0; c < 4; ++c)
+        if (s.fem_tets[4 * e + c] < 0 || s.fem_tets[4 * e + c] >= s.n_particles) return "fem_tets (vertex index)";
+      if (s.fem_group && (s.fem_group[e] < 0 || s.fem_group[e] >= std::max(s.n_groups, 1))) return "fem_group";
+    }
+  }
   return nullptr;
+}
+
+namespace {
+// Rest data of element e: Dm (edge matrix, row-major) and its determinant, in double.
+double rest_edges(const mpm_env_spec& s, long long e, double* Dm) {
+  const int* t = s.fem_tets + 4 * e;
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 3; ++c) Dm[3 * k + c] = (double)s.fem_rest[3 * t[c + 1] + k] - (double)s.fem_rest[3 * t[0] + k];
+  return Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
+         Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
+}
+}  // namespace
+
+cudaError_t fem_upload(const mpm_env_spec& s, const EnvDesc& d) {
+  if (s.material != kMatFem) return cudaSuccess;
+  const long long nt = s.n_tets, nv = s.n_particles;
+  std::vector<int4> tet((size_t)nt);
+  std::vector<float> dminv((size_t)nt * 9), vol((size_t)nt), inv_mass((size_t)d.n_pad, 0.0f);
+  std::vector<int> grp((size_t)nt, 0);
+  std::vector<double> mass((size_t)nv, 0.0);
+  for (long long e = 0; e < nt; ++e) {
+    const int* t = s.fem_tets + 4 * e;
+    tet[e] = make_int4(t[0], t[1], t[2], t[3]);
+    double Dm[9];
+    const double det = rest_edges(s, e, Dm);
+    if (det == 0.0 || !std::isfinite(det)) return cudaErrorInvalidValue;
+    // inverse by the adjugate: (Dm^-1)_ij = cof(Dm)_ji / det
+    const double cof[9] = {Dm[4] * Dm[8] - Dm[5] * Dm[7], Dm[5] * Dm[6] - Dm[3] * Dm[8], Dm[3] * Dm[7] - Dm[4] * Dm[6],
+                           Dm[2] * Dm[7] - Dm[1] * Dm[8], Dm[0] * Dm[8] - Dm[2] * Dm[6], Dm[1] * Dm[6] - Dm[0] * Dm[7],
+                           Dm[1] * Dm[5] - Dm[2] * Dm[4], Dm[2] * Dm[3] - Dm[0] * Dm[5], Dm[0] * Dm[4] - Dm[1] * Dm[3]};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) dminv[9 * e + 3 * i + j] = (float)(cof[3 * j + i] / det);
+    const double V0 = std::fabs(det) / 6.0;
+    vol[e] = (float)V0;
+    for (int c = 0; c < 4; ++c) mass[t[c]] += 0.25 * (double)s.rho * V0;
+    grp[e] = s.fem_group ? s.fem_group[e] : 0;
+  }
+  for (long long i = 0; i < nv; ++i) inv_mass[i] = mass[i] > 0.0 ? (float)(1.0 / mass[i]) : 0.0f;
+  cudaError_t err;
+  if ((err = cudaMemcpy((void*)d.fem_tet, tet.data(), sizeof(int4) * nt, cudaMemcpyHostToDevice))) return err;
+  if ((err = cudaMemcpy((void*)d.fem_dminv, dminv.data(), sizeof(float) * 9 * nt, cudaMemcpyHostToDevice))) return err;
+  if ((err = cudaMemcpy((void*)d.fem_vol, vol.data(), sizeof(float) * nt, cudaMemcpyHostToDevice))) return err;
+  if ((err = cudaMemcpy((void*)d.fem_group, grp.data(), sizeof(int) * nt, cudaMemcpyHostToDevice))) return err;
+  return cudaMemcpy((void*)d.fem_inv_mass, inv_mass.data(), sizeof(float) * d.n_pad, cudaMemcpyHostToDevice);
 }
 
 EnvLayout env_layout(const mpm_env_spec& s, int n_slots, bool tape, bool own, int T) {
@@ -69,6 +126,10 @@ EnvLayout env_layout(const mpm_env_spec& s, int n_slots, bool tape, bool own, in
   L.tile = cur;  cur = align256(cur + (size_t)TG3 * 4);
   L.pose = cur;  cur = align256(cur + (size_t)n_slots * kPose * 4);
   L.act = cur;   cur = align256(cur + (size_t)n_slots * A * 4);
+  if (s.material == kMatFem) {  // element records, Dm^-1, rest volumes, groups, inverse masses
+    const size_t nt = (size_t)std::max(s.n_tets, 0);
+    L.fem = cur;   cur = align256(cur + nt * (16 + 36 + 4 + 4) + (size_t)n_pad * 4);
+  }
   if (own) {
     L.acc = cur;       cur = align256(cur + (size_t)(ACC_ACT + A) * 4);
     L.ctr = cur;       cur = align256(cur + sizeof(EnvCtr));
@@ -118,7 +179,7 @@ void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base,
   d.p_vol = s.p_vol;
   d.p_mass = s.rho * s.p_vol;
   for (int i = 0; i < 3; ++i) d.gravity[i] = s.gravity[i];
-  if (s.material == 0 || s.material == 1 || s.material == 3) {
+  if (s.material == 0 || s.material == 1 || s.material == 3 || s.material == kMatFem) {
     const double E = s.E, nu = s.nu;
     d.mu = (float)(E / (2.0 * (1.0 + nu)));
     d.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
@@ -130,6 +191,19 @@ void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base,
   d.coll_mu = s.coll_mu;
   d.alpha = s.alpha;
   d.ground_mu = s.ground_mu;
+  if (s.material == kMatFem) {
+    const size_t nt = (size_t)s.n_tets;
+    char* f = base + L.fem;
+    d.fem_tet = (const int4*)f;
+    d.fem_dminv = (const float*)(f + nt * 16);
+    d.fem_vol = d.fem_dminv + 9 * nt;
+    d.fem_group = (const int*)(d.fem_vol + nt);
+    d.fem_inv_mass = (const float*)(d.fem_group + nt);
+    d.n_tets = s.n_tets;
+    d.k_damp = s.k_damp;
+    d.ground_z = s.ground_z;
+    d.fem_alpha = (float)(1.0 + 0.75 * (double)d.mu / (double)d.lam);
+  }
   if (s.collider == MPM_COLL_CAPSULES) {
     d.n_caps = s.n_caps;
     for (int i = 0; i < 3; ++i) d.cap_offset[i] = s.cap_offset[i];
@@ -164,7 +238,7 @@ void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base,
 
 void Group::release() {
   void* ptrs[] = {d_desc, d_items, d_items_env, active, active_n, sort.keys[0], sort.keys[1], sort.vals[0],
-                  sort.vals[1], sort.hist, tape.mp, tape.list, tape.slot, tape.cursor};
+                  sort.vals[1], sort.hist, tape.mp, tape.list, tape.slot, tape.cursor, d_fem};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d_desc = nullptr;
@@ -176,6 +250,8 @@ void Group::release() {
   active_cap = hist_cap = 0;
   tape = GridTape{nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
   tape_mp_cap = tape_list_cap = tape_slot_cap = tape_cursor_cap = 0;
+  d_fem = nullptr;
+  fem_cap = 0;
 }
 
 namespace {
@@ -205,14 +281,22 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
   g.desc = descs;
   g.spec = specs;
   g.n_envs = (int)descs.size();
-  g.S_max = 1;
+  g.S_max = 0;
   g.A_max = 1;
   g.P = 0;
   g.tiles = 0;
+  g.fem_envs.clear();
+  g.fem_nv_max = g.fem_act_max = 0;
   int G_max = 8;
   for (int e = 0; e < g.n_envs; ++e) {
     const auto& s = specs[e];
-    g.S_max = std::max(g.S_max, s.substeps);
+    if (s.material == kMatFem) {
+      g.fem_envs.push_back(e);
+      g.fem_nv_max = std::max(g.fem_nv_max, s.n_particles);
+      g.fem_act_max = std::max(g.fem_act_max, s.n_groups);
+    } else {
+      g.S_max = std::max(g.S_max, s.substeps);
+    }
     g.A_max = std::max(g.A_max, s.n_coll_act + s.n_groups);
     G_max = std::max(G_max, s.grid_res);
     g.desc[e].key_env = (unsigned)e;
@@ -254,6 +338,7 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
   g.mats.clear();
   for (size_t i = 0; i < g.items.size(); ++i) {
     const int mat = specs[g.items[i].env].material;
+    if (mat == kMatFem) break;  // FEM items sort last; their envs run the FEM step kernels
     if (g.mats.empty() || g.mats.back().material != mat)
       g.mats.push_back({mat, (int)i, std::vector<int>(g.S_max + 1, 0), box0});
     auto& m = g.mats.back();
@@ -294,8 +379,15 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
   size_t hcap = (size_t)g.hist_cap;
   if ((e = ensure(g.sort.hist, hcap, (size_t)radix_hist_entries((long long)P)))) return e;
   g.hist_cap = (long long)hcap;
+  if (!g.fem_envs.empty()) {
+    size_t fc = g.fem_cap;
+    if ((e = ensure(g.d_fem, fc, g.fem_envs.size())) != cudaSuccess) return e;
+    g.fem_cap = fc;
+    if ((e = cudaMemcpy(g.d_fem, g.fem_envs.data(), sizeof(int) * g.fem_envs.size(), cudaMemcpyHostToDevice)))
+      return e;
+  }
   g.tape.cap = 0;
-  if (g.want_tape && g.tape_T > 0 && g.tape_budget > 0.0) {
+  if (g.want_tape && g.tape_T > 0 && g.tape_budget > 0.0 && g.S_max > 0) {
     // pool: the budget, or 1.5x a generous estimate of the active tiles (P/32 + 1024 per
     // substep) when that is smaller; MPM_GRID_TAPE_TILES caps it (tests make it overflow)
     constexpr double kTileBytes = 64.0 * sizeof(float4) + sizeof(uint2);
@@ -377,12 +469,19 @@ void substeps_forward(Group& g, const Launch& L, const std::vector<MatGroup>& ma
 }
 
 // tape: the group's grid tape (the recorded steps kept their grids there), or NULL.
+// fem: the FEM environments among L's (device list, count, largest vertex and action counts).
+struct FemList {
+  const int* list = nullptr;
+  int n = 0, nv_max = 0, act_max = 0;
+};
+
 void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, const float* rbar, float* agrad,
-                  int n_tot, int a_max, const GridTape* tape, const ObsAdj* obs) {
+                  int n_tot, int a_max, const GridTape* tape, const ObsAdj* obs, const FemList& fem) {
   launch_rev_begin(L);
   launch_reward_adj(L, rbar, n_tot);
   if (obs) launch_obs_adj(L, *obs, 0);  // observation of the step's end state
   launch_adj_ref(L);
+  launch_fem_reverse(L, fem.list, fem.n, fem.nv_max, fem.act_max);
   // recompute substep states 1..S-1 into the ring (envs with S > k + 1); the grid of each
   // substep comes from the tape when it was kept, else P2G rebuilds it
   for (int k = 0; k + 1 < S; ++k) {
@@ -475,14 +574,24 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
   if (!per_env) {
     Launch L = group_launch(g, st);
     launch_step_begin(L, act_in, a_max, record);
-    bin_envs(L, 0, g.P, g.cell_bits, g.key_bits, g.sort);
-    substeps_forward(g, L, g.mats, g.S_max, record && g.tape.cap > 0 ? &g.tape : nullptr);
+    launch_fem_forward(L, g.d_fem, (int)g.fem_envs.size(), g.fem_nv_max);
+    if (g.S_max > 0) {
+      bin_envs(L, 0, g.P, g.cell_bits, g.key_bits, g.sort);
+      substeps_forward(g, L, g.mats, g.S_max, record && g.tape.cap > 0 ? &g.tape : nullptr);
+    }
     launch_reward_end(L, rew, record);
     return;
   }
   // baseline path: every stage launched once per environment
+  int fem_i = 0;
   for (int e = 0; e < g.n_envs; ++e) {
     Launch L = env_launch(g, e, st);
+    if (g.spec[e].material == kMatFem) {
+      launch_step_begin(L, act_in, a_max, record);
+      launch_fem_forward(L, g.d_fem + fem_i++, 1, g.spec[e].n_particles);
+      launch_reward_end(L, rew, record);
+      continue;
+    }
     const int S = g.spec[e].substeps;
     std::vector<MatGroup> one{{g.spec[e].material, g.env_item0[e], std::vector<int>(S + 1, g.env_nitems[e])}};
     one[0].n_gt[S] = 0;
@@ -497,15 +606,22 @@ void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad,
                      const ObsAdj* obs) {
   if (g.n_envs == 0) return;
   if (!per_env) {
+    FemList fem{g.d_fem, (int)g.fem_envs.size(), g.fem_nv_max, g.fem_act_max};
     reverse_step(group_launch(g, st), g.mats, g.S_max, rbar, agrad, n_tot, a_max, g.tape.cap > 0 ? &g.tape : nullptr,
-                 obs);
+                 obs, fem);
     return;
   }
+  int fem_i = 0;
   for (int e = 0; e < g.n_envs; ++e) {
+    if (g.spec[e].material == kMatFem) {
+      FemList fem{g.d_fem + fem_i++, 1, g.spec[e].n_particles, g.spec[e].n_groups};
+      reverse_step(env_launch(g, e, st), {}, 0, rbar, agrad, n_tot, a_max, nullptr, obs, fem);
+      continue;
+    }
     const int S = g.spec[e].substeps;
     std::vector<MatGroup> one{{g.spec[e].material, g.env_item0[e], std::vector<int>(S + 1, g.env_nitems[e])}};
     one[0].n_gt[S] = 0;
-    reverse_step(env_launch(g, e, st), one, S, rbar, agrad, n_tot, a_max, nullptr, obs);
+    reverse_step(env_launch(g, e, st), one, S, rbar, agrad, n_tot, a_max, nullptr, obs, FemList{});
   }
 }
 

@@ -16,6 +16,7 @@
 namespace mpm {
 
 constexpr int kChunk = 256;  // particles per work item (CTA)
+constexpr int kFemMaxVerts = 2048;  // vertices of one FEM mesh (the step kernels hold them in shared memory)
 
 const char* check_spec(const mpm_env_spec& s);
 
@@ -28,6 +29,7 @@ struct EnvLayout {
   long long n_pad = 0;
   size_t slots = 0, ring = 0, adj = 0, perm = 0, grid = 0, tile = 0, pose = 0, act = 0;
   size_t acc = 0, ctr = 0, act_env = 0, rew_env = 0, rbar_env = 0, agrad_env = 0, xout = 0;
+  size_t fem = 0;  // material FEM: element data and inverse masses
   size_t total = 0;
 };
 
@@ -38,6 +40,10 @@ EnvLayout env_layout(const mpm_env_spec& s, int n_slots, bool tape, bool own, in
 // capsule j at pose0 + j * cap_offset.
 void initial_pose(const mpm_env_spec& s, float* q);
 void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base, float* acc, EnvCtr* ctr);
+// Material FEM: the element records, Dm^-1 and rest volumes (from the spec's rest positions,
+// in double), groups and inverse lumped masses, copied into the environment's buffers
+// (synchronous).  Nothing for other materials; cudaErrorInvalidValue for a degenerate element.
+cudaError_t fem_upload(const mpm_env_spec& s, const EnvDesc& d);
 
 struct MatGroup {
   int material;
@@ -49,11 +55,16 @@ struct MatGroup {
 struct Group {
   std::vector<EnvDesc> desc;
   std::vector<mpm_env_spec> spec;
-  int n_envs = 0, S_max = 1, A_max = 1, cell_bits = 0, key_bits = 0;
+  int n_envs = 0, S_max = 1, A_max = 1, cell_bits = 0, key_bits = 0;  // S_max: over MPM envs (0: none)
   long long P = 0, tiles = 0;
   std::vector<WorkItem> items, items_env;
   std::vector<MatGroup> mats;
   std::vector<int> env_item0, env_nitems;
+  // FEM environments (their step kernels run one CTA per environment) and their extents
+  std::vector<int> fem_envs;
+  int* d_fem = nullptr;
+  size_t fem_cap = 0;
+  int fem_nv_max = 0, fem_act_max = 0;
   EnvDesc* d_desc = nullptr;
   size_t desc_cap = 0;
   WorkItem* d_items = nullptr;

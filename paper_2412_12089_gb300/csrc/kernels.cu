@@ -1955,6 +1955,14 @@ struct Timed {  // records the hook's events around one launch of class kc
   }
 };
 
+LaunchScope::LaunchScope(int k, cudaStream_t s) : kc(k), st(s) {
+  if (g_hook.before && (g_hook.kc == kc || g_hook.kc == -1)) g_hook.before(g_hook.user, kc, st);
+}
+LaunchScope::~LaunchScope() {
+  g_launches += 1;
+  if (g_hook.before && (g_hook.kc == kc || g_hook.kc == -1)) g_hook.after(g_hook.user, kc, st);
+}
+
 static inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
 // Six P2G CTAs per SM need the largest shared-memory carveout (the gather-heavy kernels keep

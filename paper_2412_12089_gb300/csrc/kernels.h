@@ -109,6 +109,21 @@ void launch_pose_io(const Launch& L, PoseIo mode, float* buf, int slot);
 void launch_adj_in(const Launch& L, const float* xb, const float* vb, const float* Cb, const float* Fb);
 void launch_adj_out(const Launch& L, StateRef src, float* xb, float* vb, float* Cb, float* Fb);
 
+// Tetrahedral-FEM environments (material FEM): one CTA per environment listed in `list`
+// (device, n entries) runs the whole control step (forward) or its reverse.  nv_max: the
+// largest vertex count of the listed environments; act_max: their largest action count.
+void launch_fem_forward(const Launch& L, const int* list, int n, int nv_max);
+void launch_fem_reverse(const Launch& L, const int* list, int n, int nv_max, int act_max);
+
+// Counts one kernel launch of class kc and records the timing hook's events around it (for
+// launchers outside kernels.cu).
+struct LaunchScope {
+  int kc;
+  cudaStream_t st;
+  LaunchScope(int k, cudaStream_t s);
+  ~LaunchScope();
+};
+
 // Binning: keys of the live state, LSD radix sort, per-env permutations.
 struct SortScratch {
   unsigned* keys[2];

@@ -66,6 +66,15 @@ struct EnvDesc {
   int n_caps;           // multi-capsule collider: capsules (pose entries 4 * n_caps), else 0
   float cap_offset[3];  // initial position of capsule j: pose0 + j * cap_offset
   float rparam[4];
+  // material FEM: elements (vertex indices, Dm^-1 row-major, rest volume, action index),
+  // inverse lumped vertex masses, and the law's constants
+  const int4* fem_tet;
+  const float* fem_dminv;
+  const float* fem_vol;
+  const int* fem_group;
+  const float* fem_inv_mass;
+  int n_tets;
+  float k_damp, ground_z, fem_alpha;
   // buffers
   float* slots;
   long long block;  // floats per state block = 25 * n_pad
@@ -92,6 +101,8 @@ struct EnvDesc {
   unsigned key_env;   // environment index placed in the high bits of the binning key
   int pad_;
 };
+
+constexpr int kMatFem = 4;  // material id of tetrahedral-FEM environments
 
 // Pose entries of an environment: 4 per rigid body.
 __host__ __device__ inline int pose_len(const EnvDesc& e) { return e.coll_kind == 4 ? 4 * e.n_caps : 4; }

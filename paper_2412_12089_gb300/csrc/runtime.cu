@@ -257,6 +257,9 @@ mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* 
     initial_pose(ctx->specs[e], q0);
     if (cudaMemcpy(desc[e].pose, q0, sizeof q0, cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(ctx, MPM_ERR_CUDA, "pose upload"));
+    const cudaError_t fe = fem_upload(ctx->specs[e], desc[e]);
+    if (fe == cudaErrorInvalidValue) return bail(fail(ctx, MPM_ERR_INVALID_ARG, "env %d: degenerate element", e));
+    if (fe != cudaSuccess) return bail(fail(ctx, MPM_ERR_CUDA, "FEM mesh upload"));
   }
   // grid tape for batched reverse passes: a share of the memory left after the arena
   ctx->g.want_tape = o.max_steps > 0 && !o.per_env_launch && o.grid_tape_fraction >= 0.0f;

@@ -46,6 +46,8 @@ struct Req {
   bool grad = false;
   std::vector<float> x, v, C, F, actions, rbar;
   std::vector<int32_t> group;
+  std::vector<int32_t> fem_tets, fem_group;  // material FEM: the request's mesh
+  std::vector<float> fem_rest;
   EnvLayout lay;
   char* mem = nullptr;
   EnvDesc desc{};
@@ -141,6 +143,7 @@ cudaError_t admit(mpm_server* s, Req& r, Group& scratch) {
     initial_pose(r.spec, q0);
     cudaMemcpy(r.desc.pose, q0, sizeof q0, cudaMemcpyHostToDevice);
   }
+  if ((e = fem_upload(r.spec, r.desc))) return e;
   if (r.A > 0) cudaMemcpy((void*)r.desc.act_env, r.actions.data(), (size_t)r.T * r.A * 4, cudaMemcpyHostToDevice);
   cudaMemcpy((void*)r.desc.rbar_env, r.rbar.data(), (size_t)r.T * 4, cudaMemcpyHostToDevice);
   // a one-environment group writes the state into slot 0
@@ -361,6 +364,14 @@ mpm_status mpm_submit(mpm_server* s, const mpm_request* q, uint64_t* ticket) {
   if (A > 0 && !q->actions) return sfail(s, MPM_ERR_INVALID_ARG, "actions are required");
   auto r = std::make_shared<Req>();
   r->spec = q->spec;
+  if (q->spec.material == kMatFem) {  // the mesh is read at admission: keep a copy
+    r->fem_tets.assign(q->spec.fem_tets, q->spec.fem_tets + 4 * (size_t)q->spec.n_tets);
+    r->fem_rest.assign(q->spec.fem_rest, q->spec.fem_rest + 3 * (size_t)q->spec.n_particles);
+    if (q->spec.fem_group) r->fem_group.assign(q->spec.fem_group, q->spec.fem_group + q->spec.n_tets);
+    r->spec.fem_tets = r->fem_tets.data();
+    r->spec.fem_rest = r->fem_rest.data();
+    r->spec.fem_group = q->spec.fem_group ? r->fem_group.data() : nullptr;
+  }
   r->T = q->horizon;
   r->A = A;
   r->grad = q->want_grad != 0;

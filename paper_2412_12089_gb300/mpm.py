@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmpm_gb300.so")
 
-MAT = {"neohookean": 0, "vonmises": 1, "fluid": 2, "muscle": 3}
+MAT = {"neohookean": 0, "vonmises": 1, "fluid": 2, "muscle": 3, "fem": 4}
 COLL = {"none": 0, "capsule": 1, "box": 2, "container": 3, "capsules": 4}
 REWARD = {"none": 0, "flat": 1, "reach": 2, "jump": 3}
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NUMERIC", 5: "DOMAIN", 6: "TIMEOUT",
@@ -41,7 +41,8 @@ class MpmEnvSpec(ct.Structure):
         ("bulk", ct.c_float), ("visc", ct.c_float), ("act_stress", ct.c_float), ("coll_dims", ct.c_float * 4),
         ("coll_mu", ct.c_float), ("alpha", ct.c_float), ("act_scale", ct.c_float * 4), ("ground_mu", ct.c_float),
         ("rparam", ct.c_float * 4), ("pose0", ct.c_float * 4), ("n_caps", ct.c_int32),
-        ("cap_offset", ct.c_float * 3),
+        ("cap_offset", ct.c_float * 3), ("n_tets", ct.c_int32), ("fem_tets", ct.c_void_p),
+        ("fem_rest", ct.c_void_p), ("fem_group", ct.c_void_p), ("k_damp", ct.c_float), ("ground_z", ct.c_float),
     ]
 
 
@@ -200,6 +201,16 @@ def to_c_spec(es) -> MpmEnvSpec:
     s.yield_stress, s.c_y = es.yield_stress, es.c_y
     s.bulk, s.visc, s.act_stress = es.bulk, es.visc, es.act_stress
     s.coll_mu, s.alpha, s.ground_mu = es.coll_mu, es.alpha, es.ground_mu
+    s.k_damp, s.ground_z = getattr(es, "k_damp", 0.0), getattr(es, "ground_z", 0.0)
+    if es.material == "fem":
+        # the struct points into these arrays: keep them alive as long as the struct
+        tets = np.ascontiguousarray(np.asarray(es.fem_tets, np.int32).reshape(-1, 4))
+        rest = np.ascontiguousarray(np.asarray(es.fem_rest, np.float32).reshape(-1, 3))
+        grp = None if es.fem_group is None else np.ascontiguousarray(np.asarray(es.fem_group, np.int32))
+        s.n_tets = tets.shape[0]
+        s.fem_tets, s.fem_rest = tets.ctypes.data, rest.ctypes.data
+        s.fem_group = grp.ctypes.data if grp is not None else None
+        s._keep = (tets, rest, grp)
     return s
 
 
@@ -217,7 +228,8 @@ def check(code, ctx=None, srv=None):
 # ----------------------------------------------------------------------------- same-name wrappers
 
 def mpm_create(specs, max_steps=0, per_env_launch=False, use_graphs=True, chunk=0, device=0, grid_tape_fraction=0.0):
-    arr = (MpmEnvSpec * len(specs))(*[to_c_spec(s) if not isinstance(s, MpmEnvSpec) else s for s in specs])
+    cs = [to_c_spec(s) if not isinstance(s, MpmEnvSpec) else s for s in specs]  # alive through the call
+    arr = (MpmEnvSpec * len(specs))(*cs)
     opt = MpmOptions(max_steps, 1 if per_env_launch else 0, 1 if use_graphs else 0, chunk, device, grid_tape_fraction)
     h = _P()
     code = lib().mpm_create(arr, len(specs), ct.byref(opt), ct.byref(h))
@@ -383,7 +395,8 @@ def mpm_submit(srv, spec, init, actions, horizon, want_grad=False, reward_adj=No
     a = np.ascontiguousarray(actions, np.float32).reshape(horizon, -1) if actions is not None else None
     rb = np.ascontiguousarray(reward_adj, np.float32) if reward_adj is not None else None
     req = MpmRequest()
-    req.spec = to_c_spec(spec)
+    cspec = to_c_spec(spec)  # alive through the call (FEM mesh arrays)
+    req.spec = cspec
     req.x, req.v, req.C, req.F = x.ctypes.data, v.ctypes.data, C.ctypes.data, F.ctypes.data
     req.group = g.ctypes.data if g is not None else None
     req.horizon = horizon
