@@ -254,6 +254,55 @@ def handflip_leg(cases, frames, warm, device):
             "unit": "env-frames/s", "cases": out}
 
 
+def fem_leg(n_envs, T, device, reps=3):
+    """SoftJumper as tetrahedral FEM (App. E: 80 substeps of 1/4800 s per control step,
+    stable neo-Hookean, damping, ground; 180 vertices and 440 elements per env): forward-only
+    env-steps/s, and fwd+adjoint rollouts of T control steps through the step kernels that run
+    one environment per CTA."""
+    import numpy as np
+    import torch
+
+    from paper_2412_12089_gb300 import mpm
+    from paper_2412_12089_gb300 import workloads as wl
+    from paper_2412_12089_gb300.batch import Batch
+
+    dev = torch.device("cuda", device)
+    w = wl.softjumper(n_envs=n_envs, seed=13, T=T)
+    b = Batch(w.specs, max_steps=T, device=device)
+    try:
+        acts = torch.as_tensor(w.actions).to(dev)
+        rbar = torch.ones(T, n_envs, device=dev)
+        agrad = torch.empty(T, n_envs, b.A, device=dev)
+        rew = torch.empty(n_envs, device=dev)
+        times = {"fwd": [], "fwd_adj": []}
+        for rep in range(reps + 1):
+            for kind in ("fwd", "fwd_adj"):
+                b.set_inits(w.inits)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for t in range(T):
+                    mpm.mpm_step(b.ctx, acts[t], rew, mpm.MPM_STEP_RECORD if kind == "fwd_adj" else 0)
+                if kind == "fwd_adj":
+                    mpm.mpm_backward(b.ctx, reward_adj=rbar, action_grad=agrad)
+                e1.record()
+                torch.cuda.synchronize()
+                if rep > 0:
+                    times[kind].append(e0.elapsed_time(e1) / 1e3)
+        code, flags = b.check_status()
+        nv, S = w.specs[0].n_particles, w.specs[0].substeps
+        out = {"workload": f"softjumper-fem-{n_envs}env-{nv}v-{w.specs[0].fem_tets.shape[0]}tet-{T}x{S}",
+               "envs": n_envs, "control_steps": T, "substeps": S,
+               "forward_env_steps_per_s": n_envs * T / min(times["fwd"]),
+               "fwd_adj_env_steps_per_s": n_envs * T / min(times["fwd_adj"]),
+               "fwd_adj_vertex_substeps_per_s": n_envs * T * S * nv / min(times["fwd_adj"]),
+               "rollout_ms_fwd_adj": 1e3 * min(times["fwd_adj"]), "device_gb": mpm.mpm_device_bytes(b.ctx) / 1e9,
+               "status_flags": int(np.count_nonzero(flags))}
+    finally:
+        b.close()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -295,6 +344,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=32, help="requests in the serving leg (0 = off)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate of the serving leg (1/s)")
     ap.add_argument("--handflip-frames", type=int, default=30, help="timed frames of the HandFlip-like leg (0 = off)")
+    ap.add_argument("--fem-envs", type=int, default=2048, help="envs of the SoftJumper FEM leg (0 = off)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -458,6 +508,10 @@ def main():
     if args.handflip_frames > 0 and rank == 0:
         handflip = handflip_leg([(128, 2500), (32, 30000)], args.handflip_frames, 3, local)
 
+    fem_out = None
+    if args.fem_envs > 0 and rank == 0:
+        fem_out = fem_leg(args.fem_envs, 16, local)
+
     cpu = None
     if not args.no_cpu and rank == 0:
         v, dt, sample = cpu_baseline(T)
@@ -478,6 +532,7 @@ def main():
             "per_env_launch": per_env,
             "serving": serve,
             "handflip": handflip,
+            "fem": fem_out,
             "clocks": clk, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "status": int(code),
         }

@@ -6,6 +6,7 @@ import time
 import numpy as np
 import pytest
 
+from oracle import fem
 from oracle import oracle as orc
 from paper_2412_12089_gb300 import mpm
 from paper_2412_12089_gb300 import workloads as wl
@@ -21,7 +22,8 @@ def mixed_requests(seed=0):
     d = wl.dough(n_envs=2, seed=seed, n_range=(800, 3000), substeps=6, T=5)
     f = wl.fluid(n_envs=2, seed=seed + 1, n=1500, substeps=5, T=4)
     j = wl.jumper(n_envs=1, seed=seed + 2, n=2500, G=48, substeps=4, T=3)
-    for w in (d, f, j):
+    sj = wl.softjumper(n_envs=1, seed=seed + 3, T=3)  # tetrahedral FEM
+    for w in (d, f, j, sj):
         for e in range(w.n_envs):
             T = int(rng.integers(2, w.T + 1))
             A = w.specs[e].action_dim
@@ -57,10 +59,14 @@ def test_mixed_stream_equals_alone():
     for i, (req, res) in enumerate(zip(reqs, results)):
         assert res["status"] == 0, (i, res["status"])
         alone = run_alone(req)
+        # FEM element forces accumulate in shared memory in a run-dependent order, and 3 x 80
+        # stiff substeps grow that rounding to ~1e-5 in the velocity-based reward: FEM
+        # requests are held to the oracle's horizon tolerance instead
+        tol = 1e-3 if req[0].material == "fem" else 1e-5
         assert rel_err(res["x_final"], alone["x_final"]) < 1e-5, i
-        assert np.allclose(res["rewards"], alone["rewards"], rtol=1e-5, atol=1e-7), i
+        assert np.allclose(res["rewards"], alone["rewards"], rtol=tol, atol=1e-7), i
         if req[4] and req[0].action_dim:
-            assert rel_err(res["action_grad"], alone["action_grad"]) < 1e-4, i
+            assert rel_err(res["action_grad"], alone["action_grad"]) < max(tol, 1e-4), i
         # at most max_resident requests resident at once; some overlapped in time
         others = [r for r in results if r is not res]
         if any(o["admit_ms"] < res["finish_ms"] and res["admit_ms"] < o["finish_ms"] for o in others):
@@ -112,3 +118,22 @@ def test_poll_not_ready_then_ok_and_budget():
         assert ei.value.code == 8  # BUDGET
     finally:
         mpm.mpm_server_destroy(tiny)
+
+
+def test_served_fem_rollout_matches_oracle():
+    w = wl.softjumper(n_envs=1, seed=19, T=2)
+    s, init = w.specs[0], w.inits[0]
+    acts = w.actions[:2, 0, :s.n_groups]
+    srv = mpm.mpm_server_create(mem_fraction=0.3, max_resident=2)
+    try:
+        t = mpm.mpm_submit(srv, s, init, acts, 2, want_grad=True, reward_adj=np.ones(2, np.float32))
+        res = mpm.mpm_wait(srv, t, 120000.0)
+    finally:
+        mpm.mpm_server_destroy(srv)
+    assert res["status"] == 0
+    m = fem.make_mesh(s)
+    x, v, r, _ = fem.rollout(m, init.x, init.v, acts)
+    assert rel_err(res["x_final"], x) < 1e-3
+    assert np.allclose(res["rewards"], r, rtol=1e-3, atol=1e-5)
+    ag, _, _, _ = fem.rollout_adj(m, init.x, init.v, acts, rbar=np.ones(2))
+    assert rel_err(res["action_grad"], ag) < 1e-3
