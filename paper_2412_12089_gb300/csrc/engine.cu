@@ -286,7 +286,7 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
   g.P = 0;
   g.tiles = 0;
   g.fem_envs.clear();
-  g.fem_nv_max = g.fem_act_max = 0;
+  g.fem_nv_max = g.fem_act_max = g.fem_nt_max = 0;
   int G_max = 8;
   for (int e = 0; e < g.n_envs; ++e) {
     const auto& s = specs[e];
@@ -294,6 +294,7 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
       g.fem_envs.push_back(e);
       g.fem_nv_max = std::max(g.fem_nv_max, s.n_particles);
       g.fem_act_max = std::max(g.fem_act_max, s.n_groups);
+      g.fem_nt_max = std::max(g.fem_nt_max, s.n_tets);
     } else {
       g.S_max = std::max(g.S_max, s.substeps);
     }
@@ -472,7 +473,7 @@ void substeps_forward(Group& g, const Launch& L, const std::vector<MatGroup>& ma
 // fem: the FEM environments among L's (device list, count, largest vertex and action counts).
 struct FemList {
   const int* list = nullptr;
-  int n = 0, nv_max = 0, act_max = 0;
+  int n = 0, nv_max = 0, act_max = 0, nt_max = 0;
 };
 
 void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, const float* rbar, float* agrad,
@@ -481,7 +482,7 @@ void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, con
   launch_reward_adj(L, rbar, n_tot);
   if (obs) launch_obs_adj(L, *obs, 0);  // observation of the step's end state
   launch_adj_ref(L);
-  launch_fem_reverse(L, fem.list, fem.n, fem.nv_max, fem.act_max);
+  launch_fem_reverse(L, fem.list, fem.n, fem.nv_max, fem.act_max, fem.nt_max);
   // recompute substep states 1..S-1 into the ring (envs with S > k + 1); the grid of each
   // substep comes from the tape when it was kept, else P2G rebuilds it
   for (int k = 0; k + 1 < S; ++k) {
@@ -574,7 +575,7 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
   if (!per_env) {
     Launch L = group_launch(g, st);
     launch_step_begin(L, act_in, a_max, record);
-    launch_fem_forward(L, g.d_fem, (int)g.fem_envs.size(), g.fem_nv_max);
+    launch_fem_forward(L, g.d_fem, (int)g.fem_envs.size(), g.fem_nv_max, g.fem_nt_max);
     if (g.S_max > 0) {
       bin_envs(L, 0, g.P, g.cell_bits, g.key_bits, g.sort);
       substeps_forward(g, L, g.mats, g.S_max, record && g.tape.cap > 0 ? &g.tape : nullptr);
@@ -588,7 +589,7 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
     Launch L = env_launch(g, e, st);
     if (g.spec[e].material == kMatFem) {
       launch_step_begin(L, act_in, a_max, record);
-      launch_fem_forward(L, g.d_fem + fem_i++, 1, g.spec[e].n_particles);
+      launch_fem_forward(L, g.d_fem + fem_i++, 1, g.spec[e].n_particles, g.spec[e].n_tets);
       launch_reward_end(L, rew, record);
       continue;
     }
@@ -606,7 +607,7 @@ void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad,
                      const ObsAdj* obs) {
   if (g.n_envs == 0) return;
   if (!per_env) {
-    FemList fem{g.d_fem, (int)g.fem_envs.size(), g.fem_nv_max, g.fem_act_max};
+    FemList fem{g.d_fem, (int)g.fem_envs.size(), g.fem_nv_max, g.fem_act_max, g.fem_nt_max};
     reverse_step(group_launch(g, st), g.mats, g.S_max, rbar, agrad, n_tot, a_max, g.tape.cap > 0 ? &g.tape : nullptr,
                  obs, fem);
     return;
@@ -614,7 +615,7 @@ void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad,
   int fem_i = 0;
   for (int e = 0; e < g.n_envs; ++e) {
     if (g.spec[e].material == kMatFem) {
-      FemList fem{g.d_fem + fem_i++, 1, g.spec[e].n_particles, g.spec[e].n_groups};
+      FemList fem{g.d_fem + fem_i++, 1, g.spec[e].n_particles, g.spec[e].n_groups, g.spec[e].n_tets};
       reverse_step(env_launch(g, e, st), {}, 0, rbar, agrad, n_tot, a_max, nullptr, obs, fem);
       continue;
     }

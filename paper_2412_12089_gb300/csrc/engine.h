@@ -64,7 +64,7 @@ struct Group {
   std::vector<int> fem_envs;
   int* d_fem = nullptr;
   size_t fem_cap = 0;
-  int fem_nv_max = 0, fem_act_max = 0;
+  int fem_nv_max = 0, fem_act_max = 0, fem_nt_max = 0;
   EnvDesc* d_desc = nullptr;
   size_t desc_cap = 0;
   WorkItem* d_items = nullptr;

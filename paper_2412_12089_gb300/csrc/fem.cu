@@ -22,12 +22,51 @@
 namespace mpm {
 
 constexpr int kFemThreads = 256;
+constexpr int kFemStageElems = 1024;  // meshes up to this many elements keep them in shared memory
 
 namespace {
 
 struct FemLaw {
   float mu, lam, alpha, kd;
 };
+
+// Element data as the substeps read it: in shared memory (staged once per control step, with
+// the step's activation per element) for meshes of up to kFemStageElems elements, else the
+// environment's global arrays and the activation from the action vector.
+struct Elems {
+  const int4* tet;
+  const float* dminv;
+  const float* vol;
+  const float* a;  // per-element activation, or NULL: act_scale * act[group]
+  const int* group;
+  const float* act;
+  float act_scale;
+  __device__ __forceinline__ float act_of(int el) const { return a ? a[el] : act_scale * act[group[el]]; }
+};
+
+// Shared-memory bytes reserved for staged element data when the largest mesh of a launch has
+// nt_max elements: every mesh of up to kFemStageElems elements then fits.
+__host__ __device__ __forceinline__ size_t stage_bytes(int nt_max) {
+  return (size_t)(nt_max < kFemStageElems ? nt_max : kFemStageElems) * (16 + 36 + 4 + 4);
+}
+
+// Stage (when it fits) the element data behind `base` (16-byte aligned shared memory).
+__device__ Elems stage_elems(const EnvDesc& e, const float* act, char* base) {
+  const int nt = e.n_tets;
+  const float* actv = act + e.n_coll_act;
+  if (nt > kFemStageElems) return Elems{e.fem_tet, e.fem_dminv, e.fem_vol, nullptr, e.fem_group, actv, e.act_stress};
+  int4* tet = reinterpret_cast<int4*>(base);
+  float* dmi = reinterpret_cast<float*>(tet + nt);
+  float* vol = dmi + 9 * nt;
+  float* a = vol + nt;
+  for (int el = threadIdx.x; el < nt; el += blockDim.x) {
+    tet[el] = e.fem_tet[el];
+    vol[el] = e.fem_vol[el];
+    a[el] = e.act_stress * actv[e.fem_group[el]];
+  }
+  for (int q = threadIdx.x; q < 9 * nt; q += blockDim.x) dmi[q] = e.fem_dminv[q];
+  return Elems{tet, dmi, vol, a, e.fem_group, actv, e.act_stress};
+}
 
 __device__ __forceinline__ void cross3(const float* a, const float* b, float* c) {
   c[0] = a[1] * b[2] - a[2] * b[1];
@@ -112,22 +151,18 @@ __device__ __forceinline__ void stress_adj(const FemLaw& m, const float* F, floa
   *ab = -m.lam * cp;
 }
 
-__device__ __forceinline__ float elem_act(const EnvDesc& e, const float* act, int el) {
-  return e.act_stress * act[e.n_coll_act + e.fem_group[el]];
-}
-
 // Forces of every element at (X, V) into Fo (zeroed by the caller); J <= 0 sets status 4.
-__device__ void element_forces(const EnvDesc& e, const FemLaw& m, const float* X, const float* V, float* Fo, int ns,
-                               const float* act, int& status) {
+__device__ void element_forces(const EnvDesc& e, const FemLaw& m, const Elems& E, const float* X, const float* V,
+                               float* Fo, int ns, int& status) {
   for (int el = threadIdx.x; el < e.n_tets; el += blockDim.x) {
-    const int4 t = e.fem_tet[el];
-    const float* Dmi = e.fem_dminv + 9 * el;
+    const int4 t = E.tet[el];
+    const float* Dmi = E.dminv + 9 * el;
     float Dm[9], Ds[9], F[9], P[9], H[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Dm[q] = Dmi[q];
     edge_mat(X, ns, t, Ds);
     mul3(Ds, Dm, F);
-    const float J = stress(m, F, elem_act(e, act, el), P);
+    const float J = stress(m, F, E.act_of(el), P);
     if (!(J > 0.0f)) status |= 4;
     if (m.kd != 0.0f) {
       float Vs[9], Fd[9];
@@ -137,7 +172,7 @@ __device__ void element_forces(const EnvDesc& e, const FemLaw& m, const float* X
       for (int q = 0; q < 9; ++q) P[q] += m.kd * Fd[q];
     }
     mul3bt(P, Dm, H);
-    const float nv0 = -e.fem_vol[el];
+    const float nv0 = -E.vol[el];
     const int vi[3] = {t.y, t.z, t.w};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -158,12 +193,12 @@ __device__ __forceinline__ bool on_ground(const EnvDesc& e, float z, const float
   return z <= e.ground_z && w[2] < 0.0f;
 }
 
-__device__ void fem_substep(const EnvDesc& e, const FemLaw& m, float* X, float* V, float* Fo, int ns,
-                            const float* act, int& status) {
+__device__ void fem_substep(const EnvDesc& e, const FemLaw& m, const Elems& E, float* X, float* V, float* Fo, int ns,
+                            int& status) {
   const int nv = e.n;
   for (int q = threadIdx.x; q < 3 * ns; q += blockDim.x) Fo[q] = 0.f;
   __syncthreads();
-  element_forces(e, m, X, V, Fo, ns, act, status);
+  element_forces(e, m, E, X, V, Fo, ns, status);
   __syncthreads();
   const float dt = e.dt;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
@@ -222,10 +257,11 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_forward(const EnvDesc* __re
   float* dst = e.slots + (long long)c.next * e.block;
   const float* act = e.act + (long long)c.live * e.A;
   load_xv(src, np, nv, ns, X, V);
+  const Elems E = stage_elems(e, act, reinterpret_cast<char*>(sm + 9 * ns));
   __syncthreads();
   const FemLaw m = law_of(e);
   int status = 0;
-  for (int k = 0; k < e.S; ++k) fem_substep(e, m, X, V, Fo, ns, act, status);
+  for (int k = 0; k < e.S; ++k) fem_substep(e, m, E, X, V, Fo, ns, status);
   store_xv(dst, np, nv, ns, X, V);
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
 #pragma unroll
@@ -249,6 +285,7 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
   const long long np = e.n_pad;
   const int nv = e.n, S = e.S;
   float *X = sm, *V = sm + 3 * ns, *Fo = sm + 6 * ns, *XB = sm + 9 * ns, *VB = sm + 12 * ns, *AB = sm + 15 * ns;
+  // staged element data after AB (a_stride rounded up to 4 floats keeps it 16-byte aligned)
   const int slot = c.base + c.rev;
   const float* src = e.slots + (long long)slot * e.block;
   const float* act = e.act + (long long)slot * e.A;
@@ -257,9 +294,10 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
   // recompute substep states 1..S-1 into ring blocks 0..S-2
   load_xv(src, np, nv, ns, X, V);
   for (int g = threadIdx.x; g < a_stride; g += blockDim.x) AB[g] = 0.0f;
+  const Elems E = stage_elems(e, act, reinterpret_cast<char*>(AB + a_stride));
   __syncthreads();
   for (int k = 0; k + 1 < S; ++k) {
-    fem_substep(e, m, X, V, Fo, ns, act, status);
+    fem_substep(e, m, E, X, V, Fo, ns, status);
     store_xv(e.ring + (long long)k * e.block, np, nv, ns, X, V);
   }
   const float* adj = c.par ? e.adj1 : e.adj0;
@@ -271,7 +309,7 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
     load_xv(k == 0 ? src : e.ring + (long long)(k - 1) * e.block, np, nv, ns, X, V);
     for (int q = threadIdx.x; q < 3 * ns; q += blockDim.x) Fo[q] = 0.f;
     __syncthreads();
-    element_forces(e, m, X, V, Fo, ns, act, status);
+    element_forces(e, m, E, X, V, Fo, ns, status);
     __syncthreads();
     // vertices: x' = x + dt w passes x-bar through and adds dt x-bar to w-bar; the ground
     // projection; w = v + dt (f / m + g) gives v-bar = w-bar and f-bar = dt w-bar / m
@@ -307,8 +345,8 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
     // elements: H-bar columns f-bar_{c+1} - f-bar_0; P-bar = -V0 H-bar Dm^-1; F-bar by the
     // energy's Hessian; Fdot-bar = k_damp P-bar; Ds-bar = F-bar Dm^-T, Vs-bar = Fdot-bar Dm^-T
     for (int el = threadIdx.x; el < e.n_tets; el += blockDim.x) {
-      const int4 t = e.fem_tet[el];
-      const float* Dmi = e.fem_dminv + 9 * el;
+      const int4 t = E.tet[el];
+      const float* Dmi = E.dminv + 9 * el;
       const int vi[3] = {t.y, t.z, t.w};
       float Dm[9], Hb[9], Pb[9], Ds[9], F[9], Fb[9], Db[9], ab;
 #pragma unroll
@@ -320,12 +358,12 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
         for (int cc = 0; cc < 3; ++cc) Hb[3 * k2 + cc] = Fo[k2 * ns + vi[cc]] - f0;
       }
       mul3(Hb, Dm, Pb);
-      const float nv0 = -e.fem_vol[el];
+      const float nv0 = -E.vol[el];
 #pragma unroll
       for (int q = 0; q < 9; ++q) Pb[q] *= nv0;
       edge_mat(X, ns, t, Ds);
       mul3(Ds, Dm, F);
-      stress_adj(m, F, elem_act(e, act, el), Pb, Fb, &ab);
+      stress_adj(m, F, E.act_of(el), Pb, Fb, &ab);
       atomicAdd(&AB[e.fem_group[el]], ab);
       mul3bt(Fb, Dm, Db);
 #pragma unroll
@@ -365,16 +403,16 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
   (void)status;
 }
 
-size_t fem_smem(int ns, int a_stride, bool reverse) {
-  return sizeof(float) * (reverse ? (size_t)15 * ns + (size_t)a_stride : (size_t)9 * ns);
+size_t fem_smem(int ns, int a_stride, int nt_max, bool reverse) {
+  return sizeof(float) * (reverse ? (size_t)15 * ns + (size_t)a_stride : (size_t)9 * ns) + stage_bytes(nt_max);
 }
 
 }  // namespace
 
-void launch_fem_forward(const Launch& L, const int* list, int n, int nv_max) {
+void launch_fem_forward(const Launch& L, const int* list, int n, int nv_max, int nt_max) {
   if (n <= 0) return;
   const int ns = (nv_max + 31) / 32 * 32;
-  const size_t sm = fem_smem(ns, 0, false);
+  const size_t sm = fem_smem(ns, 0, nt_max, false);
   static size_t attr = 48 * 1024;
   if (sm > attr) {
     cudaFuncSetAttribute(k_fem_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -384,11 +422,11 @@ void launch_fem_forward(const Launch& L, const int* list, int n, int nv_max) {
   k_fem_forward<<<n, kFemThreads, sm, L.stream>>>(L.envs, list, ns);
 }
 
-void launch_fem_reverse(const Launch& L, const int* list, int n, int nv_max, int act_max) {
+void launch_fem_reverse(const Launch& L, const int* list, int n, int nv_max, int act_max, int nt_max) {
   if (n <= 0) return;
   const int ns = (nv_max + 31) / 32 * 32;
-  const int a_stride = std::max(act_max, 1);
-  const size_t sm = fem_smem(ns, a_stride, true);
+  const int a_stride = (std::max(act_max, 1) + 3) / 4 * 4;
+  const size_t sm = fem_smem(ns, a_stride, nt_max, true);
   static size_t attr = 48 * 1024;
   if (sm > attr) {
     cudaFuncSetAttribute(k_fem_reverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -111,9 +111,10 @@ void launch_adj_out(const Launch& L, StateRef src, float* xb, float* vb, float* 
 
 // Tetrahedral-FEM environments (material FEM): one CTA per environment listed in `list`
 // (device, n entries) runs the whole control step (forward) or its reverse.  nv_max: the
-// largest vertex count of the listed environments; act_max: their largest action count.
-void launch_fem_forward(const Launch& L, const int* list, int n, int nv_max);
-void launch_fem_reverse(const Launch& L, const int* list, int n, int nv_max, int act_max);
+// largest vertex count of the listed environments; act_max, nt_max: their largest action and
+// element counts.
+void launch_fem_forward(const Launch& L, const int* list, int n, int nv_max, int nt_max);
+void launch_fem_reverse(const Launch& L, const int* list, int n, int nv_max, int act_max, int nt_max);
 
 // Counts one kernel launch of class kc and records the timing hook's events around it (for
 // launchers outside kernels.cu).
