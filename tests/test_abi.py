@@ -61,6 +61,28 @@ def test_invalid_spec_rejected_without_gpu_work(lib):
     assert ei.value.code == 1 and "grid_res" in str(ei.value)
 
 
+def test_invalid_fem_meshes_rejected_without_gpu_work(lib):
+    """FEM specs: vertex indices, element groups, collider and mesh size are validated first."""
+    import numpy as np
+
+    from paper_2412_12089_gb300 import mpm
+    from paper_2412_12089_gb300 import workloads as wl
+
+    good = wl.softjumper(n_envs=1, T=1).specs[0]
+    tets = good.fem_tets.copy()
+    tets[7, 2] = good.n_particles  # out of range
+    grp = good.fem_group.copy()
+    grp[3] = good.n_groups
+    cases = [(good.replace(fem_tets=tets), "fem_tets"), (good.replace(fem_group=grp), "fem_group"),
+             (good.replace(collider="capsule", act_map=(0,)), "collider"),
+             (good.replace(nu=0.0), "nu"),
+             (good.replace(n_particles=3000, fem_rest=np.zeros((3000, 3), np.float32)), "n_particles")]
+    for spec, word in cases:
+        with pytest.raises(mpm.MpmError) as ei:
+            mpm.mpm_create([spec])
+        assert ei.value.code == 1 and word in str(ei.value), (word, str(ei.value))
+
+
 def test_product_path_never_imports_oracle():
     """The package sources do not reference the oracle (it is test infrastructure)."""
     pkg = os.path.join(ROOT, "paper_2412_12089_gb300")
