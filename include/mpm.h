@@ -123,7 +123,7 @@ typedef struct {
      * lumped masses rho V0 / 4, gravity, a semi-implicit Euler substep, and the ground z =
      * ground_z (a vertex at or below it moving down stops, with Coulomb friction ground_mu).
      * No grid is used (grid_res only sizes an unused minimum arena; 8 is enough), the collider
-     * must be MPM_COLL_NONE, n_particles <= 4096.  C and F of the state are not used (get_state
+     * must be MPM_COLL_NONE, n_particles <= 1024, n_tets <= 1024.  C and F of the state are not used (get_state
      * returns C = 0, F = I).  The mesh arrays are host memory, read during mpm_create (and
      * mpm_submit), not kept.
      */

@@ -47,10 +47,10 @@ const char* check_spec(const mpm_env_spec& s) {
       !(s.E > 0.f && s.nu >= 0.f && s.nu < 0.5f))
     return "E/nu";
   if (s.material == kMatFem) {
-    if (s.n_particles > kFemMaxVerts) return "n_particles (FEM meshes hold at most 2048 vertices)";
+    if (s.n_particles > kFemMaxVerts) return "n_particles (FEM meshes hold at most 1024 vertices)";
     if (s.collider != MPM_COLL_NONE || s.n_coll_act != 0) return "collider (FEM has none)";
     if (!(s.nu > 0.f)) return "nu (FEM needs lambda > 0)";
-    if (s.n_tets < 1 || s.n_tets > (1 << 20) || !s.fem_tets || !s.fem_rest) return "fem mesh";
+    if (s.n_tets < 1 || s.n_tets > kFemMaxElems || !s.fem_tets || !s.fem_rest) return "fem mesh (1..1024 elements)";
     if (!(s.k_damp >= 0.f)) return "k_damp";
     for (long long e = 0; e < s.n_tets; ++e) {
       for (int c = 0; c < 4; ++c)
@@ -97,12 +97,35 @@ cudaError_t fem_upload(const mpm_env_spec& s, const EnvDesc& d) {
     grp[e] = s.fem_group ? s.fem_group[e] : 0;
   }
   for (long long i = 0; i < nv; ++i) inv_mass[i] = mass[i] > 0.0 ? (float)(1.0 / mass[i]) : 0.0f;
+  // incidence lists by counting sort (entries in increasing element order)
+  const long long ng = std::max(s.n_groups, 1);
+  std::vector<int> voff((size_t)d.n_pad + 1, 0), vinc((size_t)(4 * nt)), goff((size_t)ng + 1, 0), ginc((size_t)nt);
+  for (long long e = 0; e < nt; ++e) {
+    for (int c = 0; c < 4; ++c) voff[s.fem_tets[4 * e + c] + 1] += 1;
+    goff[grp[e] + 1] += 1;
+  }
+  for (long long i = 0; i < (long long)d.n_pad; ++i) voff[i + 1] += voff[i];
+  for (long long g = 0; g < ng; ++g) goff[g + 1] += goff[g];
+  {
+    std::vector<int> vc(voff.begin(), voff.end() - 1), gc(goff.begin(), goff.end() - 1);
+    for (long long e = 0; e < nt; ++e) {
+      for (int c = 0; c < 4; ++c) vinc[vc[s.fem_tets[4 * e + c]]++] = (int)(4 * e + c);
+      ginc[gc[grp[e]]++] = (int)e;
+    }
+  }
   cudaError_t err;
   if ((err = cudaMemcpy((void*)d.fem_tet, tet.data(), sizeof(int4) * nt, cudaMemcpyHostToDevice))) return err;
   if ((err = cudaMemcpy((void*)d.fem_dminv, dminv.data(), sizeof(float) * 9 * nt, cudaMemcpyHostToDevice))) return err;
   if ((err = cudaMemcpy((void*)d.fem_vol, vol.data(), sizeof(float) * nt, cudaMemcpyHostToDevice))) return err;
   if ((err = cudaMemcpy((void*)d.fem_group, grp.data(), sizeof(int) * nt, cudaMemcpyHostToDevice))) return err;
-  return cudaMemcpy((void*)d.fem_inv_mass, inv_mass.data(), sizeof(float) * d.n_pad, cudaMemcpyHostToDevice);
+  if ((err = cudaMemcpy((void*)d.fem_inv_mass, inv_mass.data(), sizeof(float) * d.n_pad, cudaMemcpyHostToDevice)))
+    return err;
+  if ((err = cudaMemcpy((void*)d.fem_vinc_off, voff.data(), sizeof(int) * voff.size(), cudaMemcpyHostToDevice)))
+    return err;
+  if ((err = cudaMemcpy((void*)d.fem_vinc, vinc.data(), sizeof(int) * vinc.size(), cudaMemcpyHostToDevice))) return err;
+  if ((err = cudaMemcpy((void*)d.fem_ginc_off, goff.data(), sizeof(int) * goff.size(), cudaMemcpyHostToDevice)))
+    return err;
+  return cudaMemcpy((void*)d.fem_ginc, ginc.data(), sizeof(int) * ginc.size(), cudaMemcpyHostToDevice);
 }
 
 EnvLayout env_layout(const mpm_env_spec& s, int n_slots, bool tape, bool own, int T) {
@@ -126,9 +149,10 @@ EnvLayout env_layout(const mpm_env_spec& s, int n_slots, bool tape, bool own, in
   L.tile = cur;  cur = align256(cur + (size_t)TG3 * 4);
   L.pose = cur;  cur = align256(cur + (size_t)n_slots * kPose * 4);
   L.act = cur;   cur = align256(cur + (size_t)n_slots * A * 4);
-  if (s.material == kMatFem) {  // element records, Dm^-1, rest volumes, groups, inverse masses
-    const size_t nt = (size_t)std::max(s.n_tets, 0);
-    L.fem = cur;   cur = align256(cur + nt * (16 + 36 + 4 + 4) + (size_t)n_pad * 4);
+  if (s.material == kMatFem) {  // element records, Dm^-1, rest volumes, groups, inverse masses, CSRs
+    const size_t nt = (size_t)std::max(s.n_tets, 0), ng = (size_t)std::max(s.n_groups, 1);
+    L.fem = cur;
+    cur = align256(cur + nt * (16 + 36 + 4 + 4) + (size_t)n_pad * 4 + ((size_t)n_pad + 1 + 4 * nt + ng + 1 + nt) * 4);
   }
   if (own) {
     L.acc = cur;       cur = align256(cur + (size_t)(ACC_ACT + A) * 4);
@@ -199,6 +223,10 @@ void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base,
     d.fem_vol = d.fem_dminv + 9 * nt;
     d.fem_group = (const int*)(d.fem_vol + nt);
     d.fem_inv_mass = (const float*)(d.fem_group + nt);
+    d.fem_vinc_off = (const int*)(d.fem_inv_mass + L.n_pad);
+    d.fem_vinc = d.fem_vinc_off + L.n_pad + 1;
+    d.fem_ginc_off = d.fem_vinc + 4 * nt;
+    d.fem_ginc = d.fem_ginc_off + std::max(s.n_groups, 1) + 1;
     d.n_tets = s.n_tets;
     d.k_damp = s.k_damp;
     d.ground_z = s.ground_z;

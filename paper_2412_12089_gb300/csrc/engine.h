@@ -16,7 +16,9 @@
 namespace mpm {
 
 constexpr int kChunk = 256;  // particles per work item (CTA)
-constexpr int kFemMaxVerts = 2048;  // vertices of one FEM mesh (the step kernels hold them in shared memory)
+// Largest FEM mesh: the step kernels hold its vertices and per-element corner terms in shared memory.
+constexpr int kFemMaxVerts = 1024;
+constexpr int kFemMaxElems = 1024;
 
 const char* check_spec(const mpm_env_spec& s);
 

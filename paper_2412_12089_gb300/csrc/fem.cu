@@ -4,9 +4,11 @@
 //
 // A mesh of a few hundred vertices is far too small to fill the GPU one substep at a time, so
 // one CTA runs a whole control step of one environment with the vertex state in shared memory:
-// per substep, the elements add their forces into a shared force array (shared atomics), then
-// the vertices integrate.  Global memory is touched only at the step's ends (and, in reverse,
-// for the recomputed substep states).  The CTAs of all FEM environments run side by side.
+// per substep, each element writes its four corner forces to shared memory, then each vertex
+// sums the corners of its elements through an incidence list (no atomics, so results are
+// deterministic) and integrates.  Global memory is touched only at the step's ends (and, in
+// reverse, for the recomputed substep states).  The CTAs of all FEM environments run side by
+// side.
 //
 // Per element e with vertices (i0..i3): Ds = [x_i1 - x_i0, x_i2 - x_i0, x_i3 - x_i0],
 // F = Ds Dm^-1, J = det F, I_C = |F|^2, a = act_scale * action[group(e)],
@@ -22,51 +24,12 @@
 namespace mpm {
 
 constexpr int kFemThreads = 256;
-constexpr int kFemStageElems = 1024;  // meshes up to this many elements keep them in shared memory
 
 namespace {
 
 struct FemLaw {
   float mu, lam, alpha, kd;
 };
-
-// Element data as the substeps read it: in shared memory (staged once per control step, with
-// the step's activation per element) for meshes of up to kFemStageElems elements, else the
-// environment's global arrays and the activation from the action vector.
-struct Elems {
-  const int4* tet;
-  const float* dminv;
-  const float* vol;
-  const float* a;  // per-element activation, or NULL: act_scale * act[group]
-  const int* group;
-  const float* act;
-  float act_scale;
-  __device__ __forceinline__ float act_of(int el) const { return a ? a[el] : act_scale * act[group[el]]; }
-};
-
-// Shared-memory bytes reserved for staged element data when the largest mesh of a launch has
-// nt_max elements: every mesh of up to kFemStageElems elements then fits.
-__host__ __device__ __forceinline__ size_t stage_bytes(int nt_max) {
-  return (size_t)(nt_max < kFemStageElems ? nt_max : kFemStageElems) * (16 + 36 + 4 + 4);
-}
-
-// Stage (when it fits) the element data behind `base` (16-byte aligned shared memory).
-__device__ Elems stage_elems(const EnvDesc& e, const float* act, char* base) {
-  const int nt = e.n_tets;
-  const float* actv = act + e.n_coll_act;
-  if (nt > kFemStageElems) return Elems{e.fem_tet, e.fem_dminv, e.fem_vol, nullptr, e.fem_group, actv, e.act_stress};
-  int4* tet = reinterpret_cast<int4*>(base);
-  float* dmi = reinterpret_cast<float*>(tet + nt);
-  float* vol = dmi + 9 * nt;
-  float* a = vol + nt;
-  for (int el = threadIdx.x; el < nt; el += blockDim.x) {
-    tet[el] = e.fem_tet[el];
-    vol[el] = e.fem_vol[el];
-    a[el] = e.act_stress * actv[e.fem_group[el]];
-  }
-  for (int q = threadIdx.x; q < 9 * nt; q += blockDim.x) dmi[q] = e.fem_dminv[q];
-  return Elems{tet, dmi, vol, a, e.fem_group, actv, e.act_stress};
-}
 
 __device__ __forceinline__ void cross3(const float* a, const float* b, float* c) {
   c[0] = a[1] * b[2] - a[2] * b[1];
@@ -151,18 +114,56 @@ __device__ __forceinline__ void stress_adj(const FemLaw& m, const float* F, floa
   *ab = -m.lam * cp;
 }
 
-// Forces of every element at (X, V) into Fo (zeroed by the caller); J <= 0 sets status 4.
-__device__ void element_forces(const EnvDesc& e, const FemLaw& m, const Elems& E, const float* X, const float* V,
-                               float* Fo, int ns, int& status) {
+__device__ __forceinline__ FemLaw law_of(const EnvDesc& e) { return FemLaw{e.mu, e.lam, e.fem_alpha, e.k_damp}; }
+
+__device__ __forceinline__ float elem_act(const EnvDesc& e, const float* act, int el) {
+  return e.act_stress * act[e.n_coll_act + e.fem_group[el]];
+}
+
+// Corner terms of an element for the four vertices from the 3x3 edge-column terms M
+// (row k = component, column c = edge c): vertex c+1 gets M[:, c], vertex 0 gets -sum_c M[:, c].
+// Written to T[12 el + 3 corner + k].
+__device__ __forceinline__ void put_corners(float* T, int el, const float* M, float scale) {
+  float* t = T + 12 * el;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float v = scale * M[3 * k + c];
+      t[3 * (c + 1) + k] = v;
+      s += v;
+    }
+    t[k] = -s;
+  }
+}
+
+// Sum of vertex i's corner terms (incidence list in shared memory).
+__device__ __forceinline__ void gather_corners(const float* T, const int* voff, const int* vinc, int i, float* out) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  for (int j = voff[i]; j < voff[i + 1]; ++j) {
+    const float* t = T + 3 * vinc[j];
+    a0 += t[0];
+    a1 += t[1];
+    a2 += t[2];
+  }
+  out[0] = a0;
+  out[1] = a1;
+  out[2] = a2;
+}
+
+// Corner forces of every element at (X, V) into EF; J <= 0 sets status 4.
+__device__ void element_forces(const EnvDesc& e, const FemLaw& m, const float* act, const float* X, const float* V,
+                               int ns, float* EF, int& status) {
   for (int el = threadIdx.x; el < e.n_tets; el += blockDim.x) {
-    const int4 t = E.tet[el];
-    const float* Dmi = E.dminv + 9 * el;
+    const int4 t = e.fem_tet[el];
+    const float* Dmi = e.fem_dminv + 9 * el;
     float Dm[9], Ds[9], F[9], P[9], H[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Dm[q] = Dmi[q];
     edge_mat(X, ns, t, Ds);
     mul3(Ds, Dm, F);
-    const float J = stress(m, F, E.act_of(el), P);
+    const float J = stress(m, F, elem_act(e, act, el), P);
     if (!(J > 0.0f)) status |= 4;
     if (m.kd != 0.0f) {
       float Vs[9], Fd[9];
@@ -171,42 +172,74 @@ __device__ void element_forces(const EnvDesc& e, const FemLaw& m, const Elems& E
 #pragma unroll
       for (int q = 0; q < 9; ++q) P[q] += m.kd * Fd[q];
     }
-    mul3bt(P, Dm, H);
-    const float nv0 = -E.vol[el];
-    const int vi[3] = {t.y, t.z, t.w};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      float s = 0.f;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float f = nv0 * H[3 * k + c];
-        atomicAdd(&Fo[k * ns + vi[c]], f);
-        s += f;
-      }
-      atomicAdd(&Fo[k * ns + t.x], -s);
-    }
+    mul3bt(P, Dm, H);  // f_{c+1} = -V0 H[:, c]
+    put_corners(EF, el, H, -e.fem_vol[el]);
   }
 }
 
-// Ground projection of the new velocity w of a vertex at height z.
+// The new velocity w of a vertex at height z, projected by the ground.
 __device__ __forceinline__ bool on_ground(const EnvDesc& e, float z, const float* w) {
   return z <= e.ground_z && w[2] < 0.0f;
 }
 
-__device__ void fem_substep(const EnvDesc& e, const FemLaw& m, const Elems& E, float* X, float* V, float* Fo, int ns,
+// Shared-memory layout of one environment's step (floats; ints share the 4-byte slots).
+struct FemSmem {
+  float *X, *V, *Fv, *XB, *VB, *EA, *EB, *ABE;
+  int *voff, *vinc, *goff, *ginc;
+};
+
+__device__ FemSmem carve(float* sm, int ns, int nts, int gs, bool reverse) {
+  FemSmem s;
+  s.X = sm;
+  s.V = s.X + 3 * ns;
+  s.Fv = s.V + 3 * ns;
+  float* p = s.Fv + 3 * ns;
+  if (reverse) {
+    s.XB = p;
+    s.VB = s.XB + 3 * ns;
+    p = s.VB + 3 * ns;
+  } else {
+    s.XB = s.VB = nullptr;
+  }
+  s.EA = p;
+  p += 12 * nts;
+  if (reverse) {
+    s.EB = p;
+    p += 12 * nts;
+    s.ABE = p;
+    p += nts;
+  } else {
+    s.EB = s.ABE = nullptr;
+  }
+  s.voff = reinterpret_cast<int*>(p);
+  s.vinc = s.voff + ns + 1;
+  s.goff = s.vinc + 4 * nts;
+  s.ginc = s.goff + gs + 1;
+  return s;
+}
+
+__device__ void stage_incidence(const EnvDesc& e, const FemSmem& s, bool groups) {
+  for (int i = threadIdx.x; i <= e.n; i += blockDim.x) s.voff[i] = e.fem_vinc_off[i];
+  for (int j = threadIdx.x; j < 4 * e.n_tets; j += blockDim.x) s.vinc[j] = e.fem_vinc[j];
+  if (groups) {
+    const int ng = e.n_groups > 0 ? e.n_groups : 1;
+    for (int g = threadIdx.x; g <= ng; g += blockDim.x) s.goff[g] = e.fem_ginc_off[g];
+    for (int j = threadIdx.x; j < e.n_tets; j += blockDim.x) s.ginc[j] = e.fem_ginc[j];
+  }
+}
+
+__device__ void fem_substep(const EnvDesc& e, const FemLaw& m, const float* act, const FemSmem& s, int ns,
                             int& status) {
-  const int nv = e.n;
-  for (int q = threadIdx.x; q < 3 * ns; q += blockDim.x) Fo[q] = 0.f;
-  __syncthreads();
-  element_forces(e, m, E, X, V, Fo, ns, status);
+  element_forces(e, m, act, s.X, s.V, ns, s.EA, status);
   __syncthreads();
   const float dt = e.dt;
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+  for (int i = threadIdx.x; i < e.n; i += blockDim.x) {
     const float im = e.fem_inv_mass[i];
-    float w[3];
+    float f[3], w[3];
+    gather_corners(s.EA, s.voff, s.vinc, i, f);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) w[k] = V[k * ns + i] + dt * (im * Fo[k * ns + i] + e.gravity[k]);
-    if (on_ground(e, X[2 * ns + i], w)) {
+    for (int k = 0; k < 3; ++k) w[k] = s.V[k * ns + i] + dt * (im * f[k] + e.gravity[k]);
+    if (on_ground(e, s.X[2 * ns + i], w)) {
       const float L = sqrtf(w[0] * w[0] + w[1] * w[1]);
       const float g = L > 0.0f ? fmaxf(0.0f, 1.0f + e.ground_mu * w[2] / L) : 0.0f;
       w[0] *= g;
@@ -215,15 +248,13 @@ __device__ void fem_substep(const EnvDesc& e, const FemLaw& m, const Elems& E, f
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      V[k * ns + i] = w[k];
-      X[k * ns + i] += dt * w[k];
-      if (!isfinite(X[k * ns + i])) status |= 2;
+      s.V[k * ns + i] = w[k];
+      s.X[k * ns + i] += dt * w[k];
+      if (!isfinite(s.X[k * ns + i])) status |= 2;
     }
   }
   __syncthreads();
 }
-
-__device__ __forceinline__ FemLaw law_of(const EnvDesc& e) { return FemLaw{e.mu, e.lam, e.fem_alpha, e.k_damp}; }
 
 __device__ __forceinline__ void load_xv(const float* b, long long np, int nv, int ns, float* X, float* V) {
   for (int i = threadIdx.x; i < nv; i += blockDim.x)
@@ -246,23 +277,23 @@ __device__ __forceinline__ void store_xv(float* b, long long np, int nv, int ns,
 // One CTA per FEM environment: the running control step's S substeps, from slot live to slot
 // next (x, v; C and H written as zero, the meta words copied).
 __global__ void __launch_bounds__(kFemThreads) k_fem_forward(const EnvDesc* __restrict__ envs,
-                                                             const int* __restrict__ list, int ns) {
+                                                             const int* __restrict__ list, int ns, int nts) {
   extern __shared__ float sm[];
   const EnvDesc& e = envs[list[blockIdx.x]];
   const EnvCtr c = *e.ctr;
   const long long np = e.n_pad;
   const int nv = e.n;
-  float *X = sm, *V = sm + 3 * ns, *Fo = sm + 6 * ns;
+  const FemSmem s = carve(sm, ns, nts, 0, false);
   const float* src = e.slots + (long long)c.live * e.block;
   float* dst = e.slots + (long long)c.next * e.block;
   const float* act = e.act + (long long)c.live * e.A;
-  load_xv(src, np, nv, ns, X, V);
-  const Elems E = stage_elems(e, act, reinterpret_cast<char*>(sm + 9 * ns));
+  load_xv(src, np, nv, ns, s.X, s.V);
+  stage_incidence(e, s, false);
   __syncthreads();
   const FemLaw m = law_of(e);
   int status = 0;
-  for (int k = 0; k < e.S; ++k) fem_substep(e, m, E, X, V, Fo, ns, status);
-  store_xv(dst, np, nv, ns, X, V);
+  for (int k = 0; k < e.S; ++k) fem_substep(e, m, act, s, ns, status);
+  store_xv(dst, np, nv, ns, s.X, s.V);
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
 #pragma unroll
     for (int q = 6; q < kComp; ++q) dst[q * np + i] = 0.0f;
@@ -278,51 +309,50 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_forward(const EnvDesc* __re
 // buffer (the reverse step's end flips the parity), the activations' adjoints to the action
 // accumulators.
 __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __restrict__ envs,
-                                                             const int* __restrict__ list, int ns, int a_stride) {
+                                                             const int* __restrict__ list, int ns, int nts, int gs) {
   extern __shared__ float sm[];
   const EnvDesc& e = envs[list[blockIdx.x]];
   const EnvCtr c = *e.ctr;
   const long long np = e.n_pad;
   const int nv = e.n, S = e.S;
-  float *X = sm, *V = sm + 3 * ns, *Fo = sm + 6 * ns, *XB = sm + 9 * ns, *VB = sm + 12 * ns, *AB = sm + 15 * ns;
-  // staged element data after AB (a_stride rounded up to 4 floats keeps it 16-byte aligned)
+  const FemSmem s = carve(sm, ns, nts, gs, true);
   const int slot = c.base + c.rev;
   const float* src = e.slots + (long long)slot * e.block;
   const float* act = e.act + (long long)slot * e.A;
   const FemLaw m = law_of(e);
   int status = 0;
   // recompute substep states 1..S-1 into ring blocks 0..S-2
-  load_xv(src, np, nv, ns, X, V);
-  for (int g = threadIdx.x; g < a_stride; g += blockDim.x) AB[g] = 0.0f;
-  const Elems E = stage_elems(e, act, reinterpret_cast<char*>(AB + a_stride));
+  load_xv(src, np, nv, ns, s.X, s.V);
+  stage_incidence(e, s, true);
+  for (int el = threadIdx.x; el < e.n_tets; el += blockDim.x) s.ABE[el] = 0.0f;
   __syncthreads();
   for (int k = 0; k + 1 < S; ++k) {
-    fem_substep(e, m, E, X, V, Fo, ns, status);
-    store_xv(e.ring + (long long)k * e.block, np, nv, ns, X, V);
+    fem_substep(e, m, act, s, ns, status);
+    store_xv(e.ring + (long long)k * e.block, np, nv, ns, s.X, s.V);
   }
   const float* adj = c.par ? e.adj1 : e.adj0;
   float* adj_out = c.par ? e.adj0 : e.adj1;
-  load_xv(adj, np, nv, ns, XB, VB);
-  __syncthreads();  // ring writes of this CTA are read back below by the same threads' peers
+  load_xv(adj, np, nv, ns, s.XB, s.VB);
   const float dt = e.dt;
   for (int k = S - 1; k >= 0; --k) {
-    load_xv(k == 0 ? src : e.ring + (long long)(k - 1) * e.block, np, nv, ns, X, V);
-    for (int q = threadIdx.x; q < 3 * ns; q += blockDim.x) Fo[q] = 0.f;
+    // every thread reads back the ring vertices it wrote itself
+    load_xv(k == 0 ? src : e.ring + (long long)(k - 1) * e.block, np, nv, ns, s.X, s.V);
     __syncthreads();
-    element_forces(e, m, E, X, V, Fo, ns, status);
+    element_forces(e, m, act, s.X, s.V, ns, s.EA, status);
     __syncthreads();
     // vertices: x' = x + dt w passes x-bar through and adds dt x-bar to w-bar; the ground
     // projection; w = v + dt (f / m + g) gives v-bar = w-bar and f-bar = dt w-bar / m
     for (int i = threadIdx.x; i < nv; i += blockDim.x) {
       const float im = e.fem_inv_mass[i];
-      float w[3], ob[3], wb[3];
+      float f[3], w[3], ob[3], wb[3];
+      gather_corners(s.EA, s.voff, s.vinc, i, f);
 #pragma unroll
       for (int k2 = 0; k2 < 3; ++k2) {
-        w[k2] = V[k2 * ns + i] + dt * (im * Fo[k2 * ns + i] + e.gravity[k2]);
-        ob[k2] = VB[k2 * ns + i] + dt * XB[k2 * ns + i];
+        w[k2] = s.V[k2 * ns + i] + dt * (im * f[k2] + e.gravity[k2]);
+        ob[k2] = s.VB[k2 * ns + i] + dt * s.XB[k2 * ns + i];
         wb[k2] = ob[k2];
       }
-      if (on_ground(e, X[2 * ns + i], w)) {
+      if (on_ground(e, s.X[2 * ns + i], w)) {
         const float L = sqrtf(w[0] * w[0] + w[1] * w[1]);
         const float g = L > 0.0f ? fmaxf(0.0f, 1.0f + e.ground_mu * w[2] / L) : 0.0f;
         if (L > 0.0f && g > 0.0f) {
@@ -337,74 +367,80 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
       }
 #pragma unroll
       for (int k2 = 0; k2 < 3; ++k2) {
-        VB[k2 * ns + i] = wb[k2];
-        Fo[k2 * ns + i] = dt * im * wb[k2];  // f-bar
+        s.VB[k2 * ns + i] = wb[k2];
+        s.Fv[k2 * ns + i] = dt * im * wb[k2];  // f-bar
       }
     }
     __syncthreads();
     // elements: H-bar columns f-bar_{c+1} - f-bar_0; P-bar = -V0 H-bar Dm^-1; F-bar by the
     // energy's Hessian; Fdot-bar = k_damp P-bar; Ds-bar = F-bar Dm^-T, Vs-bar = Fdot-bar Dm^-T
     for (int el = threadIdx.x; el < e.n_tets; el += blockDim.x) {
-      const int4 t = E.tet[el];
-      const float* Dmi = E.dminv + 9 * el;
+      const int4 t = e.fem_tet[el];
+      const float* Dmi = e.fem_dminv + 9 * el;
       const int vi[3] = {t.y, t.z, t.w};
       float Dm[9], Hb[9], Pb[9], Ds[9], F[9], Fb[9], Db[9], ab;
 #pragma unroll
       for (int q = 0; q < 9; ++q) Dm[q] = Dmi[q];
 #pragma unroll
       for (int k2 = 0; k2 < 3; ++k2) {
-        const float f0 = Fo[k2 * ns + t.x];
+        const float f0 = s.Fv[k2 * ns + t.x];
 #pragma unroll
-        for (int cc = 0; cc < 3; ++cc) Hb[3 * k2 + cc] = Fo[k2 * ns + vi[cc]] - f0;
+        for (int cc = 0; cc < 3; ++cc) Hb[3 * k2 + cc] = s.Fv[k2 * ns + vi[cc]] - f0;
       }
       mul3(Hb, Dm, Pb);
-      const float nv0 = -E.vol[el];
+      const float nv0 = -e.fem_vol[el];
 #pragma unroll
       for (int q = 0; q < 9; ++q) Pb[q] *= nv0;
-      edge_mat(X, ns, t, Ds);
+      edge_mat(s.X, ns, t, Ds);
       mul3(Ds, Dm, F);
-      stress_adj(m, F, E.act_of(el), Pb, Fb, &ab);
-      atomicAdd(&AB[e.fem_group[el]], ab);
+      stress_adj(m, F, elem_act(e, act, el), Pb, Fb, &ab);
+      s.ABE[el] += ab;
       mul3bt(Fb, Dm, Db);
-#pragma unroll
-      for (int k2 = 0; k2 < 3; ++k2) {
-        float s = 0.f;
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          atomicAdd(&XB[k2 * ns + vi[cc]], Db[3 * k2 + cc]);
-          s += Db[3 * k2 + cc];
-        }
-        atomicAdd(&XB[k2 * ns + t.x], -s);
-      }
+      put_corners(s.EA, el, Db, 1.0f);
       if (m.kd != 0.0f) {
-#pragma unroll
-        for (int q = 0; q < 9; ++q) Pb[q] *= m.kd;
         mul3bt(Pb, Dm, Db);
+        put_corners(s.EB, el, Db, m.kd);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+      float xa[3], va[3];
+      gather_corners(s.EA, s.voff, s.vinc, i, xa);
 #pragma unroll
-        for (int k2 = 0; k2 < 3; ++k2) {
-          float s = 0.f;
+      for (int k2 = 0; k2 < 3; ++k2) s.XB[k2 * ns + i] += xa[k2];
+      if (m.kd != 0.0f) {
+        gather_corners(s.EB, s.voff, s.vinc, i, va);
 #pragma unroll
-          for (int cc = 0; cc < 3; ++cc) {
-            atomicAdd(&VB[k2 * ns + vi[cc]], Db[3 * k2 + cc]);
-            s += Db[3 * k2 + cc];
-          }
-          atomicAdd(&VB[k2 * ns + t.x], -s);
-        }
+        for (int k2 = 0; k2 < 3; ++k2) s.VB[k2 * ns + i] += va[k2];
       }
     }
     __syncthreads();
   }
-  store_xv(adj_out, np, nv, ns, XB, VB);
+  store_xv(adj_out, np, nv, ns, s.XB, s.VB);
   for (int i = threadIdx.x; i < nv; i += blockDim.x)
 #pragma unroll
     for (int q = 6; q < kComp; ++q) adj_out[q * np + i] = 0.0f;
-  for (int g = threadIdx.x; g < e.n_groups; g += blockDim.x)
-    if (AB[g] != 0.0f) atomicAdd(e.acc + ACC_ACT + e.n_coll_act + g, e.act_stress * AB[g]);
+  // activations: per group, its elements in a fixed order (this CTA is the only writer of its
+  // environment's action accumulators during the launch)
+  for (int g = threadIdx.x; g < e.n_groups; g += blockDim.x) {
+    float a = 0.0f;
+    for (int j = s.goff[g]; j < s.goff[g + 1]; ++j) a += s.ABE[s.ginc[j]];
+    e.acc[ACC_ACT + e.n_coll_act + g] += e.act_stress * a;
+  }
   (void)status;
 }
 
-size_t fem_smem(int ns, int a_stride, int nt_max, bool reverse) {
-  return sizeof(float) * (reverse ? (size_t)15 * ns + (size_t)a_stride : (size_t)9 * ns) + stage_bytes(nt_max);
+size_t fem_smem(int ns, int nts, int gs, bool reverse) {
+  const size_t floats = (reverse ? 15 : 9) * (size_t)ns + (reverse ? 25 : 12) * (size_t)nts;
+  const size_t ints = (size_t)ns + 1 + 4 * (size_t)nts + (reverse ? (size_t)gs + 1 + nts : 0);
+  return 4 * (floats + ints);
+}
+
+void set_smem_attr(const void* fn, size_t sm, size_t& attr) {
+  if (sm > attr) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = sm;
+  }
 }
 
 }  // namespace
@@ -412,28 +448,22 @@ size_t fem_smem(int ns, int a_stride, int nt_max, bool reverse) {
 void launch_fem_forward(const Launch& L, const int* list, int n, int nv_max, int nt_max) {
   if (n <= 0) return;
   const int ns = (nv_max + 31) / 32 * 32;
-  const size_t sm = fem_smem(ns, 0, nt_max, false);
+  const size_t sm = fem_smem(ns, nt_max, 0, false);
   static size_t attr = 48 * 1024;
-  if (sm > attr) {
-    cudaFuncSetAttribute(k_fem_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = sm;
-  }
+  set_smem_attr((const void*)k_fem_forward, sm, attr);
   LaunchScope ls(KC_OTHER, L.stream);
-  k_fem_forward<<<n, kFemThreads, sm, L.stream>>>(L.envs, list, ns);
+  k_fem_forward<<<n, kFemThreads, sm, L.stream>>>(L.envs, list, ns, nt_max);
 }
 
 void launch_fem_reverse(const Launch& L, const int* list, int n, int nv_max, int act_max, int nt_max) {
   if (n <= 0) return;
   const int ns = (nv_max + 31) / 32 * 32;
-  const int a_stride = (std::max(act_max, 1) + 3) / 4 * 4;
-  const size_t sm = fem_smem(ns, a_stride, nt_max, true);
+  const int gs = std::max(act_max, 1);
+  const size_t sm = fem_smem(ns, nt_max, gs, true);
   static size_t attr = 48 * 1024;
-  if (sm > attr) {
-    cudaFuncSetAttribute(k_fem_reverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = sm;
-  }
+  set_smem_attr((const void*)k_fem_reverse, sm, attr);
   LaunchScope ls(KC_OTHER, L.stream);
-  k_fem_reverse<<<n, kFemThreads, sm, L.stream>>>(L.envs, list, ns, a_stride);
+  k_fem_reverse<<<n, kFemThreads, sm, L.stream>>>(L.envs, list, ns, nt_max, gs);
 }
 
 }  // namespace mpm

@@ -73,6 +73,13 @@ struct EnvDesc {
   const float* fem_vol;
   const int* fem_group;
   const float* fem_inv_mass;
+  // incidence lists (CSR): vertex i's element corners (4 el + c) at vinc[vinc_off[i] ..
+  // vinc_off[i+1]), action group g's elements at ginc[ginc_off[g] .. ginc_off[g+1]), in
+  // increasing order, so the sums over them are deterministic
+  const int* fem_vinc_off;
+  const int* fem_vinc;
+  const int* fem_ginc_off;
+  const int* fem_ginc;
   int n_tets;
   float k_damp, ground_z, fem_alpha;
   // buffers

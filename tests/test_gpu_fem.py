@@ -6,7 +6,7 @@ the CUDA path against the FP64 FEM oracle:
 - gradients of rewards plus a loss on the final positions with respect to all actions and
   the initial state (1e-3), with and without ground contact;
 - FEM and MPM environments mixed in one batch, forward and reverse, each against its own
-  oracle.
+  oracle, and bitwise equal to the per-environment launch path for the FEM environment.
 """
 import numpy as np
 import pytest
@@ -141,6 +141,18 @@ def test_fem_and_mpm_in_one_batch():
         rew = torch.stack(rew).cpu().numpy()
     finally:
         b.close()
+    # the FEM kernels sum in a fixed order: the per-env launch path gives identical bits
+    bp = Batch(w.specs, max_steps=T, per_env_launch=True, use_graphs=False)
+    try:
+        bp.set_inits(w.inits)
+        for t in range(T):
+            bp.step(torch.as_tensor(acts[t]).cuda(), record=True)
+        stp = {k: v.cpu().numpy() for k, v in bp.get_state().items()}
+        gp = {k: v.cpu().numpy() for k, v in bp.backward(reward_adj=rbar).items()}
+    finally:
+        bp.close()
+    assert np.array_equal(split(w, stp["x"])[0], split(w, st["x"])[0])
+    assert np.array_equal(gp["action_grad"][:, 0], g["action_grad"][:, 0])
     # FEM env
     s0 = specs[0]
     m = fem.make_mesh(s0)
