@@ -396,7 +396,7 @@ def main():
     tuned = None
     for i in range(args.warmup):
         if i == args.warmup - 1:
-            mpm.mpm_time_kernel(b.ctx, "all")  # survey: which kernel class dominates
+            mpm.mpm_time_kernel(b.ctx, "all")  # per-class timing: which kernel class dominates
         one_step()
         if i == 0:
             # autotune the scatter kernels' shared-box capacity on a binned state
