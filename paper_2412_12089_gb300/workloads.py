@@ -7,8 +7,9 @@ both see the same FP32-representable values.
 
 The shapes follow the paper's deformable tasks (arXiv 2412.12089, App. E): RollingFlat
 (elastoplastic dough under a rolling pin, 48^3 grid), FluidMove (fluid in a moving
-container), SoftJumper (recast as an MPM solid with active fibres), and a neo-Hookean
-cube for the single-environment case.  The task assets (PlasticineLab dough meshes,
+container), SoftJumper (as an MPM solid with active fibres, and as the paper's tetrahedral
+FEM quadruped), HandFlip (a slab on driven capsule fingers), and a neo-Hookean cube for the
+single-environment case.  The task assets (PlasticineLab dough meshes,
 SoftGym containers, the Shadow hand) are not available, so each is replaced by a
 parametric stand-in with the paper's sizes, materials and time steps.
 """
