@@ -322,7 +322,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "fluid-1024env-8192p-64grid-16x25", "sample": sample},
+            "config": {"workload": f"fluid-{args.envs}env-{args.particles}p-64grid-{args.control_steps}x"
+                                   f"{args.substeps}-fwd+adjoint", "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
