@@ -263,12 +263,13 @@ __device__ __forceinline__ unsigned cell_pack(int b0, int b1, int b2) {
 //     w_ip (q_p + A_p r_ip)            (r_ip = x_i - x_p)
 // (and w_ip m_p for P2G's mass).  A CTA does it for its chunk of binned particles group by
 // group, a group being the chunk's particles of one cell base (found by a counting sort in
-// shared memory; runs of equal cell base in binned order when the chunk's box is too large).  (1) Every particle writes a record to shared memory: q, its offsets
-// g = f dx from the base node, the weights of the three axes and A.  (2) Work units (group,
-// z offset c) sum the group's contributions to the nine nodes base + (0..2, 0..2, c) in
-// registers and add them into a shared-memory box (no two units of a group touch the same
-// node), or, when the chunk's box is too large, straight into the grid with float4 atomics.
-// Groups are taken largest first, so the lanes of a warp loop over groups of similar size.
+// shared memory; runs of equal cell base in binned order when the chunk's box is too large).
+// (1) Every particle writes a record to shared memory: q, its offsets g = f dx from the base
+// node, the weights of the three axes and A.  (2) Work units (group, z offset c) sum the
+// group's contributions to the nine nodes base + (0..2, 0..2, c) in registers and add them
+// into a shared-memory box (no two units of a group touch the same node), or, when the
+// chunk's box is too large, straight into the grid with float4 atomics.  Groups are taken in
+// cell order (ordering them by size to balance a warp's lanes cost more than it saved).
 // (3) The box is flushed to the grid with float4 atomics.
 
 // Box capacities the scatter kernels are built for (nodes); the autotuner picks one per
@@ -279,26 +280,27 @@ constexpr int kRec = 24;  // floats per particle record
 
 template <int kScBox>
 struct ScatterShared {
-  float4 rec[kBlock * kPPT * kRec / 4];      // particle records in chunk order (24 KB)
+  float4 rec[kRec / 4 * kBlock * kPPT];      // particle records (24 KB): quad j of particle l at
+                                             // rec[j * kRecStride + l], so the lanes of a warp
+                                             // reading different particles hit different banks
   float box[4 * kScBox];                     // box nodes, component-major (8 or 16 KB)
   unsigned key[kBlock * kPPT];               // packed cell base per particle (~0u: none)
   unsigned short gstart[kBlock * kPPT + 1];  // first particle of each group, then the end
-  unsigned short order[kBlock * kPPT];       // groups by decreasing size (balanced warps)
   unsigned short sidx[kBlock * kPPT];        // grouped position -> particle record
   int seg[kPPT * kBlock / 32];               // group heads per (particle slot, warp)
-  int bucket[32];                            // groups per size class, then class offsets
 };
 
-// Record layout: (q0 q1 q2 gx) (gy gz wx0 wx1) (wx2 wy0 wy1 wy2) (wz0 wz1 wz2 A00)
-// (A01 A02 A10 A11) (A12 A20 A21 A22).
+// Record quads: (q0 q1 q2 gx) (gy gz wx0 wx1) (wx2 wy0 wy1 wy2) (wz0 wz1 wz2 A00)
+// (A01 A02 A10 A11) (A12 A20 A21 A22), quad j at r[j * kRecStride] (r = rec + particle).
+constexpr int kRecStride = kBlock * kPPT;
 __device__ __forceinline__ void write_record(float4* r, const float* q, const float* g, const float* wx,
                                              const float* wy, const float* wz, const float* A) {
   r[0] = make_float4(q[0], q[1], q[2], g[0]);
-  r[1] = make_float4(g[1], g[2], wx[0], wx[1]);
-  r[2] = make_float4(wx[2], wy[0], wy[1], wy[2]);
-  r[3] = make_float4(wz[0], wz[1], wz[2], A[0]);
-  r[4] = make_float4(A[1], A[2], A[3], A[4]);
-  r[5] = make_float4(A[5], A[6], A[7], A[8]);
+  r[kRecStride] = make_float4(g[1], g[2], wx[0], wx[1]);
+  r[2 * kRecStride] = make_float4(wx[2], wy[0], wy[1], wy[2]);
+  r[3 * kRecStride] = make_float4(wz[0], wz[1], wz[2], A[0]);
+  r[4 * kRecStride] = make_float4(A[1], A[2], A[3], A[4]);
+  r[5 * kRecStride] = make_float4(A[5], A[6], A[7], A[8]);
 }
 
 // Steps (2) and (3), after make_box (whose barriers publish the records and keys).
@@ -405,36 +407,17 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
     for (int q = 0; q < kPPT * (kBlock / 32); ++q) ngrp += sh.seg[q];
   }
   if (threadIdx.x == 0) sh.gstart[ngrp] = (unsigned short)count;
-  if (threadIdx.x < 32) sh.bucket[threadIdx.x] = 0;
-  __syncthreads();
-  // order the groups by decreasing size (classes 1..31, 32+), so the lanes of a warp loop over
-  // groups of about the same length
-  for (int g = threadIdx.x; g < ngrp; g += kBlock) atomicAdd(&sh.bucket[32 - min(sh.gstart[g + 1] - sh.gstart[g], 32)], 1);
+  __syncthreads();  // the grouped positions are written (they read the counts) before the clear
   if (kMass && fits) {  // the cell counts are no longer read: clear the mass component
     const int vol = bx.nx * bx.ny * bx.nz;
     for (int q = threadIdx.x; q < vol; q += kBlock) sh.box[3 * kScBox + q] = 0.f;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int c = sh.bucket[threadIdx.x];
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    sh.bucket[threadIdx.x] = incl - c;
-  }
-  __syncthreads();
-  for (int g = threadIdx.x; g < ngrp; g += kBlock)
-    sh.order[atomicAdd(&sh.bucket[32 - min(sh.gstart[g + 1] - sh.gstart[g], 32)], 1)] = (unsigned short)g;
-  __syncthreads();
   const float dx = e.dx;
   // units: (group, z offset c), each summing the nine nodes base + (0..2, 0..2, c)
   const int nunits = ngrp * 3;
   for (int u = threadIdx.x; u < nunits; u += kBlock) {
-    const int gi = u / 3, oc = u - 3 * gi;
-    const int g = sh.order[gi];
+    const int g = u / 3, oc = u - 3 * g;
     const int q0 = sh.gstart[g], q1 = sh.gstart[g + 1];
     const unsigned key = sh.key[sh.sidx[q0]];
     const int cx = (int)(key & 1023u), cy = (int)((key >> 10) & 1023u), cz = (int)(key >> 20);
@@ -448,8 +431,9 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
         ap[ob][a][0] = ap[ob][a][1] = ap[ob][a][2] = 0.f;
       }
     for (int q = q0; q < q1; ++q) {
-      const float4* r = sh.rec + sh.sidx[q] * (kRec / 4);
-      const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
+      const float4* r = sh.rec + sh.sidx[q];
+      const float4 r0 = r[0], r1 = r[kRecStride], r2 = r[2 * kRecStride], r3 = r[3 * kRecStride],
+                   r4 = r[4 * kRecStride], r5 = r[5 * kRecStride];
       const float wzc = oc == 0 ? r3.x : (oc == 1 ? r3.y : r3.z);
       const float rz = cdx - r1.y;
       const float tz0 = r0.x + r4.y * rz, tz1 = r0.y + r5.x * rz, tz2 = r0.z + r5.w * rz;
@@ -566,7 +550,7 @@ __global__ void __launch_bounds__(kBlock, BOX == kScBoxSmall ? 6 : 5) k_p2g(cons
     bspline(f2, wz, dw);
     const float mv[3] = {pm * s[3], pm * s[4], pm * s[5]};
     const float g[3] = {f0 * dx, f1 * dx, f2 * dx};
-    write_record(sh.rec + l * (kRec / 4), mv, g, wx, wy, wz, A);
+    write_record(sh.rec + l, mv, g, wx, wy, wz, A);
   }
   if (oob) atomicOr(&e.ctr->status, 1);
   const Box bx = make_box(base, valid, sred);
@@ -1181,7 +1165,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_g2p_adj(const EnvDesc* __restrict
     {
       const float q[3] = {vnb[0] - vref[0], vnb[1] - vref[1], vnb[2] - vref[2]};
       const float g[3] = {fx[0] * dx, fx[1] * dx, fx[2] * dx};
-      write_record(sh.rec + l * (kRec / 4), q, g, w[0], w[1], w[2], Ab);
+      write_record(sh.rec + l, q, g, w[0], w[1], w[2], Ab);
     }
     // gather: x-bar += sum_i (g_i . (v-bar' + A' r_i)) grad w_i - A'^T sum_i w_i g_i with
     // g_i = v_i - v_c (the stencil-uniform part of v_i adds nothing: sum grad w = 0 and
