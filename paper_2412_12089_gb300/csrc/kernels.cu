@@ -26,7 +26,6 @@ namespace mpm {
 
 constexpr int kBlock = 128;         // threads per particle CTA
 constexpr int kPPT = 2;             // particles per thread
-constexpr int kBoxNodes = 2048;     // shared-memory box capacity (float4 nodes, 32 KB)
 
 // ------------------------------------------------------------------ common device helpers
 
@@ -147,8 +146,6 @@ __device__ __forceinline__ void load_state(const float* b, long long np, int j, 
 // Shared-memory box over a CTA's particle stencils: node (ix,iy,iz) -> box index.
 struct Box {
   int lx, ly, lz, nx, ny, nz;
-  bool fits;
-  __device__ __forceinline__ int idx(int ix, int iy, int iz) const { return ((iz - lz) * ny + (iy - ly)) * nx + (ix - lx); }
 };
 
 // Block-wide min/max of the particles' base cells -> box of their stencils (base..base+2).
@@ -182,7 +179,6 @@ __device__ __forceinline__ Box make_box(const int (*base)[3], const bool* valid,
   bx.nx = sred[3] - sred[0] + 3;
   bx.ny = sred[4] - sred[1] + 3;
   bx.nz = sred[5] - sred[2] + 3;
-  bx.fits = sred[3] >= 0 && (long long)bx.nx * bx.ny * bx.nz <= kBoxNodes;
   return bx;
 }
 
@@ -197,17 +193,6 @@ __device__ __forceinline__ void mark_tile(const EnvDesc& e, int env, int ix, int
       active[s] = make_uint2((unsigned)env, (unsigned)t);
     }
   }
-}
-
-// Shared-memory box, structure of arrays: component c of box node i at s[c * kBoxNodes + i]
-// (consecutive nodes fall in consecutive banks).
-struct SBox {
-  float v[4 * kBoxNodes];
-};
-
-__device__ __forceinline__ void zero_box(SBox& sb, int vol, int ncomp) {
-  for (int i = threadIdx.x; i < vol; i += blockDim.x)
-    for (int c = 0; c < ncomp; ++c) sb.v[c * kBoxNodes + i] = 0.f;
 }
 
 // Flush a shared box of kNc components into a dense grid with float4 atomics (nodes whose
@@ -227,29 +212,6 @@ __device__ __forceinline__ void flush_box(const EnvDesc& e, int env, const Box& 
     int iz = bx.lz + r / bx.ny;
     atomicAdd(grid + ((long long)iz * G + iy) * G + ix, val);
     if (kMark) mark_tile(e, env, ix, iy, iz, active, active_n);
-  }
-}
-
-__device__ __forceinline__ float pick3(int i, const float* w) { return i == 0 ? w[0] : (i == 1 ? w[1] : w[2]); }
-
-// One axis of a particle's 3-node stencil, visited in an order rotated by r (node offsets
-// o[h] = (h + r) mod 3) with the matching weights, weight derivatives and node offsets
-// r[h] = (o[h] - fx) dx.  Lanes with different rotations update different nodes at the
-// same loop step, yet the 27-node loop stays static.
-struct Axis3 {
-  int o[3];
-  float w[3], dw[3], r[3];
-};
-
-__device__ __forceinline__ void rot_axis(int rot, const float* w, const float* dw, float fx, float dx, Axis3& a) {
-#pragma unroll
-  for (int h = 0; h < 3; ++h) {
-    int o = h + rot;
-    o = o >= 3 ? o - 3 : o;
-    a.o[h] = o;
-    a.w[h] = pick3(o, w);
-    a.dw[h] = pick3(o, dw);
-    a.r[h] = ((float)o - fx) * dx;
   }
 }
 
