@@ -486,6 +486,16 @@ def main():
                 "algorithmic_bytes_per_launch": algo, "avg_launch_ms": avg_s * 1e3, "launches": dom_n,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "class_share": {k: round(v / max(sum(tot.values()), 1e-9), 4) for k, v in tot.items() if v > 0}}
+    # every kernel class against the same peak, from the last warm-up rollout (all classes
+    # timed there with CUDA events on the launching stream)
+    per_class = {}
+    for k, (pp, pn) in ALGO_BYTES.items():
+        if cnt.get(k):
+            a = pp * P + pn * n_nodes
+            t_avg = tot[k] / cnt[k] / 1e3
+            per_class[k] = {"achieved": a / t_avg / 1e9, "frac": a / t_avg / 1e9 / peak, "avg_launch_ms": t_avg * 1e3,
+                            "launches": int(cnt[k]), "algorithmic_bytes_per_launch": a}
+    roofline["per_class_warmup"] = per_class
 
     # ---- per-environment-launch path on a sample of the same workload (one control step)
     per_env = None
