@@ -122,39 +122,41 @@ __device__ __forceinline__ float elem_act(const EnvDesc& e, const float* act, in
 
 // Corner terms of an element for the four vertices from the 3x3 edge-column terms M
 // (row k = component, column c = edge c): vertex c+1 gets M[:, c], vertex 0 gets -sum_c M[:, c].
-// Written to T[12 el + 3 corner + k].
-__device__ __forceinline__ void put_corners(float* T, int el, const float* M, float scale) {
-  float* t = T + 12 * el;
+// Written component-major, T[(3 corner + k) nts + el], so the lanes of a warp (consecutive
+// elements) store to consecutive banks.
+__device__ __forceinline__ void put_corners(float* T, int nts, int el, const float* M, float scale) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     float s = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float v = scale * M[3 * k + c];
-      t[3 * (c + 1) + k] = v;
+      T[(3 * (c + 1) + k) * nts + el] = v;
       s += v;
     }
-    t[k] = -s;
+    T[k * nts + el] = -s;
   }
 }
 
-// Sum of vertex i's corner terms (incidence list in shared memory).
-__device__ __forceinline__ void gather_corners(const float* T, const int* voff, const int* vinc, int i, float* out) {
+// Sum of vertex i's corner terms (incidence entries 4 el + corner, in shared memory).
+__device__ __forceinline__ void gather_corners(const float* T, int nts, const int* voff, const int* vinc, int i,
+                                               float* out) {
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   for (int j = voff[i]; j < voff[i + 1]; ++j) {
-    const float* t = T + 3 * vinc[j];
+    const int el = vinc[j] >> 2, c = vinc[j] & 3;
+    const float* t = T + 3 * c * nts + el;
     a0 += t[0];
-    a1 += t[1];
-    a2 += t[2];
+    a1 += t[nts];
+    a2 += t[2 * nts];
   }
   out[0] = a0;
   out[1] = a1;
   out[2] = a2;
 }
 
-// Corner forces of every element at (X, V) into EF; J <= 0 sets status 4.
+// Corner forces of every element at (X, V) into EF (element stride nts); J <= 0 sets status 4.
 __device__ void element_forces(const EnvDesc& e, const FemLaw& m, const float* act, const float* X, const float* V,
-                               int ns, float* EF, int& status) {
+                               int ns, int nts, float* EF, int& status) {
   for (int el = threadIdx.x; el < e.n_tets; el += blockDim.x) {
     const int4 t = e.fem_tet[el];
     const float* Dmi = e.fem_dminv + 9 * el;
@@ -173,7 +175,7 @@ __device__ void element_forces(const EnvDesc& e, const FemLaw& m, const float* a
       for (int q = 0; q < 9; ++q) P[q] += m.kd * Fd[q];
     }
     mul3bt(P, Dm, H);  // f_{c+1} = -V0 H[:, c]
-    put_corners(EF, el, H, -e.fem_vol[el]);
+    put_corners(EF, nts, el, H, -e.fem_vol[el]);
   }
 }
 
@@ -228,15 +230,15 @@ __device__ void stage_incidence(const EnvDesc& e, const FemSmem& s, bool groups)
   }
 }
 
-__device__ void fem_substep(const EnvDesc& e, const FemLaw& m, const float* act, const FemSmem& s, int ns,
+__device__ void fem_substep(const EnvDesc& e, const FemLaw& m, const float* act, const FemSmem& s, int ns, int nts,
                             int& status) {
-  element_forces(e, m, act, s.X, s.V, ns, s.EA, status);
+  element_forces(e, m, act, s.X, s.V, ns, nts, s.EA, status);
   __syncthreads();
   const float dt = e.dt;
   for (int i = threadIdx.x; i < e.n; i += blockDim.x) {
     const float im = e.fem_inv_mass[i];
     float f[3], w[3];
-    gather_corners(s.EA, s.voff, s.vinc, i, f);
+    gather_corners(s.EA, nts, s.voff, s.vinc, i, f);
 #pragma unroll
     for (int k = 0; k < 3; ++k) w[k] = s.V[k * ns + i] + dt * (im * f[k] + e.gravity[k]);
     if (on_ground(e, s.X[2 * ns + i], w)) {
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_forward(const EnvDesc* __re
   __syncthreads();
   const FemLaw m = law_of(e);
   int status = 0;
-  for (int k = 0; k < e.S; ++k) fem_substep(e, m, act, s, ns, status);
+  for (int k = 0; k < e.S; ++k) fem_substep(e, m, act, s, ns, nts, status);
   store_xv(dst, np, nv, ns, s.X, s.V);
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
 #pragma unroll
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
   for (int el = threadIdx.x; el < e.n_tets; el += blockDim.x) s.ABE[el] = 0.0f;
   __syncthreads();
   for (int k = 0; k + 1 < S; ++k) {
-    fem_substep(e, m, act, s, ns, status);
+    fem_substep(e, m, act, s, ns, nts, status);
     store_xv(e.ring + (long long)k * e.block, np, nv, ns, s.X, s.V);
   }
   const float* adj = c.par ? e.adj1 : e.adj0;
@@ -338,14 +340,14 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
     // every thread reads back the ring vertices it wrote itself
     load_xv(k == 0 ? src : e.ring + (long long)(k - 1) * e.block, np, nv, ns, s.X, s.V);
     __syncthreads();
-    element_forces(e, m, act, s.X, s.V, ns, s.EA, status);
+    element_forces(e, m, act, s.X, s.V, ns, nts, s.EA, status);
     __syncthreads();
     // vertices: x' = x + dt w passes x-bar through and adds dt x-bar to w-bar; the ground
     // projection; w = v + dt (f / m + g) gives v-bar = w-bar and f-bar = dt w-bar / m
     for (int i = threadIdx.x; i < nv; i += blockDim.x) {
       const float im = e.fem_inv_mass[i];
       float f[3], w[3], ob[3], wb[3];
-      gather_corners(s.EA, s.voff, s.vinc, i, f);
+      gather_corners(s.EA, nts, s.voff, s.vinc, i, f);
 #pragma unroll
       for (int k2 = 0; k2 < 3; ++k2) {
         w[k2] = s.V[k2 * ns + i] + dt * (im * f[k2] + e.gravity[k2]);
@@ -396,20 +398,20 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
       stress_adj(m, F, elem_act(e, act, el), Pb, Fb, &ab);
       s.ABE[el] += ab;
       mul3bt(Fb, Dm, Db);
-      put_corners(s.EA, el, Db, 1.0f);
+      put_corners(s.EA, nts, el, Db, 1.0f);
       if (m.kd != 0.0f) {
         mul3bt(Pb, Dm, Db);
-        put_corners(s.EB, el, Db, m.kd);
+        put_corners(s.EB, nts, el, Db, m.kd);
       }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nv; i += blockDim.x) {
       float xa[3], va[3];
-      gather_corners(s.EA, s.voff, s.vinc, i, xa);
+      gather_corners(s.EA, nts, s.voff, s.vinc, i, xa);
 #pragma unroll
       for (int k2 = 0; k2 < 3; ++k2) s.XB[k2 * ns + i] += xa[k2];
       if (m.kd != 0.0f) {
-        gather_corners(s.EB, s.voff, s.vinc, i, va);
+        gather_corners(s.EB, nts, s.voff, s.vinc, i, va);
 #pragma unroll
         for (int k2 = 0; k2 < 3; ++k2) s.VB[k2 * ns + i] += va[k2];
       }
