@@ -147,6 +147,22 @@ def test_edge_cases_tiny_envs():
         assert rel_err(split(w2, st["x"])[e], o.x) < 1e-5
 
 
+def test_maximum_env_size_and_grid():
+    """The largest environment the ABI takes: 1,048,575 particles (the 20-bit particle id) on
+    the largest grid, 128^3, one substep from a perturbed state, against the oracle; about
+    60 particles per cell, so the scatter's cell groups are far larger than in the tasks."""
+    w = perturb(wl.cube(seed=11, n=(1 << 20) - 1, G=128, substeps=1, T=1), seed=12)
+    b, _, st = gpu_run(w, 1)
+    try:
+        code, flags = b.check_status()
+    finally:
+        b.close()
+    assert code == 0 and not flags.any()
+    o, _, _ = oracle_run(w, 0, 1)
+    for k in ("x", "v", "F"):
+        assert rel_err(st[k], getattr(o, k)) < 1e-5, (k, rel_err(st[k], getattr(o, k)))
+
+
 def test_domain_status_flag():
     w = small("cube", seed=8, substeps=1, T=1, n=300)
     w.inits[0].x[5] = np.array([0.001, 0.5, 0.5], np.float32)  # below the first cell: base clamped
