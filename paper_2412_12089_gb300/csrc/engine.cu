@@ -21,6 +21,17 @@ int bits_for(unsigned long long v) {
 }
 }  // namespace
 
+namespace {
+// Rest data of element e: Dm (edge matrix, row-major) and its determinant, in double.
+double rest_edges(const mpm_env_spec& s, long long e, double* Dm) {
+  const int* t = s.fem_tets + 4 * e;
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 3; ++c) Dm[3 * k + c] = (double)s.fem_rest[3 * t[c + 1] + k] - (double)s.fem_rest[3 * t[0] + k];
+  return Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
+         Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
+}
+}  // namespace
+
 const char* check_spec(const mpm_env_spec& s) {
   if (s.n_particles < 1 || s.n_particles > (int)kIdMask) return "n_particles";
   if (s.grid_res < 8 || s.grid_res > 128 || s.grid_res % 4) return "grid_res";
@@ -56,21 +67,13 @@ const char* check_spec(const mpm_env_spec& s) {
       for (int c = 0; c < 4; ++c)
         if (s.fem_tets[4 * e + c] < 0 || s.fem_tets[4 * e + c] >= s.n_particles) return "fem_tets (vertex index)";
       if (s.fem_group && (s.fem_group[e] < 0 || s.fem_group[e] >= std::max(s.n_groups, 1))) return "fem_group";
+      double Dm[9];
+      const double det = rest_edges(s, e, Dm);
+      if (det == 0.0 || !std::isfinite(det)) return "fem_rest (degenerate element)";
     }
   }
   return nullptr;
 }
-
-namespace {
-// Rest data of element e: Dm (edge matrix, row-major) and its determinant, in double.
-double rest_edges(const mpm_env_spec& s, long long e, double* Dm) {
-  const int* t = s.fem_tets + 4 * e;
-  for (int k = 0; k < 3; ++k)
-    for (int c = 0; c < 3; ++c) Dm[3 * k + c] = (double)s.fem_rest[3 * t[c + 1] + k] - (double)s.fem_rest[3 * t[0] + k];
-  return Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
-         Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
-}
-}  // namespace
 
 cudaError_t fem_upload(const mpm_env_spec& s, const EnvDesc& d) {
   if (s.material != kMatFem) return cudaSuccess;

@@ -73,7 +73,10 @@ def test_invalid_fem_meshes_rejected_without_gpu_work(lib):
     tets[7, 2] = good.n_particles  # out of range
     grp = good.fem_group.copy()
     grp[3] = good.n_groups
+    flat = good.fem_rest.copy()
+    flat[good.fem_tets[5]] = flat[good.fem_tets[5][0]]  # element 5 collapses to a point
     cases = [(good.replace(fem_tets=tets), "fem_tets"), (good.replace(fem_group=grp), "fem_group"),
+             (good.replace(fem_rest=flat), "degenerate"),
              (good.replace(collider="capsule", act_map=(0,)), "collider"),
              (good.replace(nu=0.0), "nu"),
              (good.replace(n_particles=3000, fem_rest=np.zeros((3000, 3), np.float32)), "n_particles")]
