@@ -229,6 +229,6 @@ def iteration(batch, agent, eps):
         loss = sum(((c(o).squeeze(-1) - y) ** 2).mean() for c in agent.critics)
         loss.backward()
         agent.opt_critic.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     return {"reward": float(buf["rew"].mean()), "entropy": float(h.mean()), "alpha": float(agent.alpha.detach()),
             "critic_loss_first": losses[0], "critic_loss_last": losses[-1]}

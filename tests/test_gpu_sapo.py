@@ -54,19 +54,24 @@ def test_stepwise_equals_whole_tape():
         assert rel_err(got[k], ref[k]) < 1e-4, (k, rel_err(got[k], ref[k]))
 
 
-def test_closed_loop_gradient_matches_finite_differences():
+@pytest.mark.parametrize("task", ["fluid", "softjumper"])
+def test_closed_loop_gradient_matches_finite_differences(task):
     import torch
 
     from paper_2412_12089_gb300 import sapo
     from paper_2412_12089_gb300.batch import Batch
 
     H = 3
-    w = wl.fluid(n_envs=2, seed=62, n=1500, substeps=5, T=H)
+    if task == "fluid":
+        w = wl.fluid(n_envs=2, seed=62, n=1500, substeps=5, T=H)
+    else:  # tetrahedral FEM: observations of the mesh vertices, 220 activations
+        w = wl.softjumper(n_envs=2, seed=62, T=H)
+    A = w.specs[0].action_dim
     b = Batch(w.specs, max_steps=H)
     try:
-        agent = sapo.Agent(b.obs_dim, 3, sapo.SapoConfig(horizon=H, hidden=32), device=b.device, seed=3)
+        agent = sapo.Agent(b.obs_dim, A, sapo.SapoConfig(horizon=H, hidden=32), device=b.device, seed=3)
         gen = torch.Generator(device="cpu").manual_seed(5)
-        eps = torch.randn(H, b.n_envs, 3, generator=gen).to(b.device)
+        eps = torch.randn(H, b.n_envs, A, generator=gen).to(b.device)
         b.set_inits(w.inits)
         sapo.actor_gradient(b, agent, eps)
         params = list(agent.actor.parameters())
