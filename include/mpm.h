@@ -16,7 +16,14 @@
  *    the task definitions of App. E.
  *  - Gradients are the exact discrete adjoint of the FP32 forward pass (Sec. 4.1), with
  *    checkpoints at control-step boundaries and the substeps recomputed in reverse
- *    (Sec. 4.1, gradient checkpointing).
+ *    (Sec. 4.1, gradient checkpointing).  mpm_backward reverses every recorded step;
+ *    mpm_backward_begin/_step/_end reverse them one at a time, for consumers whose actions
+ *    depend on observations (mpm_observe).
+ *  - Environments may also be tetrahedral FEM meshes (App. D.2's stable neo-Hookean
+ *    elements, MPM_MAT_FEM), batched, recorded, reversed and served alongside the MPM ones,
+ *    and the collider may be a union of independently driven capsules (MPM_COLL_CAPSULES).
+ *  - A continuous-batching server (mpm_server_create / mpm_submit / mpm_poll) admits
+ *    rollout requests as memory frees up and runs them together.
  *
  * General conventions
  *  - Every call returns an mpm_status; no C++ exception crosses the ABI.  On failure
