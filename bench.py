@@ -173,12 +173,14 @@ def cpu_baseline_all_cores(T, pool=None):
                                    f"particles, forward + checkpointed reverse, FP64")
 
 
-def serving_leg(n_req, rate, seed):
+def serving_leg(n_req, rates, seed):
     """Continuous batching under a Poisson request stream: rollouts of the three materials
     (dough, fluid, muscle solid), particle counts log-uniform in [1k, 200k], horizons uniform
     in [8, 64] control steps, half of them with gradients, admitted by an 80% memory budget.
     The same stream also runs through a server holding one request at a time (every
-    request's kernels launched on their own), the per-request-launch baseline."""
+    request's kernels launched on their own), the per-request-launch baseline.  The request
+    set is drawn once and replayed at every arrival rate in `rates`; the result for the first
+    rate is returned, the others under "sweep"."""
     import numpy as np
 
     from paper_2412_12089_gb300 import mpm
@@ -203,11 +205,24 @@ def serving_leg(n_req, rate, seed):
         sp = w.specs[0]
         A = sp.action_dim
         reqs.append((sp, w.inits[0], w.actions[:T, 0, :A] if A else None, T, grad, n * T * sp.substeps))
-    gaps = rng.exponential(1.0 / rate, n_req)
+    # unit-mean exponential gaps, drawn once: rate r spaces the arrivals by gap / r
+    unit_gaps = rng.exponential(1.0, n_req)
     work = sum(r[5] for r in reqs)
+    outs = [_serve_stream(mpm, reqs, unit_gaps / r, work) for r in rates]
     out = {"workload": f"{n_req} requests, dough/fluid/muscle, n logU[1k,200k], T U[8,64], 50% grad, "
-                       f"grid 48/64/96 capped at 8 particles per cell, Poisson {rate:g}/s, 80% memory budget",
-           "unit_latency": "ms", "unit_throughput": "particle-substeps/s (forward substeps of all requests)"}
+                       f"grid 48/64/96 capped at 8 particles per cell, Poisson {rates[0]:g}/s, 80% memory budget",
+           "unit_latency": "ms", "unit_throughput": "particle-substeps/s (forward substeps of all requests)",
+           **outs[0]}
+    if len(rates) > 1:
+        out["sweep"] = [{"rate_per_s": r, **o} for r, o in zip(rates, outs)]
+    return out
+
+
+def _serve_stream(mpm, reqs, gaps, work):
+    """One arrival stream through the batching server and through the one-at-a-time server."""
+    import numpy as np
+
+    out = {}
     for mode, resident in (("batched", 64), ("per_request", 1)):
         srv = mpm.mpm_server_create(mem_fraction=0.8, max_resident=resident)
         try:
@@ -381,7 +396,9 @@ def main():
     ap.add_argument("--control-steps", type=int, default=16, help="control steps per rollout (small cases)")
     ap.add_argument("--substeps", type=int, default=25, help="substeps per control step (small cases)")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests in the serving leg (0 = off)")
-    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate of the serving leg (1/s)")
+    ap.add_argument("--serve-rate", type=str, default="200",
+                    help="Poisson arrival rate(s) of the serving leg (1/s), comma-separated; the first is reported "
+                         "as `serving`, all of them under `serving.sweep`")
     ap.add_argument("--handflip-frames", type=int, default=30, help="timed frames of the HandFlip-like leg (0 = off)")
     ap.add_argument("--fem-envs", type=int, default=2048, help="envs of the SoftJumper FEM leg (0 = off)")
     args = ap.parse_args()
@@ -551,7 +568,7 @@ def main():
 
     serve = None
     if args.serve_requests > 0 and rank == 0:
-        serve = serving_leg(args.serve_requests, args.serve_rate, seed=11)
+        serve = serving_leg(args.serve_requests, [float(r) for r in args.serve_rate.split(",")], seed=11)
 
     handflip = None
     if args.handflip_frames > 0 and rank == 0:
