@@ -104,8 +104,10 @@ def test_g2p_affine_reproduction():
 
 
 def test_g2p_momentum_matches_grid():
-    """P2G followed directly by G2P (no forces, no walls) conserves linear momentum:
-    sum m v_p' = sum_i m_i v_i."""
+    """P2G followed directly by G2P (no forces, no walls) conserves linear momentum,
+    sum m v_p' = sum_i m_i v_i, and APIC angular momentum at the pre-advection positions,
+    sum m (x_p x v_p' + (dx^2/4) eps:C_p'^T) = sum_i m_i x_i x v_i, for any grid field
+    (C_p' = D^-1 sum w v_i r^T makes the particles' spin carry the stencil's moment)."""
     G = 16
     sp = spec_for("neohookean", G=G, bound=0, gravity=(0.0, 0.0, 0.0))
     st = _rand_state(50, G, RNG)
@@ -116,6 +118,18 @@ def test_g2p_momentum_matches_grid():
     out, _ = orc.g2p(sp, st, gv)
     assert np.allclose((sp.p_mass * out.v).sum(0), (m[..., None] * gv).sum((0, 1, 2)), rtol=1e-11, atol=1e-15)
     assert np.allclose((m[..., None] * gv).sum((0, 1, 2)), sp.p_mass * st.v.sum(0), rtol=1e-11, atol=1e-15)
+    # a non-affine grid field (random per node) on the same masses
+    gr = RNG.standard_normal(gv.shape)
+    out, _ = orc.g2p(sp, st, gr)
+    iz, iy, ix = np.meshgrid(np.arange(G), np.arange(G), np.arange(G), indexing="ij")
+    xi = np.stack([ix, iy, iz], -1) / G
+    Lg = (m[..., None] * np.cross(xi, gr)).sum((0, 1, 2))
+    eps = np.zeros((3, 3, 3))
+    eps[0, 1, 2] = eps[1, 2, 0] = eps[2, 0, 1] = 1
+    eps[0, 2, 1] = eps[2, 1, 0] = eps[1, 0, 2] = -1
+    Lp = (sp.p_mass * np.cross(st.x, out.v)).sum(0)
+    Lp += sp.p_mass / (4 * G * G) * np.einsum("kab,pba->k", eps, out.C)
+    assert np.allclose(Lp, Lg, rtol=1e-11, atol=1e-15)
 
 
 def test_free_fall_closed_form():
