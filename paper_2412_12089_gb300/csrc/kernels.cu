@@ -40,8 +40,9 @@ constexpr int kStatusWait = 8;
 // A copy needs 16-byte aligned source and destination and a size that is a multiple of 16
 // bytes: chunks start at multiples of four particles, component arrays hold n_pad (a multiple
 // of 32) floats, and a run of `count` particles is rounded up to four, which stays inside the
-// array.  The wait is bounded: after kWaitLimit polls the caller sets kStatusWait and skips
-// the chunk's work.
+// array.  The wait is bounded: after kWaitLimit polls the caller sets kStatusWait, waits once
+// more (again bounded) for copies still in flight into its shared memory, and skips the
+// chunk's work.
 constexpr int kWaitLimit = 1 << 22;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -804,9 +805,13 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
       mbar_arrive_expect_tx(&bar, 12 * bytes);
       copy_runs(stage, b, np, comps, 12, it.start, bytes, &bar);
     }
-    // every thread polls on its own; the CTA leaves together if any of them gave up
+    // every thread polls on its own; the CTA leaves together if any of them gave up, thread 0
+    // last, after a second bounded wait for the copies (its shared memory lives until then)
     if (!__syncthreads_and(mbar_wait(&bar, 0) ? 1 : 0)) {
-      if (threadIdx.x == 0) atomicOr(&e.ctr->status, kStatusWait);
+      if (threadIdx.x == 0) {
+        atomicOr(&e.ctr->status, kStatusWait);
+        (void)mbar_wait(&bar, 0);
+      }
       return;
     }
   }
