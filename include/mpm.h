@@ -241,11 +241,17 @@ mpm_status mpm_backward_end(mpm_ctx* ctx, const float* obs_adj, float* xb0, floa
 /* Forget the recorded steps; the current state stays. */
 mpm_status mpm_reset_tape(mpm_ctx* ctx);
 
+/* Status word masks, per environment. */
+#define MPM_FLAG_DOMAIN 0x1u  /* a particle left the grid (its stencil was clamped) */
+#define MPM_FLAG_NAN 0x2u     /* NaN or Inf in the state */
+#define MPM_FLAG_INVERTED 0x4u /* J = det F <= 0 */
+#define MPM_FLAG_WAIT 0x8u    /* a bounded wait on an asynchronous copy gave up; that chunk's work was skipped */
+
 /*
- * Synchronise and read the per-environment status words (bit 1: a particle left the
- * grid, bit 2: NaN/Inf, bit 4: J <= 0, bit 8: a bounded wait on an asynchronous copy gave up
- * and the chunk's work was skipped), accumulated since the last call, which clears them.
- * flags: [n_envs] host array or NULL.  Returns TIMEOUT / NUMERIC / DOMAIN if a bit is set.
+ * Synchronise and read the per-environment status words (an OR of the MPM_FLAG_* masks),
+ * accumulated since the last call, which clears them.
+ * flags: [n_envs] host array or NULL.  Returns TIMEOUT (MPM_FLAG_WAIT), NUMERIC (MPM_FLAG_NAN
+ * or MPM_FLAG_INVERTED) or DOMAIN (MPM_FLAG_DOMAIN) if a mask is set, in that order.
  */
 mpm_status mpm_check_status(mpm_ctx* ctx, int32_t* flags);
 

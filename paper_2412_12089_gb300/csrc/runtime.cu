@@ -576,9 +576,10 @@ mpm_status mpm_check_status(mpm_ctx* ctx, int32_t* flags) {
     c[e].status = 0;
   }
   CK(cudaMemcpy(ctx->ctr_all, c.data(), sizeof(EnvCtr) * ctx->n_envs, cudaMemcpyHostToDevice));
-  if (any & 8) return fail(ctx, MPM_ERR_TIMEOUT, "a bounded wait on an asynchronous copy gave up");
-  if (any & 6) return fail(ctx, MPM_ERR_NUMERIC, "NaN/Inf or inverted F flagged (bits %d)", any);
-  if (any & 1) return fail(ctx, MPM_ERR_DOMAIN, "a particle left the grid");
+  if (any & MPM_FLAG_WAIT) return fail(ctx, MPM_ERR_TIMEOUT, "a bounded wait on an asynchronous copy gave up");
+  if (any & (MPM_FLAG_NAN | MPM_FLAG_INVERTED))
+    return fail(ctx, MPM_ERR_NUMERIC, "NaN/Inf or inverted F flagged (mask 0x%x)", any);
+  if (any & MPM_FLAG_DOMAIN) return fail(ctx, MPM_ERR_DOMAIN, "a particle left the grid");
   return MPM_OK;
 }
 

@@ -23,6 +23,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NUMERIC", 5: "DOMA
           7: "NOT_READY", 8: "BUDGET", 9: "STATE"}
 MPM_OK, MPM_NOT_READY = 0, 7
 MPM_STEP_RECORD = 1
+# per-environment status word masks (mpm_check_status)
+MPM_FLAG_DOMAIN, MPM_FLAG_NAN, MPM_FLAG_INVERTED, MPM_FLAG_WAIT = 0x1, 0x2, 0x4, 0x8
 
 
 class MpmError(RuntimeError):

@@ -50,6 +50,19 @@ def test_struct_layouts(tmp_path):
     assert got == want
 
 
+def test_header_constants_match_binding(tmp_path):
+    from paper_2412_12089_gb300 import mpm
+
+    names = ["MPM_STEP_RECORD", "MPM_FLAG_DOMAIN", "MPM_FLAG_NAN", "MPM_FLAG_INVERTED", "MPM_FLAG_WAIT"]
+    prog = tmp_path / "consts.c"
+    prog.write_text('#include <stdio.h>\n#include "mpm.h"\nint main(){'
+                    + "".join(f'printf("%u\\n", (unsigned)({n}));' for n in names) + "return 0;}\n")
+    exe = tmp_path / "consts"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert got == [getattr(mpm, n) for n in names]
+
+
 def test_invalid_spec_rejected_without_gpu_work(lib):
     """mpm_create validates specs before touching the device."""
     from paper_2412_12089_gb300 import mpm
