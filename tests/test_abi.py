@@ -68,10 +68,20 @@ def test_invalid_spec_rejected_without_gpu_work(lib):
     from paper_2412_12089_gb300 import mpm
     from paper_2412_12089_gb300 import workloads as wl
 
-    bad = wl.cube(n=64).specs[0].replace(grid_res=30)
+    good = wl.cube(n=64).specs[0]
+    nan = float("nan")
+    cases = [(good.replace(grid_res=30), "grid_res"), (good.replace(grid_res=4), "grid_res"),
+             (good.replace(grid_res=132), "grid_res"), (good.replace(n_particles=0), "n_particles"),
+             (good.replace(n_particles=1 << 20), "n_particles"), (good.replace(substeps=0), "substeps"),
+             (good.replace(dt=0.0), "dt"), (good.replace(dt=nan), "dt"), (good.replace(E=-1.0), "E/nu"),
+             (good.replace(nu=0.5), "E/nu"), (good.replace(bound=16), "bound")]
+    for spec, word in cases:
+        with pytest.raises(mpm.MpmError) as ei:
+            mpm.mpm_create([good, spec])
+        assert ei.value.code == 1 and "env 1" in str(ei.value) and word in str(ei.value), (word, str(ei.value))
     with pytest.raises(mpm.MpmError) as ei:
-        mpm.mpm_create([bad])
-    assert ei.value.code == 1 and "grid_res" in str(ei.value)
+        mpm.mpm_create([])
+    assert ei.value.code == 1 and "n_envs" in str(ei.value)
 
 
 def test_invalid_fem_meshes_rejected_without_gpu_work(lib):
