@@ -6,7 +6,9 @@ the CUDA path against the FP64 FEM oracle:
 - gradients of rewards plus a loss on the final positions with respect to all actions and
   the initial state (1e-3), with and without ground contact;
 - FEM and MPM environments mixed in one batch, forward and reverse, each against its own
-  oracle, and bitwise equal to the per-environment launch path for the FEM environment.
+  oracle, and bitwise equal to the per-environment launch path for the FEM environment;
+- the smallest meshes (one element, one voxel) beside the largest element count the ABI takes
+  (1,020 of 1,024), forward and reverse.
 """
 import numpy as np
 import pytest
@@ -172,3 +174,71 @@ def test_fem_and_mpm_in_one_batch():
                                              rbar=np.ones(T))
     assert rel_err(g["action_grad"][:, 1, :A1], ag1) < 1e-3
     assert rel_err(split(w, g["xb0"])[1], xb1) < 1e-3
+
+
+def fem_body(tets, rest, n_act, substeps=80, ground_z=-1.0):
+    """A SoftJumper-like FEM environment (same material, damping and reward) on any mesh."""
+    n, n_t = rest.shape[0], tets.shape[0]
+    group = (np.arange(n_t) * n_act // n_t).astype(np.int32)
+    h0 = float(np.float32(rest[:, 2].astype(np.float64).mean()))
+    return wl.EnvSpec(n_particles=n, grid_res=8, substeps=substeps, dt=(1.0 / 60.0) / substeps, material="fem",
+                      E=2500.0, nu=0.25, rho=1.0, act_stress=0.2, n_groups=n_act, ground_mu=0.5, reward="jump",
+                      n_sub=n, rparam=(h0, 3.0, 1e-4, 0.0), k_damp=1.0, ground_z=float(np.float32(ground_z)),
+                      fem_tets=tets, fem_rest=rest, fem_group=group, bound=0)
+
+
+def tiny_and_largest_meshes(T, seed=21):
+    rng = np.random.default_rng(seed)
+    one = np.array([[0.5, 0.5, 0.5], [0.55, 0.5, 0.5], [0.5, 0.55, 0.5], [0.5, 0.5, 0.55]], np.float32)
+    vox_rest, vox_tets = wl.voxel_mesh(np.ones((1, 1, 1), bool), 0.05, origin=(0.45, 0.45, 0.3))
+    slab_rest, slab_tets = wl.voxel_mesh(np.ones((12, 17, 1), bool), 0.05, origin=(0.2, 0.075, 0.2))
+    assert slab_tets.shape[0] == 1020
+    specs = [fem_body(np.array([[0, 1, 2, 3]], np.int32), one, 1),
+             fem_body(vox_tets, vox_rest, 2, ground_z=float(vox_rest[:, 2].min()) + 0.004),
+             fem_body(slab_tets, slab_rest, 255)]
+    inits = []
+    for sp in specs:
+        v = (0.1 * rng.standard_normal((sp.n_particles, 3))).astype(np.float32)
+        inits.append(wl.EnvInit(sp.fem_rest.copy(), v, np.zeros((sp.n_particles, 3, 3), np.float32),
+                                np.broadcast_to(np.eye(3, dtype=np.float32), (sp.n_particles, 3, 3)).copy()))
+    acts = np.zeros((T, 3, 255), np.float32)
+    for e, sp in enumerate(specs):
+        acts[:, e, :sp.n_groups] = rng.uniform(-1.0, 1.0, (T, sp.n_groups))
+    return wl.Workload("fem-sizes", specs, inits, acts, T)
+
+
+def test_fem_smallest_and_largest_meshes():
+    import torch
+
+    from paper_2412_12089_gb300.batch import Batch
+
+    T = 2
+    w = tiny_and_largest_meshes(T)
+    rng = np.random.default_rng(22)
+    xw = rng.standard_normal((w.n_particles, 3)).astype(np.float32)
+    rbar = rng.standard_normal((T, w.n_envs)).astype(np.float32)
+    b = Batch(w.specs, max_steps=T)
+    try:
+        b.set_inits(w.inits)
+        rew = [b.step(torch.as_tensor(w.actions[t]).cuda(), record=True).clone() for t in range(T)]
+        st = {k: v.cpu().numpy() for k, v in b.get_state().items()}
+        g = {k: v.cpu().numpy() for k, v in b.backward(xb=xw, reward_adj=rbar).items()}
+        code, flags = b.check_status()
+        rew = torch.stack(rew).cpu().numpy()
+    finally:
+        b.close()
+    assert code == 0 and not flags.any()
+    for e in range(w.n_envs):
+        s = w.specs[e]
+        m = fem.make_mesh(s)
+        A = s.n_groups
+        x, v, r, status = fem.rollout(m, w.inits[e].x, w.inits[e].v, w.actions[:T, e, :A])
+        assert status == 0
+        assert rel_err(split(w, st["x"])[e], x) < 1e-3, (e, rel_err(split(w, st["x"])[e], x))
+        assert rel_err(split(w, st["v"])[e], v) < 1e-3, (e, rel_err(split(w, st["v"])[e], v))
+        assert np.allclose(rew[:, e], r, rtol=1e-3, atol=1e-5), (e, rew[:, e], r)
+        ag, xb, vb, _ = fem.rollout_adj(m, w.inits[e].x, w.inits[e].v, w.actions[:T, e, :A],
+                                        xbT=split(w, xw)[e], rbar=rbar[:, e])
+        assert rel_err(g["action_grad"][:, e, :A], ag) < 1e-3, (e, rel_err(g["action_grad"][:, e, :A], ag))
+        assert rel_err(split(w, g["xb0"])[e], xb) < 1e-3, (e, "xb0", rel_err(split(w, g["xb0"])[e], xb))
+        assert rel_err(split(w, g["vb0"])[e], vb) < 1e-3, (e, "vb0", rel_err(split(w, g["vb0"])[e], vb))

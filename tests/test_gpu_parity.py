@@ -147,6 +147,29 @@ def test_edge_cases_tiny_envs():
         assert rel_err(split(w2, st["x"])[e], o.x) < 1e-5
 
 
+def test_edge_cases_tiny_envs_gradients():
+    """The reverse pass of single-particle and sub-warp environments next to a normal one:
+    gradients of a random linear loss on the final positions, two recorded control steps."""
+    T = 2
+    w = small("cube", seed=17, substeps=3, T=T, n=700)
+    s0, i0 = w.specs[0], w.inits[0]
+    specs = [s0.replace(n_particles=1), s0.replace(n_particles=17), s0]
+    inits = [wl.EnvInit(i0.x[:k].copy(), i0.v[:k].copy(), i0.C[:k].copy(), i0.F[:k].copy()) for k in (1, 17)] + [i0]
+    w2 = wl.Workload("tiny", specs, inits, np.zeros((T, 3, 1), np.float32), T)
+    xw = np.random.default_rng(18).standard_normal((w2.n_particles, 3)).astype(np.float32)
+    g, _ = _gpu_grads(w2, T, xbT=lambda xT: xw)
+    for e in range(3):
+        sp = orc.make_spec(specs[e])
+        so = orc.State.from_init(inits[e])
+        _, (xb, vb, Cb, Fb), _ = orc.rollout_adj(sp, so, np.zeros(4), np.zeros((T, 1)),
+                                                 adj_final=(split(w2, xw)[e].astype(np.float64), None, None, None))
+        # a lone particle's stress momentum cancels exactly in G2P (v_p = v), so its F gradient
+        # is zero up to rounding and has no relative error to compare
+        quantities = (("x", g["xb0"], xb), ("v", g["vb0"], vb)) + ((("F", g["Fb0"], Fb),) if e else ())
+        for name, gg, ref in quantities:
+            assert rel_err(split(w2, gg)[e], ref) < 1e-3, (e, name, rel_err(split(w2, gg)[e], ref))
+
+
 def test_maximum_env_size_and_grid():
     """The largest environment the ABI takes: 1,048,575 particles (the 20-bit particle id) on
     the largest grid, 128^3, one substep from a perturbed state, against the oracle; about
