@@ -275,17 +275,6 @@ def g2p(spec, st: State, gv):
 
 # ------------------------------------------------------------------------ substeps / rollouts
 
-def pose_velocity(es, a):
-    """Pose velocity u for one control step (relative-pose actions, held over the step)."""
-    h = es.substeps * es.dt
-    if es.collider == "capsules":
-        return np.array([es.act_scale[j % 4] * a[j] / h for j in range(4 * es.n_caps)])
-    u = np.zeros(4)
-    for j, m in enumerate(es.act_map):
-        u[m] += es.act_scale[j] * a[j] / h
-    return u
-
-
 def substep(spec, st: State, q=None, u=None, act=None):
     out = st.copy()
     pl = pose_len(spec)

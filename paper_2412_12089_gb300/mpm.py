@@ -136,20 +136,6 @@ def lib():
     return L
 
 
-def exported_symbols():
-    """Names of the entry points the loaded library exports (for ABI checks)."""
-    L = lib()
-    names = []
-    for n in ("mpm_create", "mpm_destroy", "mpm_n_envs", "mpm_n_particles", "mpm_action_dim", "mpm_tape_length",
-              "mpm_device_bytes", "mpm_last_error", "mpm_set_state", "mpm_get_state", "mpm_step", "mpm_backward",
-              "mpm_reset_tape", "mpm_check_status", "mpm_bin", "mpm_kernel_launches", "mpm_time_kernel",
-              "mpm_kernel_time", "mpm_last_active_tiles", "mpm_server_create", "mpm_server_destroy",
-              "mpm_submit", "mpm_poll", "mpm_wait", "mpm_release", "mpm_server_last_error"):
-        if hasattr(L, n):
-            names.append(n)
-    return names
-
-
 # ----------------------------------------------------------------------------- marshalling
 
 def ptr(a):

@@ -382,10 +382,3 @@ def softjumper(n_envs: int = 256, seed: int = 0, substeps: int = 80, T: int = 16
         inits.append(_rest_state(rest, np.zeros((n, 3))))
         acts.append(rng.uniform(-1.0, 1.0, (T, n_act)))
     return Workload("softjumper", specs, inits, _pad_actions(acts, T), T)
-
-
-def concat_inits(inits):
-    """Concatenate per-env initial states in env order (particle-major arrays)."""
-    return EnvInit(np.concatenate([i.x for i in inits]), np.concatenate([i.v for i in inits]),
-                   np.concatenate([i.C for i in inits]), np.concatenate([i.F for i in inits]),
-                   np.concatenate([i.group for i in inits]))

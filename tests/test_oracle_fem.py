@@ -11,7 +11,6 @@ Euler; App. E SoftJumper damping, activations and reward) against what the mathe
 - the checkpointed reverse mode matches central differences of a rollout loss.
 """
 import numpy as np
-import pytest
 
 from oracle import fem
 from paper_2412_12089_gb300 import workloads as wl

@@ -11,7 +11,7 @@ from oracle import oracle as orc
 from paper_2412_12089_gb300 import mpm
 from paper_2412_12089_gb300 import workloads as wl
 
-from gpu_helpers import perturb, rel_err
+from gpu_helpers import rel_err
 
 pytestmark = pytest.mark.gpu
 
