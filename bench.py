@@ -47,8 +47,8 @@ ALGO_BYTES = {
 MEASURED_TRAFFIC = {
     # ncu captures of one launch over 1,310,720 binned fluid particles (160 envs, 64^3), in
     # dram__bytes_read.sum + dram__bytes_write.sum per particle; scaled by particle count
-    "g2p_adj": (202.3, "a04951eda31bad8c"),  # 217.0 MB read + 48.2 MB written, adjoint substep 4
-    "g2p": (104.8, "a04951eda31bad8c"),      # 70.5 MB read + 66.8 MB written, forward substep 1
+    "g2p_adj": (200.1, "d89daff75e39d176"),  # 214.5 MB read + 47.7 MB written, adjoint substep 4
+    "g2p": (104.7, "d89daff75e39d176"),      # 70.5 MB read + 66.8 MB written, forward substep 1
 }
 
 

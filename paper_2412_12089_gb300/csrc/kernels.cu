@@ -1149,20 +1149,26 @@ __global__ void __launch_bounds__(kBlock, 5) k_g2p_adj(const EnvDesc* __restrict
         const float q1 = vnb[1] + Ab[4] * ry + Ab[5] * rz;
         const float q2 = vnb[2] + Ab[7] * ry + Ab[8] * rz;
         const float4* rowp = e.grid_v + ((long long)(b2 + oc) * e.G + (b1 + ob)) * e.G + b0;
+        // the row's sums over x first; its y and z factors are applied once
+        float sd = 0.f, sw = 0.f, gw0 = 0.f, gw1 = 0.f, gw2 = 0.f;
 #pragma unroll
         for (int oa = 0; oa < 3; ++oa) {
           const float4 gv = __ldg(rowp + oa);
           const float g0 = gv.x - vc.x, g1 = gv.y - vc.y, g2 = gv.z - vc.z;
           const float rx = ((float)oa - fx[0]) * dx;
           const float sdw = g0 * (q0 + Ab[0] * rx) + g1 * (q1 + Ab[3] * rx) + g2 * (q2 + Ab[6] * rx);
-          xbp[0] += sdw * (dw[0][oa] * wyz);
-          xbp[1] += sdw * (w[0][oa] * dwy_wz);
-          xbp[2] += sdw * (w[0][oa] * wy_dwz);
-          const float wt = w[0][oa] * wyz;
-          swg[0] += wt * g0;
-          swg[1] += wt * g1;
-          swg[2] += wt * g2;
+          sd += sdw * dw[0][oa];
+          sw += sdw * w[0][oa];
+          gw0 += w[0][oa] * g0;
+          gw1 += w[0][oa] * g1;
+          gw2 += w[0][oa] * g2;
         }
+        xbp[0] += sd * wyz;
+        xbp[1] += sw * dwy_wz;
+        xbp[2] += sw * wy_dwz;
+        swg[0] += gw0 * wyz;
+        swg[1] += gw1 * wyz;
+        swg[2] += gw2 * wyz;
       }
     }
 #pragma unroll
