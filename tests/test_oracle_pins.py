@@ -798,3 +798,68 @@ def test_capsules_rollout_adjoint_fd():
         assert close(fd, qb[i], np.abs(qb).max()), (i, fd, qb[i])
     # every capsule takes part in the contact
     assert all(np.abs(qb[4 * j:4 * j + 3]).max() > 0 for j in range(3))
+
+
+# ------------------------------------------------------------------ symmetries of a substep (App. D.3)
+
+_RZ = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])  # quarter turn about z
+
+
+def _rotate(st, c):
+    """The state turned a quarter about the vertical axis through (c/2, c/2): points
+    (x, y, z) -> (c - y, x, z), vectors by _RZ, matrices by _RZ M _RZ^T."""
+    x = np.stack([c - st.x[:, 1], st.x[:, 0], st.x[:, 2]], 1)
+    out = orc.State(x, st.v @ _RZ.T, _RZ @ st.C @ _RZ.T, _RZ @ st.F @ _RZ.T, st.group)
+    return out
+
+
+def _rotate_pose(q, u, c):
+    return (np.array([c - q[1], q[0], q[2], q[3] + np.pi / 2]), np.array([-u[1], u[0], u[2], u[3]]))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_substep_quarter_turn_equivariance(name):
+    """A substep commutes with a quarter turn about the vertical axis through the centre of
+    the node lattice, which maps nodes onto nodes (i, j) -> (G-1-j, i) and the quadratic
+    B-spline stencil onto itself: the materials are isotropic (the muscle fibre is vertical),
+    gravity and the ground are vertical, the walls are symmetric, and the collider turns with
+    its pose.  Any mixed-up axis or index in P2G, the grid update or G2P breaks this."""
+    sp, st, q, u, act = _tiny_case(name, seed=23)
+    c = (sp.G - 1) / sp.G
+    out, s0 = orc.substep(sp, st, q, u, act)
+    qr, ur = _rotate_pose(q, u, c)
+    out_r, s1 = orc.substep(sp, _rotate(st, c), qr, ur, act)
+    assert s0 == 0 and s1 == 0
+    want = _rotate(out, c)
+    for k, (a, b) in enumerate(zip(out_r.arrays(), want.arrays())):
+        assert np.abs(a - b).max() <= 1e-11 * max(np.abs(b).max(), 1.0), (name, k, np.abs(a - b).max())
+    # the substep moved something (the comparison is not between two unchanged states)
+    assert np.abs(out.v - st.v).max() > 1e-6
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_substep_whole_cell_translation_invariance(name):
+    """Away from the walls, shifting the particles and the collider by whole cells shifts
+    the result by the same amount and leaves v, C and F unchanged (weights depend only on
+    positions relative to the node lattice)."""
+    kw = dict(CASES[name])
+    rng = np.random.default_rng(29)
+    G = 32
+    sp = spec_for(G=G, dt=2e-3, bound=2, **kw)
+    st = _rand_state(12, G, rng, lo=0.4, hi=0.6, vs=0.5)
+    if name == "container":
+        st.F = np.broadcast_to(np.eye(3), st.F.shape) * np.cbrt(1 + 0.02 * rng.standard_normal((12, 1, 1)))
+    st.group = rng.integers(-1, 4, 12).astype(np.int32)
+    q = np.array([0.5, 0.5, 0.42, 0.2]) + 0.02 * rng.standard_normal(4)
+    u = 0.3 * rng.standard_normal(4)
+    act = np.concatenate([np.zeros(len(kw.get("act_map", ()))), rng.uniform(-1, 1, 4)])
+    shift = np.array([3.0, -2.0, 1.0]) / G
+    out, s0 = orc.substep(sp, st, q, u, act)
+    moved = st.copy()
+    moved.x = st.x + shift
+    out_m, s1 = orc.substep(sp, moved, q + np.append(shift, 0.0), u, act)
+    assert s0 == 0 and s1 == 0
+    assert np.abs(out_m.x - (out.x + shift)).max() < 1e-13
+    for a, b in ((out_m.v, out.v), (out_m.C, out.C), (out_m.F, out.F)):
+        assert np.abs(a - b).max() <= 1e-10 * max(np.abs(b).max(), 1.0)
+    assert np.abs(out.v - st.v).max() > 1e-6
