@@ -8,7 +8,8 @@ Euler; App. E SoftJumper damping, activations and reward) against what the mathe
   the energy), and equal -dE/dx;
 - a rest mesh in free fall follows the closed form of the discrete scheme;
 - the ground stops a falling vertex and applies Coulomb friction;
-- the checkpointed reverse mode matches central differences of a rollout loss.
+- the checkpointed reverse mode matches central differences of a rollout loss;
+- a substep commutes with vertical-axis turns and horizontal shifts of the body.
 """
 import numpy as np
 
@@ -179,3 +180,34 @@ def test_softjumper_mesh_and_rollout():
         np.diag(s.fem_rest.max(0) - s.fem_rest.min(0))) / (7 * 4 * 4)), rtol=1e-5)
     x, v, r, st = fem.rollout(m, w.inits[0].x, w.inits[0].v, w.actions[:2, 0, :220])
     assert st == 0 and np.all(np.isfinite(x)) and x[:, 2].min() > -0.01
+
+
+def test_substep_commutes_with_vertical_rotations_and_horizontal_shifts():
+    """Objectivity of the semi-implicit step: turning the deformed, moving body about a
+    vertical axis (rest shape unchanged) turns the result, and shifting it horizontally shifts
+    the result.  Gravity, the ground and its friction are vertical or horizontal-isotropic, the
+    energy and the damping stress k_damp * Fdot are frame-indifferent, and the activations
+    act on J.  A dropped or transposed term in P or in the corner forces breaks this."""
+    rng = np.random.default_rng(31)
+    m, x = _mesh((2, 2, 1), rng=rng, jitter=0.001, mu=900.0, lam=1300.0, k_damp=1.5, n_act=3, ground_mu=0.4,
+                 act_scale=0.3, dt=1e-4)
+    m.spec.ground_z = float(np.sort(x[:, 2])[3])  # four vertices at or below the ground
+    v = 0.3 * rng.standard_normal(x.shape)
+    v[:, 2] = -0.2 - np.abs(v[:, 2])  # moving down: the ground projects and rubs
+    ae = rng.uniform(-0.2, 0.2, m.spec.n_t)
+    x1, v1, st = fem.substep(m, x, v, ae)
+    on = x[:, 2] <= m.spec.ground_z
+    assert st == 0 and on.sum() >= 4 and np.all(v1[on, 2] == 0.0)
+    assert (np.hypot(v1[on, 0], v1[on, 1]) > 0.0).sum() >= 2  # sliding: friction depends on direction
+    th = 0.7
+    R = np.array([[np.cos(th), -np.sin(th), 0.0], [np.sin(th), np.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    p = np.array([0.4, 0.35, 0.0])  # a point on the axis
+    xr, vr, st = fem.substep(m, (x - p) @ R.T + p, v @ R.T, ae)
+    assert st == 0
+    assert np.abs(xr - ((x1 - p) @ R.T + p)).max() <= 1e-13
+    assert np.abs(vr - v1 @ R.T).max() <= 1e-11 * np.abs(v1).max()
+    s = np.array([0.125, -0.0625, 0.0])
+    xs, vs, st = fem.substep(m, x + s, v, ae)
+    assert st == 0
+    assert np.abs(xs - (x1 + s)).max() <= 1e-13 and np.abs(vs - v1).max() <= 1e-11 * np.abs(v1).max()
+    assert np.abs(v1 - v).max() > 1e-4  # the step changed the state
