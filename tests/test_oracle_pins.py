@@ -863,3 +863,26 @@ def test_substep_whole_cell_translation_invariance(name):
     for a, b in ((out_m.v, out.v), (out_m.C, out.C), (out_m.F, out.F)):
         assert np.abs(a - b).max() <= 1e-10 * max(np.abs(b).max(), 1.0)
     assert np.abs(out.v - st.v).max() > 1e-6
+
+
+@pytest.mark.parametrize("material", ["neohookean", "vonmises", "muscle", "fluid"])
+def test_substep_preserves_affine_velocity(material):
+    """APIC through a whole substep (P2G, grid update, G2P): particles at rest shape (F = I, so
+    no stress) carrying an affine field v_p = a + B x_p with C_p = B keep it exactly, with no
+    gravity and away from the walls: P2G gives m_i (a + B x_i) on every node and G2P reads
+    it back.  For the fluid B is a rotation rate, since its viscosity acts on C + C^T."""
+    rng = np.random.default_rng(37)
+    G = 16
+    sp = spec_for(material, G=G, dt=1e-3, bound=3, gravity=(0.0, 0.0, 0.0))
+    n = 40
+    x = 0.35 + 0.3 * rng.random((n, 3))
+    a = rng.standard_normal(3)
+    B = rng.standard_normal((3, 3))
+    if material == "fluid":
+        B = B - B.T
+    st = orc.State(x, a + x @ B.T, np.broadcast_to(B, (n, 3, 3)), np.broadcast_to(np.eye(3), (n, 3, 3)))
+    out, status = orc.substep(sp, st, act=np.zeros(4))
+    assert status == 0
+    assert np.abs(out.v - (a + st.x @ B.T)).max() <= 1e-12 * np.abs(st.v).max()
+    assert np.abs(out.C - B).max() <= 1e-10 * np.abs(B).max()
+    assert np.abs(out.x - (st.x + sp.dt * out.v)).max() <= 1e-15
