@@ -109,6 +109,75 @@ def test_invalid_fem_meshes_rejected_without_gpu_work(lib):
         assert ei.value.code == 1 and word in str(ei.value), (word, str(ei.value))
 
 
+def test_binning_entry_points_validate_before_device_work(lib):
+    """mpm_bin / mpm_bin_static reject bad sizes, grids and pointers before any launch, and
+    an empty input is a no-op (all without a GPU)."""
+    import numpy as np
+
+    from paper_2412_12089_gb300 import mpm
+
+    x = np.zeros((4, 3), np.float32)
+    k = np.zeros(4, np.uint32)
+    p = np.zeros(4, np.uint32)
+    for fn in (mpm.mpm_bin, mpm.mpm_bin_static):
+        for args in ((x, -1, 32, k, p), (x, 4, 30, k, p), (x, 4, 4, k, p), (x, 4, 132, k, p), (None, 4, 32, k, p),
+                     (x, 4, 32, None, p), (x, 4, 32, k, None)):
+            with pytest.raises(mpm.MpmError) as ei:
+                fn(*args)
+            assert ei.value.code == 1, (fn.__name__, args[1:3])
+        assert fn(x, 0, 32, k, p) == 0
+    big = mpm.mpm_bin_static_max() + 1
+    with pytest.raises(mpm.MpmError) as ei:
+        mpm.mpm_bin_static(x, big, 32, k, p)
+    assert ei.value.code == 1
+
+
+_NULL_CALLS = """
+import ctypes as ct
+from paper_2412_12089_gb300 import mpm
+L = mpm.lib()
+N = None
+calls = {
+    "mpm_set_state": (N,) * 8, "mpm_get_state": (N,) * 7, "mpm_step": (N, N, N, 0, N),
+    "mpm_backward": (N,) * 13, "mpm_backward_begin": (N,) * 6, "mpm_backward_step": (N,) * 6,
+    "mpm_backward_end": (N,) * 8, "mpm_reset_tape": (N,), "mpm_check_status": (N, N),
+    "mpm_time_kernel": (N, 0), "mpm_kernel_time": (N, N, N), "mpm_observe": (N, N, N),
+    "mpm_set_obs_adjoint": (N, N, N), "mpm_autotune": (N, 3, N, N),
+    "mpm_submit": (N, N, N), "mpm_poll": (N, 0, N), "mpm_wait": (N, 0, 1.0, N), "mpm_release": (N, 0),
+}
+bad = {k: getattr(L, k)(*a) for k, a in calls.items()}
+L.mpm_destroy(None)
+L.mpm_server_destroy(None)
+getters = (L.mpm_n_envs(None), L.mpm_n_particles(None), L.mpm_action_dim(None), L.mpm_tape_length(None),
+           L.mpm_device_bytes(None), L.mpm_kernel_launches(None), L.mpm_obs_dim(None))
+print(repr((bad, getters, L.mpm_last_error(None), L.mpm_server_last_error(None))))
+"""
+
+
+def test_null_handles_are_rejected_not_dereferenced(lib):
+    """Every entry point that takes a context or server handle returns INVALID_ARG for a NULL
+    one, getters return 0, destroy is a no-op, and the error strings say why; run in a child
+    process so that a dereference would show as a crash, not take the test runner down."""
+    import ast
+    import sys
+
+    out = subprocess.run([sys.executable, "-c", _NULL_CALLS], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    bad, getters, err, serr = ast.literal_eval(out.stdout.strip().splitlines()[-1])
+    assert all(code == 1 for code in bad.values()), bad
+    assert all(g == 0 for g in getters), getters
+    assert b"null" in err and b"null" in serr
+
+
+def test_server_options_validated_before_device_work(lib):
+    from paper_2412_12089_gb300 import mpm
+
+    for kw in (dict(mem_fraction=0.0), dict(mem_fraction=1.5), dict(max_resident=0), dict(chunk=128)):
+        with pytest.raises(mpm.MpmError) as ei:
+            mpm.mpm_server_create(**kw)
+        assert ei.value.code == 1, kw
+
+
 def test_product_path_never_imports_oracle():
     """The package sources do not reference the oracle (it is test infrastructure)."""
     pkg = os.path.join(ROOT, "paper_2412_12089_gb300")
