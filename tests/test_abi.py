@@ -82,6 +82,11 @@ def test_invalid_spec_rejected_without_gpu_work(lib):
     with pytest.raises(mpm.MpmError) as ei:
         mpm.mpm_create([])
     assert ei.value.code == 1 and "n_envs" in str(ei.value)
+    for kw, word in ((dict(max_steps=-1), "max_steps"), (dict(max_steps=100001), "max_steps"),
+                     (dict(chunk=128), "chunk")):
+        with pytest.raises(mpm.MpmError) as ei:
+            mpm.mpm_create([good], **kw)
+        assert ei.value.code == 1 and word in str(ei.value), (kw, str(ei.value))
 
 
 def test_invalid_fem_meshes_rejected_without_gpu_work(lib):
