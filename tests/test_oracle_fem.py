@@ -9,7 +9,8 @@ Euler; App. E SoftJumper damping, activations and reward) against what the mathe
 - a rest mesh in free fall follows the closed form of the discrete scheme;
 - the ground stops a falling vertex and applies Coulomb friction;
 - the checkpointed reverse mode matches central differences of a rollout loss;
-- a substep commutes with vertical-axis turns and horizontal shifts of the body.
+- a substep commutes with vertical-axis turns and horizontal shifts of the body;
+- rest volumes, Dm^-1 and lumped masses of a voxel mesh in closed form.
 """
 import numpy as np
 
@@ -211,3 +212,21 @@ def test_substep_commutes_with_vertical_rotations_and_horizontal_shifts():
     assert st == 0
     assert np.abs(xs - (x1 + s)).max() <= 1e-13 and np.abs(vs - v1).max() <= 1e-11 * np.abs(v1).max()
     assert np.abs(v1 - v).max() > 1e-4  # the step changed the state
+
+
+def test_rest_quantities_closed_form():
+    """Rest data of a voxel mesh: the five elements of each voxel fill it (their rest volumes
+    sum to the voxel count times edge^3, the central element holding a third of each voxel),
+    Dm^-1 inverts each element's edge matrix, and the lumped masses rho V / 4 per corner add
+    up to the body's mass."""
+    m, x = _mesh((3, 2, 2), size=0.05, rho=7.0)
+    n_vox, size = 12, 0.05
+    # the lattice is stored in FP32, so the voxels are cubes to about 1e-7
+    assert abs(m.vol.sum() - n_vox * size ** 3) <= 1e-6 * n_vox * size ** 3
+    central = m.vol.reshape(n_vox, 5)[:, 4]
+    assert np.allclose(central, size ** 3 / 3.0, rtol=1e-6)
+    for e, t in enumerate(m.tets):
+        Dm = np.stack([x[t[c + 1]] - x[t[0]] for c in range(3)], 1)
+        assert np.allclose(m.dminv[e].reshape(3, 3) @ Dm, np.eye(3), atol=1e-10)
+        assert abs(abs(np.linalg.det(Dm)) / 6.0 - m.vol[e]) <= 1e-15
+    assert abs((1.0 / m.inv_mass).sum() - 7.0 * m.vol.sum()) <= 1e-12 * 7.0 * m.vol.sum()
