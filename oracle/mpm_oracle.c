@@ -1206,6 +1206,7 @@ double orc_reward(const orc_spec* s, int n, const double* x, const double* v, co
 void orc_reward_adj(const orc_spec* s, int n, const double* x, const double* v, const double* q,
                     const double* a, double rb, double* xb, double* vb, double* qb, double* ab)
 {
+    (void)v; /* every reward is linear in v: its adjoint does not depend on v's value */
     int ns = s->n_sub < n ? s->n_sub : n;
     switch (s->reward_kind) {
     case ORC_REWARD_FLAT: {
