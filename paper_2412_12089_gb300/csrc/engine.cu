@@ -488,7 +488,7 @@ Launch mat_launch(const Launch& L, const MatGroup& m, int k) {
 }
 
 // tape: record every substep's grid into the grid tape (recorded steps), or NULL.
-void substeps_forward(Group& g, const Launch& L, const std::vector<MatGroup>& mats, int S, const GridTape* tape) {
+void substeps_forward(const Launch& L, const std::vector<MatGroup>& mats, int S, const GridTape* tape) {
   for (int k = 0; k < S; ++k) {
     cudaMemsetAsync(L.active_n, 0, sizeof(int), L.stream);
     const StateRef src{k == 0 ? REF_LIVE : REF_NEXT, k};
@@ -609,7 +609,7 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
     launch_fem_forward(L, g.d_fem, (int)g.fem_envs.size(), g.fem_nv_max, g.fem_nt_max);
     if (g.S_max > 0) {
       bin_envs(L, 0, g.P, g.cell_bits, g.key_bits, g.sort);
-      substeps_forward(g, L, g.mats, g.S_max, record && g.tape.cap > 0 ? &g.tape : nullptr);
+      substeps_forward(L, g.mats, g.S_max, record && g.tape.cap > 0 ? &g.tape : nullptr);
     }
     launch_reward_end(L, rew, record);
     return;
@@ -629,7 +629,7 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
     one[0].n_gt[S] = 0;
     launch_step_begin(L, act_in, a_max, record);
     bin_envs(L, g.desc[e].poff, g.spec[e].n_particles, g.cell_bits, g.cell_bits, g.sort);
-    substeps_forward(g, L, one, S, nullptr);
+    substeps_forward(L, one, S, nullptr);
     launch_reward_end(L, rew, record);
   }
 }
