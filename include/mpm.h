@@ -161,26 +161,40 @@ typedef struct mpm_ctx mpm_ctx;
  * steps with its recompute ring, and scratch.  The state starts at rest at the origin
  * with collider poses pose0; call mpm_set_state before stepping.
  * Errors: INVALID_ARG for an unusable spec (field named in mpm_last_error), OOM, CUDA.
+ * Passage: App. F (the parallel environments of a task share one physics scene and are
+ *   stepped together); the spec's fields are App. D.3's material, grid and contact
+ *   parameters and App. E's task constants.
  */
 mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* opt, mpm_ctx** out);
+/* Release the context and every device buffer it owns (NULL is ignored).
+ * Passage: none in the paper (resource management of the C ABI). */
 void mpm_destroy(mpm_ctx* ctx);
 
+/* Sizes of a context: environments, particles P, the action width A_max (the largest
+ * n_coll_act + n_groups of the batch), control steps recorded since the last reset, and the
+ * device bytes held (arena, grids, tape, scratch).  0 for a NULL context.
+ * Passage: none in the paper (queries of the C ABI). */
 int32_t mpm_n_envs(const mpm_ctx* ctx);
-int64_t mpm_n_particles(const mpm_ctx* ctx);  /* P */
-int32_t mpm_action_dim(const mpm_ctx* ctx);   /* A_max = max over envs of n_coll_act + n_groups */
-int32_t mpm_tape_length(const mpm_ctx* ctx);  /* control steps recorded since the last reset */
-/* Device bytes the context holds (arena, grids, tape, scratch). */
+int64_t mpm_n_particles(const mpm_ctx* ctx);
+int32_t mpm_action_dim(const mpm_ctx* ctx);
+int32_t mpm_tape_length(const mpm_ctx* ctx);
 int64_t mpm_device_bytes(const mpm_ctx* ctx);
+/* Text of the last failure of a call on this context ("" if none); owned by the context,
+ * valid until its next call.
+ * Passage: none in the paper (error reporting of the C ABI). */
 const char* mpm_last_error(const mpm_ctx* ctx);
 
 /*
  * Set the particle state (x, v, C, F: layouts above; group: [P] actuator group per
  * particle, -1 = passive, NULL = all passive) and collider poses (pose: [n_envs][4],
  * NULL = keep).  Resets the checkpoint tape.  Any pointer may be host or device memory.
+ * Passage: App. D.3 (the MPM particle state: position, velocity, APIC affine matrix C and
+ *   deformation gradient F) and Sec. 3 (the environment state s_t an episode starts from).
  */
 mpm_status mpm_set_state(mpm_ctx* ctx, const float* x, const float* v, const float* C, const float* F,
                          const int32_t* group, const float* pose, void* stream);
-/* Copy the current state out, in the caller's particle order (any pointer may be NULL). */
+/* Copy the current state out, in the caller's particle order (any pointer may be NULL).
+ * Passage: App. D.3 (the particle state) and Sec. 3 (the next state s_{t+1} of a step). */
 mpm_status mpm_get_state(mpm_ctx* ctx, float* x, float* v, float* C, float* F, float* pose,
                          void* stream);
 
@@ -193,6 +207,8 @@ mpm_status mpm_get_state(mpm_ctx* ctx, float* x, float* v, float* C, float* F, f
  * reward:  [n_envs] output, or NULL.
  * flags:   MPM_STEP_RECORD to append the step to the tape (STATE if the tape is full);
  *   without it the tape is reset.
+ * Passage: Alg. 1 and Sec. 3 (the transition env.step(a_t) -> s_{t+1}, r_t); each substep
+ *   is App. D.3's MLS-MPM pass, the rewards are App. E's.
  */
 mpm_status mpm_step(mpm_ctx* ctx, const float* actions, float* reward, uint32_t flags, void* stream);
 
@@ -205,6 +221,8 @@ mpm_status mpm_step(mpm_ctx* ctx, const float* actions, float* reward, uint32_t 
  *  xb0..Fb0:       adjoint of the state at the start of the tape, or NULL.
  *  pose_grad0:     [n_envs][4] adjoint of the collider pose at the start, or NULL.
  * The tape is kept, so mpm_backward may be called again with other adjoints.
+ * Passage: Sec. 4.1 (analytic first-order gradients through the simulator, with gradient
+ *   checkpointing at control-step boundaries).
  */
 mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const float* Cb, const float* Fb,
                         const float* reward_adj, float* action_grad, float* xb0, float* vb0, float* Cb0,
@@ -230,6 +248,8 @@ mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const fl
  * Pointers are device or host; each call copies its inputs before it returns.  mpm_step,
  * mpm_set_state and mpm_reset_tape abandon an open pass; mpm_backward refuses to run during
  * one.  With the same adjoints the results equal mpm_backward's.
+ * Passage: Sec. 4.1 and Alg. 1 (the actor's first-order gradient through a closed-loop
+ *   rollout).
  */
 mpm_status mpm_backward_begin(mpm_ctx* ctx, const float* xb, const float* vb, const float* Cb, const float* Fb,
                               void* stream);
@@ -238,7 +258,8 @@ mpm_status mpm_backward_step(mpm_ctx* ctx, const float* reward_adj, const float*
 mpm_status mpm_backward_end(mpm_ctx* ctx, const float* obs_adj, float* xb0, float* vb0, float* Cb0, float* Fb0,
                             float* pose_grad0, void* stream);
 
-/* Forget the recorded steps; the current state stays. */
+/* Forget the recorded steps; the current state stays.
+ * Passage: Sec. 4.1 (the checkpoint tape of a rollout). */
 mpm_status mpm_reset_tape(mpm_ctx* ctx);
 
 /* Status word masks, per environment. */
@@ -252,6 +273,7 @@ mpm_status mpm_reset_tape(mpm_ctx* ctx);
  * accumulated since the last call, which clears them.
  * flags: [n_envs] host array or NULL.  Returns TIMEOUT (MPM_FLAG_WAIT), NUMERIC (MPM_FLAG_NAN
  * or MPM_FLAG_INVERTED) or DOMAIN (MPM_FLAG_DOMAIN) if a mask is set, in that order.
+ * Passage: none in the paper (failure reporting of the C ABI).
  */
 mpm_status mpm_check_status(mpm_ctx* ctx, int32_t* flags);
 
@@ -262,22 +284,30 @@ mpm_status mpm_check_status(mpm_ctx* ctx, int32_t* flags);
  * nearest), key = ((bz/4 * G/4 + by/4) * G/4 + bx/4) * 64 + (bz%4)*16 + (by%4)*4 + bx%4.
  * perm: the stable sort of keys (perm[j] = index of the j-th smallest key, ties in index
  * order).  keys, perm: device [n].  Uses a device scratch it allocates and frees.
+ * Passage: App. D.3 (MLS-MPM's quadratic B-spline stencil of the cell base); the sort is
+ *   the binning scheme of this library, with no counterpart in the paper.
  */
 mpm_status mpm_bin(const float* x, int32_t n, int32_t grid_res, uint32_t* keys, uint32_t* perm, void* stream);
 
 /*
- * mpm_bin without any allocation (no counterpart in the paper: a systems entry point).
+ * mpm_bin without any allocation.  Passage: none; the paper has no counterpart (a systems
+ * entry point).
  * Same arguments, keys and perm as mpm_bin, bit for bit, but the sort scratch is a fixed
  * file-scope device array sized for mpm_bin_static_max() = 262144 particles (4 MiB + 64 KiB),
- * so it calls no cudaMalloc, cudaFree or allocating library routine.  It is for callers that
- * cannot allocate: the serving loop, where a per-call cudaFree would synchronise the whole
- * device and stall the forward and reverse streams running other requests, and callers that
- * have committed the device's memory to resident environments (the admission budget), where
- * a cudaMalloc can fail in the middle of a run.
+ * so it calls no cudaMalloc, cudaFree or allocating library routine.  It is for external
+ * callers that cannot allocate device memory: a loop that keeps other streams busy, where a
+ * cudaFree would synchronise the whole device and stall them, and a process that has
+ * committed the device's memory to resident work, where a cudaMalloc can fail in the middle
+ * of a run.  (This library's own server keeps a sort scratch of its own and does not call it.)
  *   n > mpm_bin_static_max(): MPM_ERR_INVALID_ARG, nothing launched.  Other argument errors
  *   as mpm_bin.  The work is enqueued on `stream` and the call returns without waiting.
+ *   A CUDA error already pending on the calling thread when the call starts: MPM_ERR_CUDA,
+ *   nothing launched, the pending error left in place for its owner.  A failed launch of
+ *   this call: MPM_ERR_CUDA, and that error is consumed.
  *   The first call on a device, with that device current, looks up the array's device
- *   address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   address (cudaGetSymbolAddress) and keeps it for the process; make that first call
+ *   before any stream capture.  cudaDeviceReset on that device unloads the array and makes
+ *   the kept address stale: do not call mpm_bin_static on a device after resetting it.
  *   Every call shares the one array: calls whose work overlaps on the GPU (other streams,
  *   unordered threads) race and give wrong keys and perm.  Nothing in the array needs to
  *   start at zero, so stale contents of an earlier call do not matter.
@@ -294,6 +324,7 @@ int32_t mpm_bin_static_max(void);
  *        [x' (3 * ns_max, zero padded past ns)][mean (3)][pose (4, zero padded)][p* (3)],
  *        ns_max = the largest ns of the batch, so mpm_obs_dim = 3 * ns_max + 10.
  *   Stream-ordered; the context's live state is read, nothing changed.
+ * Passage: App. E (the observation spaces of the MPM tasks).
  */
 int32_t mpm_obs_dim(const mpm_ctx* ctx);
 mpm_status mpm_observe(mpm_ctx* ctx, float* obs, void* stream);
@@ -303,6 +334,7 @@ mpm_status mpm_observe(mpm_ctx* ctx, float* obs, void* stream);
  * length (row t: the state before recorded step t; row T: the current state).  Copied
  * before the call returns.  NULL forgets adjoints set earlier.  MPM_ERR_STATE without a
  * tape (max_steps = 0).
+ * Passage: Sec. 4.1 and App. E (gradients through the observations a policy reads).
  */
 mpm_status mpm_set_obs_adjoint(mpm_ctx* ctx, const float* obs_adj, void* stream);
 
@@ -317,6 +349,7 @@ mpm_status mpm_set_obs_adjoint(mpm_ctx* ctx, const float* obs_adj, void* stream)
  *   box_out: [4] host, chosen capacity by material (MPM_MAT_*), 0 for absent materials;
  *   ms_out:  [4][2] host, mean P2G time (ms) per material with 512 and 1024 nodes;
  *   either may be NULL.  trials in [1, 1000], else MPM_ERR_INVALID_ARG.  Synchronises.
+ * Passage: none in the paper (launch-shape tuning of this library).
  */
 mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* ms_out);
 
@@ -326,17 +359,20 @@ mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* m
 enum { MPM_K_P2G = 1, MPM_K_GRID = 2, MPM_K_G2P = 3, MPM_K_G2P_ADJ = 4, MPM_K_GRID_ADJ = 5, MPM_K_P2G_ADJ = 6,
        MPM_K_BIN = 7, MPM_K_OTHER = 8 };
 
-/* Number of CUDA kernels this context has launched (a replayed graph counts its kernels). */
+/* Number of CUDA kernels this context has launched (a replayed graph counts its kernels).
+ * Passage: none in the paper (instrumentation). */
 int64_t mpm_kernel_launches(const mpm_ctx* ctx);
 /* Time every launch of one kernel class (MPM_K_*), or of every class (-1), with CUDA events
  * recorded on the launching stream; 0 = off.  While on, the context launches its kernels
- * directly instead of replaying graphs. */
+ * directly instead of replaying graphs.  Passage: none in the paper (instrumentation). */
 mpm_status mpm_time_kernel(mpm_ctx* ctx, int32_t kernel_class);
 /* Synchronise and return the summed duration (ms) and count of the timed launches since the
  * last call, which resets them.  One class timed: total_ms[0], launches[0].  All classes
- * timed: total_ms[k], launches[k] for k = 0..MPM_K_OTHER (arrays of MPM_K_OTHER + 1). */
+ * timed: total_ms[k], launches[k] for k = 0..MPM_K_OTHER (arrays of MPM_K_OTHER + 1).
+ * Passage: none in the paper (instrumentation). */
 mpm_status mpm_kernel_time(mpm_ctx* ctx, double* total_ms, int64_t* launches);
-/* Synchronise and return the number of active 4^3 grid tiles of the last substep. */
+/* Synchronise and return the number of active 4^3 grid tiles of the last substep.
+ * Passage: none in the paper (instrumentation). */
 int32_t mpm_last_active_tiles(mpm_ctx* ctx);
 
 /* ------------------------------------------------------------------ serving */
@@ -377,17 +413,28 @@ typedef struct {
  * running, as slots and memory free up (admission by memory budget), and all resident
  * environments advance together, one control step per tick, forward and reverse on two
  * streams.  Results stay library-owned until mpm_release.
+ * Passage: none in the paper, which runs a fixed batch of parallel environments (App. F);
+ *   request serving is a systems layer of this library.  Each request's rollout is the
+ *   transition of Alg. 1 repeated, its gradient the reverse pass of Sec. 4.1.
  */
 mpm_status mpm_server_create(const mpm_server_options* opt, mpm_server** out);
+/* Stop the server and free everything it holds, outstanding results included.
+ * Passage: none in the paper (systems call). */
 void mpm_server_destroy(mpm_server* srv);
 /* Copies the request's host arrays; returns at once with a ticket.  BUDGET if the
- * request alone can never fit the budget. */
+ * request alone can never fit the budget.
+ * Passage: none in the paper (systems call); the request is one rollout of Alg. 1's
+ *   env.step over its horizon, with Sec. 4.1's reverse pass when want_grad is set. */
 mpm_status mpm_submit(mpm_server* srv, const mpm_request* req, uint64_t* ticket);
-/* Non-blocking: NOT_READY, or OK with *out filled. */
+/* Non-blocking: NOT_READY, or OK with *out filled.
+ * Passage: none in the paper (systems call). */
 mpm_status mpm_poll(mpm_server* srv, uint64_t ticket, mpm_result* out);
-/* Block until the ticket finishes or timeout_ms passes (TIMEOUT). */
+/* Block until the ticket finishes or timeout_ms passes (TIMEOUT).
+ * Passage: none in the paper (systems call). */
 mpm_status mpm_wait(mpm_server* srv, uint64_t ticket, double timeout_ms, mpm_result* out);
+/* Free a finished ticket's result buffers.  Passage: none in the paper (systems call). */
 mpm_status mpm_release(mpm_server* srv, uint64_t ticket);
+/* Text of the server's last failure.  Passage: none in the paper (systems call). */
 const char* mpm_server_last_error(const mpm_server* srv);
 
 #ifdef __cplusplus

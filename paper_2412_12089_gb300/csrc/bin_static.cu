@@ -4,7 +4,9 @@
 // The scratch holds two key and two value buffers of the LSD radix sort plus its per-CTA
 // digit histogram, for at most kBinStaticMax particles (4 MiB + 64 KiB).  Its device address
 // is taken with cudaGetSymbolAddress once per device, on the first call made with that device
-// current; that first call should come before any stream capture.  Every call shares the one
+// current, and kept for the process; that first call should come before any stream capture.
+// A cudaDeviceReset unloads the module and leaves the kept address stale, so the entry point
+// is not for a device that has been reset.  Every call shares the one
 // array and finds the previous call's contents in it: nothing there is read before this call
 // writes it (each sort pass overwrites every histogram entry it later reads, and only the
 // first n keys and values are touched), so no part of it needs clearing.  Calls whose work
@@ -61,6 +63,9 @@ mpm_status mpm_bin_static(const float* x, int32_t n, int32_t grid_res, uint32_t*
   if (n > kBinStaticMax) return MPM_ERR_INVALID_ARG;  // beyond the fixed scratch
   if (n == 0) return MPM_OK;
   if (mpm::radix_hist_entries(n) > kHistEntries) return MPM_ERR_INVALID_ARG;  // scratch layout check
+  // An error already pending on this thread belongs to an earlier call of the caller's: leave
+  // it in place and launch nothing, so that every error reported below is this call's own.
+  if (cudaPeekAtLastError() != cudaSuccess) return MPM_ERR_CUDA;
   unsigned* base = nullptr;
   if (scratch_for_current_device(&base) != cudaSuccess) return MPM_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
@@ -70,6 +75,7 @@ mpm_status mpm_bin_static(const float* x, int32_t n, int32_t grid_res, uint32_t*
   unsigned* v2 = base + 3 * (size_t)kBinStaticMax;
   unsigned* hist = base + 4 * (size_t)kBinStaticMax;
   mpm::launch_bin_keys_plain(x, n, grid_res, k1, v1, st);
+  if (cudaPeekAtLastError() != cudaSuccess) return (void)cudaGetLastError(), MPM_ERR_CUDA;
   if (cudaMemcpyAsync(keys, k1, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return MPM_ERR_CUDA;
   int bits = 0;
   for (unsigned long long v = (unsigned long long)(grid_res / 4) * (grid_res / 4) * (grid_res / 4) * 64ull - 1ull; v;
@@ -78,9 +84,10 @@ mpm_status mpm_bin_static(const float* x, int32_t n, int32_t grid_res, uint32_t*
   unsigned* kk[2] = {k1, k2};
   unsigned* vv[2] = {v1, v2};
   const int cur = mpm::radix_sort(kk, vv, n, bits, hist, st);
+  if (cudaPeekAtLastError() != cudaSuccess) return (void)cudaGetLastError(), MPM_ERR_CUDA;
   if (cudaMemcpyAsync(perm, vv[cur], sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return MPM_ERR_CUDA;
-  return cudaGetLastError() == cudaSuccess ? MPM_OK : MPM_ERR_CUDA;
+  return MPM_OK;
 }
 
 }  // extern "C"

@@ -33,6 +33,55 @@ def test_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def comment_blocks():
+    """Each declared entry point with the comment block that documents it: the comment that
+    ends nearest above its declaration, with only other declarations between them (a group of
+    declarations shares one block)."""
+    src = open(HEADER).read()
+    out = {}
+    last_comment, last_end = "", -1
+    pos = 0
+    for m in re.finditer(r"/\*.*?\*/|\b(mpm_[a-z_0-9]+)\s*\(", src, flags=re.S):
+        if m.group(0).startswith("/*"):
+            gap = src[last_end:m.start()] if last_end >= 0 else ""
+            last_comment, last_end = m.group(0), m.end()
+            continue
+        name = m.group(1)
+        # the text between the block and this declaration holds only declarations
+        between = src[last_end:m.start()]
+        if "#define" in between or "typedef" in between or "enum" in between:
+            out.setdefault(name, "")
+        else:
+            out.setdefault(name, last_comment)
+    return out
+
+
+# The entry points the hot-path boundary names: the batch context, the transition, the
+# reverse pass and the request calls.
+BOUNDARY = ["mpm_create", "mpm_destroy", "mpm_set_state", "mpm_get_state", "mpm_step", "mpm_backward",
+            "mpm_submit", "mpm_poll", "mpm_last_error"]
+
+
+def test_every_declaration_cites_its_passage():
+    """Every entry point's comment block names the paper passage that defines its operation
+    (Sec., App., Alg.), or says that the paper has none (systems calls)."""
+    blocks = comment_blocks()
+    for name in BOUNDARY:
+        assert name in blocks, name
+    bad = []
+    for name, block in blocks.items():
+        m = re.search(r"Passage:(.*?)(\*/|\n \*\s*\n|$)", block, flags=re.S)
+        if not m:
+            bad.append((name, "no Passage line"))
+            continue
+        text = m.group(1)
+        if not (re.search(r"\b(Sec|App|Alg|Eq)\. ?[0-9A-Z]", text) or "none" in text):
+            bad.append((name, text.strip()[:60]))
+    assert not bad, bad
+    for name in ("mpm_step", "mpm_backward", "mpm_create", "mpm_set_state", "mpm_get_state"):
+        assert re.search(r"Passage:.*?\b(Sec|App|Alg)\.", blocks[name], flags=re.S), name
+
+
 def test_struct_layouts(tmp_path):
     from paper_2412_12089_gb300 import mpm
 

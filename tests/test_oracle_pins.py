@@ -198,6 +198,29 @@ def test_muscle_fibre_stress():
     assert np.allclose(orc.tau(sp, F, a_g=0.7) - orc.tau(nh, F), 0.7 * sp.act_stress * np.outer(f, f), atol=1e-8)
 
 
+def test_fluid_viscosity_rigid_rotation_and_dissipation():
+    """The viscous part of the fluid stress is Newtonian: a rigid rotation (antisymmetric
+    velocity gradient C) produces no viscous stress, and in any flow the viscous stress does
+    non-negative work on the velocity gradient (tau_visc : C >= 0), equal to 2 visc J |sym C|^2.
+    Checked on the stress the oracle returns with the bulk part taken out at the same J."""
+    sp = spec_for("fluid")
+    for J in (0.95, 1.0, 1.03):
+        F = np.cbrt(J) * np.eye(3)
+        base = orc.tau(sp, F, np.zeros((3, 3)))
+        for _ in range(5):
+            W = RNG.standard_normal((3, 3))
+            W = W - W.T  # antisymmetric: a rigid rotation rate
+            assert np.abs(orc.tau(sp, F, W) - base).max() < 1e-12 * max(1.0, np.abs(base).max())
+            C = RNG.standard_normal((3, 3))
+            tv = orc.tau(sp, F, C) - base
+            work = float(np.sum(tv * C))
+            assert work >= 0.0
+            S = 0.5 * (C + C.T)
+            assert abs(work - 2.0 * sp.visc * J * float(np.sum(S * S))) <= 1e-12 * max(1.0, abs(work))
+            # a pure shear rate of the same magnitude but opposite sense dissipates equally
+            assert abs(float(np.sum((orc.tau(sp, F, -C) - base) * -C)) - work) <= 1e-12 * max(1.0, work)
+
+
 def test_fluid_closed_form():
     """App. D.3 fluid: P = K J (J-1) F^-T gives tau = K J (J-1) I; viscosity adds
     visc J (C + C^T)."""
@@ -615,8 +638,14 @@ def test_binning_keys_and_stable_sort():
     TG = G // 4
     b = np.stack([(tile % TG) * 4 + cell % 4, ((tile // TG) % TG) * 4 + (cell // 4) % 4,
                   (tile // (TG * TG)) * 4 + cell // 16], -1)
-    X = x.astype(np.float64) * G
-    assert np.all(b + 0.5 <= X + 1e-6) and np.all(X < b + 1.5 + 1e-6)
+    # the same cell base from numpy float32 arithmetic, one rounding per operation (numpy
+    # never fuses a multiply and a subtract), compared with no slack
+    Xf = np.multiply(x, np.float32(G), dtype=np.float32)
+    exp = np.clip(np.floor(np.subtract(Xf, np.float32(0.5), dtype=np.float32)).astype(np.int64), 0, G - 3)
+    assert np.array_equal(b, exp)
+    # and the particle lies in its cell's half-open support interval [b + 0.5, b + 1.5) in the
+    # FP32 coordinate the key was made from
+    assert np.all(b + 0.5 <= Xf) and np.all(Xf < b + 1.5)
     perm = orc.stable_sort(keys)
     assert np.array_equal(np.sort(perm), np.arange(5000))
     assert np.array_equal(perm, np.argsort(keys, kind="stable"))
