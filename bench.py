@@ -349,6 +349,53 @@ def fem_leg(n_envs, T, device, reps=3):
     return out
 
 
+def jumper_leg(n_envs, n, T, device, reps=2):
+    """Differentiation at scale: the MPM soft jumper (muscle legs with per-group actuation, a
+    passive torso, ground friction; 96^3 grids) recorded over T control steps x 20 substeps
+    with a checkpoint per control step, then the whole horizon reversed.  Reports fwd+adjoint
+    particle-substeps/s, the rollout time and the device memory the batch holds."""
+    import numpy as np
+    import torch
+
+    from paper_2412_12089_gb300 import mpm
+    from paper_2412_12089_gb300 import workloads as wl
+    from paper_2412_12089_gb300.batch import Batch
+
+    dev = torch.device("cuda", device)
+    w = wl.jumper(n_envs=n_envs, n=n, seed=0, T=T)
+    S = w.specs[0].substeps
+    b = Batch(w.specs, max_steps=T, device=device)
+    try:
+        acts = torch.as_tensor(w.actions).to(dev)
+        rbar = torch.ones(T, n_envs, device=dev)
+        agrad = torch.empty(T, n_envs, b.A, device=dev)
+        rew = torch.empty(T, n_envs, device=dev)
+        times = []
+        for rep in range(reps + 1):
+            b.set_inits(w.inits)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for t in range(T):
+                mpm.mpm_step(b.ctx, acts[t], rew[t], mpm.MPM_STEP_RECORD)
+            mpm.mpm_backward(b.ctx, reward_adj=rbar, action_grad=agrad)
+            e1.record()
+            torch.cuda.synchronize()
+            if rep > 0:  # the first rollout warms up (graph capture, grid tape)
+                times.append(e0.elapsed_time(e1) / 1e3)
+        code, flags = b.check_status()
+        sec = min(times)
+        out = {"workload": f"jumper-{n_envs}env-{n}p-96grid-{T}x{S}-fwd+adjoint, checkpoint per control step",
+               "envs": n_envs, "particles_per_env": n, "control_steps": T, "substeps": S,
+               "value": n_envs * n * T * S / sec, "unit": UNIT, "rollout_ms": 1e3 * sec,
+               "rollout_ms_all": [1e3 * t for t in times], "device_gb": mpm.mpm_device_bytes(b.ctx) / 1e9,
+               "action_grad_finite": bool(torch.isfinite(agrad).all().item()),
+               "status_flags": int(np.count_nonzero(flags))}
+    finally:
+        b.close()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -401,6 +448,7 @@ def main():
                          "as `serving`, all of them under `serving.sweep`")
     ap.add_argument("--handflip-frames", type=int, default=30, help="timed frames of the HandFlip-like leg (0 = off)")
     ap.add_argument("--fem-envs", type=int, default=2048, help="envs of the SoftJumper FEM leg (0 = off)")
+    ap.add_argument("--jumper-envs", type=int, default=64, help="envs of the 100k-particle jumper leg (0 = off)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -578,6 +626,10 @@ def main():
     if args.fem_envs > 0 and rank == 0:
         fem_out = fem_leg(args.fem_envs, 16, local)
 
+    jumper = None
+    if args.jumper_envs > 0 and rank == 0:
+        jumper = jumper_leg(args.jumper_envs, 100_000, 64, local)
+
     cpu = None
     if not args.no_cpu and rank == 0:
         v1, dt1, sample1 = cpu_baseline(T)
@@ -601,6 +653,7 @@ def main():
             "serving": serve,
             "handflip": handflip,
             "fem": fem_out,
+            "jumper": jumper,
             "clocks": clk, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "status": int(code),
         }

@@ -367,6 +367,12 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
     const int v = std::atoi(b);
     if (v == kScatterBoxes[0] || v == kScatterBoxes[1]) box0 = v;
   }
+  // test-only: shorten G2P's first bounded wait so that it gives up (the status path)
+  g.wait_polls = -1;
+  if (const char* wp = std::getenv("MPM_TEST_G2P_WAIT_POLLS")) {
+    const int v = std::atoi(wp);
+    if (v >= 0) g.wait_polls = v;
+  }
   g.mats.clear();
   for (size_t i = 0; i < g.items.size(); ++i) {
     const int mat = specs[g.items[i].env].material;
@@ -460,6 +466,7 @@ Launch group_launch(const Group& g, cudaStream_t st) {
   L.env0 = 0;
   L.n_env = g.n_envs;
   L.stream = st;
+  L.wait_polls = g.wait_polls;
   return L;
 }
 

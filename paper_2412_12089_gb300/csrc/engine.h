@@ -61,6 +61,7 @@ struct Group {
   long long P = 0, tiles = 0;
   std::vector<WorkItem> items, items_env;
   std::vector<MatGroup> mats;
+  int wait_polls = -1;     // G2P's first bounded wait (test-only MPM_TEST_G2P_WAIT_POLLS; < 0: full)
   std::vector<int> env_item0, env_nitems;
   // FEM environments (their step kernels run one CTA per environment) and their extents
   std::vector<int> fem_envs;

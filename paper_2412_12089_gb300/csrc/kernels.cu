@@ -62,9 +62,9 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
                ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
-// Waits for the barrier's phase `parity` to complete; false after kWaitLimit polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (int it = 0; it < kWaitLimit; ++it) {
+// Waits for the barrier's phase `parity` to complete; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int limit = kWaitLimit) {
+  for (int it = 0; it < limit; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -782,8 +782,11 @@ __global__ void __launch_bounds__(256) k_restore(const EnvDesc* __restrict__ env
 // ------------------------------------------------------------------ G2P
 
 template <int MAT>
+// wait_polls: polls of the first wait on the staged copies (< 0: kWaitLimit); a test sets it
+// to 0 to make that wait give up and exercise the status path.
 __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
-                                                int item_off, StateRef src, StateRef dst, int use_perm, int rev) {
+                                                int item_off, StateRef src, StateRef dst, int use_perm, int rev,
+                                                int wait_polls) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   // x and H of the chunk's particles, staged by bulk copies when they are read in place
@@ -807,7 +810,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
     }
     // every thread polls on its own; the CTA leaves together if any of them gave up, thread 0
     // last, after a second bounded wait for the copies (its shared memory lives until then)
-    if (!__syncthreads_and(mbar_wait(&bar, 0) ? 1 : 0)) {
+    if (!__syncthreads_and(mbar_wait(&bar, 0, wait_polls < 0 ? kWaitLimit : wait_polls) ? 1 : 0)) {
       if (threadIdx.x == 0) {
         atomicOr(&e.ctr->status, kStatusWait);
         (void)mbar_wait(&bar, 0);
@@ -2000,10 +2003,10 @@ void launch_g2p(const Launch& L, StateRef src, StateRef dst, bool use_perm, int 
   Timed tm_(KC_G2P, L.stream);
   const int rev = (dst.kind == REF_RING) ? 1 : 0;
   switch (L.material) {
-    case MAT_NEOHOOKEAN: k_g2p<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev); break;
-    case MAT_VONMISES: k_g2p<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev); break;
-    case MAT_FLUID: k_g2p<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev); break;
-    default: k_g2p<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev); break;
+    case MAT_NEOHOOKEAN: k_g2p<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls); break;
+    case MAT_VONMISES: k_g2p<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls); break;
+    case MAT_FLUID: k_g2p<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls); break;
+    default: k_g2p<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls); break;
   }
 }
 

@@ -37,6 +37,7 @@ struct Launch {
   int env0, n_env;       // environment range of the per-env kernels
   cudaStream_t stream;
   int sc_box = 512;      // shared-box capacity (nodes) of the scatter kernels: 512 or 1024
+  int wait_polls = -1;   // polls of G2P's first wait on its staged copies (< 0: the full limit)
 };
 
 constexpr int kScatterBoxes[2] = {512, 1024};  // capacities the scatter kernels are built for

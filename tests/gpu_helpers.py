@@ -63,3 +63,63 @@ def oracle_run(w: wl.Workload, e: int, T: int):
     acts = w.actions[:T, e, :max(A, 1)].astype(np.float64)
     out, q, rew, status = orc.rollout(sp, st, orc.initial_pose(s), acts)
     return out, q, rew
+
+
+def oracle_pool(n_jobs):
+    """A process pool for oracle runs, started with spawn (safe after CUDA is initialised)."""
+    import multiprocessing as mp
+    import os
+
+    return mp.get_context("spawn").Pool(max(1, min(n_jobs, len(os.sched_getaffinity(0)))))
+
+
+def oracle_trajectory(job):
+    """Pool worker: the oracle's state after each of T control steps of env e of a workload
+    (rebuilt from its maker and keyword arguments).  Returns (e, [(x, v, C, F)] * T, rewards)."""
+    maker, kw, e, T = job
+    w = getattr(wl, maker)(**kw)
+    s = w.specs[e]
+    sp = orc.make_spec(s)
+    st = orc.State.from_init(w.inits[e])
+    acts = w.actions[:T, e, :max(s.action_dim, 1)].astype(np.float64)
+    q = orc.initial_pose(s)
+    traj, rews = [], []
+    for t in range(T):
+        st, q, r, _ = orc.rollout(sp, st, q, acts[t:t + 1])
+        traj.append((st.x.copy(), st.v.copy(), st.C.copy(), st.F.copy()))
+        rews.append(r[0])
+    return e, traj, np.array(rews)
+
+
+def final_adjoint(w, e):
+    """A seeded adjoint of the final positions (the loss sum_p xbar_p . x_p), env e."""
+    return np.random.default_rng(100 + e).standard_normal((w.specs[e].n_particles, 3))
+
+
+def oracle_gradients(job):
+    """Pool worker: the oracle's gradients of sum_t r_t + sum_p xbar_p . x_p(T) for env e:
+    (e, action gradient (T, A), (xb0, vb0, Cb0, Fb0))."""
+    maker, kw, e, T = job
+    w = getattr(wl, maker)(**kw)
+    s = w.specs[e]
+    sp = orc.make_spec(s)
+    st = orc.State.from_init(w.inits[e])
+    acts = w.actions[:T, e, :max(s.action_dim, 1)].astype(np.float64)
+    ag, sb, _ = orc.rollout_adj(sp, st, orc.initial_pose(s), acts, adj_final=(final_adjoint(w, e), None, None, None),
+                                rbar=np.ones(T))
+    return e, ag, sb
+
+
+def oracle_return(job):
+    """Pool worker: the oracle's total reward sum_t r_t of env e over T control steps, with
+    action entry (t, j) shifted by h (t < 0: no shift).  For central differences."""
+    maker, kw, e, T, t, j, h = job
+    w = getattr(wl, maker)(**kw)
+    s = w.specs[e]
+    sp = orc.make_spec(s)
+    st = orc.State.from_init(w.inits[e])
+    acts = w.actions[:T, e, :max(s.action_dim, 1)].astype(np.float64)
+    if t >= 0:
+        acts[t, j] += h
+    _, _, rew, status = orc.rollout(sp, st, orc.initial_pose(s), acts)
+    return float(rew.sum()), int(status)

@@ -194,6 +194,39 @@ def test_domain_status_flag():
     assert code == 5 and flags[0] & 1
 
 
+def test_bounded_wait_gives_up_with_status(monkeypatch):
+    """G2P waits on its staged bulk copies with a bounded number of polls.  The test-only
+    MPM_TEST_G2P_WAIT_POLLS=0 makes that first wait give up at once (the copies themselves are
+    ordinary and complete; the CTA's thread 0 waits for them, again bounded, before the CTA
+    returns), so every staged chunk sets MPM_FLAG_WAIT and skips its work, and the host reads
+    MPM_ERR_TIMEOUT.  A context created without the option then runs oracle-correct."""
+    import torch
+
+    from paper_2412_12089_gb300.batch import Batch
+
+    # two substeps: G2P of substep 0 reads through the binning permutation (no staging); the
+    # staged G2P of substep 1 is the step's last particle kernel, so the skipped chunks' state
+    # is read only by the reward and get_state
+    w = small("fluid", seed=9, substeps=2, T=1, n_envs=2, n=1500)
+    monkeypatch.setenv("MPM_TEST_G2P_WAIT_POLLS", "0")
+    b = Batch(w.specs, max_steps=0)
+    monkeypatch.delenv("MPM_TEST_G2P_WAIT_POLLS")
+    b.set_inits(w.inits)
+    b.step(torch.as_tensor(w.actions[0]).cuda())
+    code, flags = b.check_status()
+    b.close()
+    assert code == 6, code  # MPM_ERR_TIMEOUT
+    assert all(f & 0x8 for f in flags), flags  # MPM_FLAG_WAIT in every env
+    b2, rew, st = gpu_run(w, 1)
+    code2, flags2 = b2.check_status()
+    assert code2 == 0 and not flags2.any()
+    for e in range(w.n_envs):
+        o, q, r = oracle_run(w, e, 1)
+        for k in ("x", "v", "F"):
+            assert rel_err(split(w, st[k])[e], getattr(o, k)) < 1e-4, (e, k)
+    b2.close()
+
+
 # ------------------------------------------------------------------ gradients
 
 def _gpu_grads(w, T, xbT=None, rbar=None, S=None):
