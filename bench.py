@@ -31,15 +31,21 @@ METRIC = "fwd+adjoint particle-substeps/s (batched)"
 UNIT = "particle-substeps/s"
 
 # Algorithmic bytes of each kernel class: (bytes per particle per launch, bytes per active
-# grid node per launch).  FP32 SoA state x(3) v(3) C(9) H(9) = 96 B per particle.
+# grid node per launch).  FP32 SoA state x(3) v(3) C(9) H(9) = 96 B per particle.  Per node,
+# the method's bytes: P2G writes (m, p) 16 B; the grid update reads (m, p) and writes v, 28 B;
+# G2P reads v, 12 B; the grid adjoint reads v-bar and (m, p) and writes (m-bar, p-bar), 56 B.
 ALGO_BYTES = {
     "p2g": (96, 16),       # read x, v, C, H; write (m, p) once per node
-    "g2p": (144, 16),      # read x, H; write x, v, C, H; read grid v once per node
-    "g2p_adj": (228, 32),  # read x, H, C' + adjoint 96 B, write partial x-bar, H-bar; grid v in, v-bar out
+    "g2p": (144, 12),      # read x, H; write x, v, C, H; read grid v once per node
+    "g2p_adj": (228, 24),  # read x, H, C' + adjoint 96 B, write partial x-bar, H-bar; grid v in, v-bar out
     "p2g_adj": (240, 16),  # read state 96 + partial 48, write adjoint 96; grid (m-bar, p-bar) in
-    "grid": (0, 48),       # read (m, p), write v, clear (m, p)
-    "grid_adj": (0, 80),   # read (m, p), v-bar; write (m-bar, p-bar); clear (m, p), v-bar
+    "grid": (0, 28),       # read (m, p), write v
+    "grid_adj": (0, 56),   # read (m, p), v-bar; write (m-bar, p-bar)
 }
+# The method's bytes per particle-substep of a forward + adjoint rollout (particle state read
+# and written once forward; recompute forward + the substep-start store; adjoint pass reload,
+# adjoint read and write), without grid terms: 192 + 288 + 288.
+STEP_BYTES_PER_PARTICLE_SUBSTEP = 768
 
 # dram__bytes_read.sum + dram__bytes_write.sum per particle of one launch, from the ncu
 # capture (kernel source hash at capture time).  Reported only
@@ -396,6 +402,106 @@ def jumper_leg(n_envs, n, T, device, reps=2):
     return out
 
 
+def cube_leg(device, reps=20):
+    """The plain method on one environment: the neo-Hookean cube (4096 particles, 32^3, E=1e4,
+    nu=0.3), 50 substeps forward and the reverse pass of the loss sum |x_50 - x*|^2 (x* = x_0
+    + (0.05, 0, 0)) with respect to the initial state, replayed as captured graphs."""
+    import numpy as np
+    import torch
+
+    from paper_2412_12089_gb300 import mpm
+    from paper_2412_12089_gb300 import workloads as wl
+    from paper_2412_12089_gb300.batch import Batch
+
+    dev = torch.device("cuda", device)
+    w = wl.cube(seed=0)
+    s = w.specs[0]
+    n, S = s.n_particles, s.substeps
+    b = Batch(w.specs, max_steps=1, device=device)
+    try:
+        xs = {k: torch.as_tensor(getattr(w.inits[0], k)).to(dev) for k in ("x", "v", "C", "F")}
+        target = xs["x"] + torch.tensor([0.05, 0.0, 0.0], device=dev)
+        xT = torch.empty(n, 3, device=dev)
+        xb = torch.empty(n, 3, device=dev)
+        outs = {k: torch.empty(n, 3, 3, device=dev) if k in ("Cb0", "Fb0") else torch.empty(n, 3, device=dev)
+                for k in ("xb0", "vb0", "Cb0", "Fb0")}
+        act = torch.zeros(1, max(b.A, 1), device=dev)
+        ag = torch.empty(1, 1, max(b.A, 1), device=dev)
+
+        def rollout():
+            mpm.mpm_set_state(b.ctx, xs["x"], xs["v"], xs["C"], xs["F"])
+            mpm.mpm_step(b.ctx, act, None, mpm.MPM_STEP_RECORD)
+            mpm.mpm_get_state(b.ctx, x=xT)
+            torch.mul(torch.sub(xT, target), 2.0, out=xb)
+            mpm.mpm_backward(b.ctx, xb=xb, action_grad=ag, xb0=outs["xb0"], vb0=outs["vb0"], Cb0=outs["Cb0"],
+                             Fb0=outs["Fb0"])
+
+        for _ in range(3):
+            rollout()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            rollout()
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        code, flags = b.check_status()
+        return {"workload": f"cube-1env-{n}p-32grid-{S}substeps-fwd+adjoint (loss sum |x_S - x*|^2)",
+                "value": n * S / sec, "unit": UNIT, "rollout_ms": 1e3 * sec, "reps": reps,
+                "status_flags": int(np.count_nonzero(flags))}
+    finally:
+        b.close()
+
+
+def dough_leg(device, reps=3, n_envs=512, T=32):
+    """Batching: 512 von Mises dough environments (2k-16k particles each, log-uniform), 48^3
+    grids, a kinematic capsule roller driven by seeded actions, 32 control steps x 20
+    substeps, forward only, replayed as captured graphs."""
+    import numpy as np
+    import torch
+
+    from paper_2412_12089_gb300 import mpm
+    from paper_2412_12089_gb300 import workloads as wl
+    from paper_2412_12089_gb300.batch import Batch
+
+    dev = torch.device("cuda", device)
+    w = wl.dough(n_envs=n_envs, seed=0, T=T)
+    S, P = w.specs[0].substeps, w.n_particles
+    b = Batch(w.specs, max_steps=0, device=device)
+    try:
+        xs = {k: torch.as_tensor(np.concatenate([getattr(i, k) for i in w.inits])).to(dev) for k in ("x", "v", "C", "F")}
+        poses = torch.as_tensor(np.array([s.pose0 for s in w.specs], np.float32)).to(dev)
+        acts = torch.as_tensor(w.actions).to(dev)
+        rew = torch.empty(T, n_envs, device=dev)
+
+        def rollout():
+            mpm.mpm_set_state(b.ctx, xs["x"], xs["v"], xs["C"], xs["F"], pose=poses)
+            for t in range(T):
+                mpm.mpm_step(b.ctx, acts[t], rew[t], 0)
+
+        rollout()
+        mpm.mpm_autotune(b.ctx, trials=3)
+        rollout()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rollout()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        code, flags = b.check_status()
+        sec = min(times)
+        return {"workload": f"dough-{n_envs}env-2k..16k-48grid-{T}x{S}-forward", "particles": P,
+                "value": P * T * S / sec, "unit": "particle-substeps/s (forward)", "rollout_ms": 1e3 * sec,
+                "rollout_ms_all": [1e3 * t for t in times], "device_gb": mpm.mpm_device_bytes(b.ctx) / 1e9,
+                "status_flags": int(np.count_nonzero(flags))}
+    finally:
+        b.close()
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -449,6 +555,8 @@ def main():
     ap.add_argument("--handflip-frames", type=int, default=30, help="timed frames of the HandFlip-like leg (0 = off)")
     ap.add_argument("--fem-envs", type=int, default=2048, help="envs of the SoftJumper FEM leg (0 = off)")
     ap.add_argument("--jumper-envs", type=int, default=64, help="envs of the 100k-particle jumper leg (0 = off)")
+    ap.add_argument("--no-direct", action="store_true", help="skip the direct-launch (no graphs) timing")
+    ap.add_argument("--no-legs", action="store_true", help="skip the cube (C1) and dough (C2) legs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -477,7 +585,7 @@ def main():
     # ---- workload: env shard of this rank (weak scaling: every rank runs a full batch)
     w = wl.fluid(n_envs=args.envs, n=args.particles, seed=1000 * rank, T=args.control_steps, substeps=args.substeps)
     T, S, P = w.T, w.specs[0].substeps, w.n_particles
-    b = Batch(w.specs, max_steps=T, use_graphs=False, device=local)
+    b = Batch(w.specs, max_steps=T, use_graphs=True, device=local)
     xs = {k: torch.as_tensor(np.concatenate([getattr(i, k) for i in w.inits])).to(dev) for k in ("x", "v", "C", "F")}
     poses = torch.as_tensor(np.array([s.pose0 for s in w.specs], np.float32)).to(dev)
     acts = torch.as_tensor(w.actions).to(dev)
@@ -499,20 +607,16 @@ def main():
 
     tuned = None
     for i in range(args.warmup):
-        if i == args.warmup - 1:
-            mpm.mpm_time_kernel(b.ctx, "all")  # per-class timing: which kernel class dominates
         one_step()
         if i == 0:
-            # autotune the scatter kernels' shared-box capacity on a binned state
+            # autotune the scatter kernels' shared-box capacity on a binned state (the captured
+            # graphs are dropped and captured again with the choice)
             chosen, p2g_ms = mpm.mpm_autotune(b.ctx, trials=3)
-            tuned = {"scatter_box_nodes": chosen, "p2g_trial_ms_512_1024": p2g_ms}
+            tuned = {"scatter_box_nodes": chosen, "p2g_trial_ms_512_1024": p2g_ms, **mpm.mpm_autotune_config(b.ctx)}
     torch.cuda.synchronize()
-    tot, cnt = mpm.mpm_kernel_time(b.ctx, all_classes=True)
-    dominant = max((k for k in ALGO_BYTES), key=lambda k: tot[k])
-    mpm.mpm_time_kernel(b.ctx, dominant)
     tiles = max(mpm.mpm_last_active_tiles(b.ctx), 0)
 
-    # ---- timed region
+    # ---- timed region: the rollouts replay captured CUDA graphs, no per-launch events
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -530,12 +634,24 @@ def main():
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     launches = mpm.mpm_kernel_launches(b.ctx) - launches0
-    dom_ms, dom_n = mpm.mpm_kernel_time(b.ctx)
-    mpm.mpm_time_kernel(b.ctx, 0)
     step_ms = sorted(step_ev[k].elapsed_time(step_ev[k + 1]) for k in range(args.steps))
     ms = max_over_ranks(ms, device=dev)  # the job ends when the slowest rank does
     code, flags = b.check_status()
     value = sum_over_ranks(P * T * S * args.steps, device=dev) / (ms / 1e3)
+
+    # ---- kernel timing: a second timed region of direct launches with CUDA events recorded
+    # on the launching stream around every launch of every class; it gives each class's mean
+    # launch duration, the dominant class and the roofline figures
+    k_steps = max(1, min(args.steps, 3))
+    mpm.mpm_time_kernel(b.ctx, "all")
+    barrier()
+    for _ in range(k_steps):
+        one_step()
+    barrier()
+    tot, cnt = mpm.mpm_kernel_time(b.ctx, all_classes=True)
+    mpm.mpm_time_kernel(b.ctx, 0)
+    dominant = max((k for k in ALGO_BYTES), key=lambda k: tot[k])
+    dom_ms, dom_n = tot[dominant], cnt[dominant]
 
     # ---- roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
@@ -546,13 +662,17 @@ def main():
     achieved = algo / avg_s / 1e9 if dom_n else None
     mt = MEASURED_TRAFFIC.get(dominant)
     traffic = mt[0] * P if (mt and mt[1] == kernel_source_hash()) else None
+    step_gbs = STEP_BYTES_PER_PARTICLE_SUBSTEP * (value / max(world, 1)) / 1e9
     roofline = {"bound": "hbm", "kernel": f"k_{dominant}", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "algorithmic_bytes_per_launch": algo, "avg_launch_ms": avg_s * 1e3, "launches": dom_n,
                 "peak_source": f"{peak_kind} hbm_gbs",
-                "class_share": {k: round(v / max(sum(tot.values()), 1e-9), 4) for k, v in tot.items() if v > 0}}
-    # every kernel class against the same peak, from the last warm-up rollout (all classes
-    # timed there with CUDA events on the launching stream)
+                "timing": f"{k_steps} rollout(s) of direct launches, CUDA events around every launch",
+                "class_share": {k: round(v / max(sum(tot.values()), 1e-9), 4) for k, v in tot.items() if v > 0},
+                "whole_step": {"bytes_per_particle_substep": STEP_BYTES_PER_PARTICLE_SUBSTEP, "achieved": step_gbs,
+                               "frac": step_gbs / peak,
+                               "what": "the method's 768 B per fwd+adjoint particle-substep at the graph-timed rate"}}
+    # every kernel class against the same peak, from the same kernel-timing region
     per_class = {}
     for k, (pp, pn) in ALGO_BYTES.items():
         if cnt.get(k):
@@ -560,7 +680,7 @@ def main():
             t_avg = tot[k] / cnt[k] / 1e3
             per_class[k] = {"achieved": a / t_avg / 1e9, "frac": a / t_avg / 1e9 / peak, "avg_launch_ms": t_avg * 1e3,
                             "launches": int(cnt[k]), "algorithmic_bytes_per_launch": a}
-    roofline["per_class_warmup"] = per_class
+    roofline["per_class"] = per_class
 
     # ---- per-environment-launch path on a sample of the same workload (one control step)
     per_env = None
@@ -614,6 +734,33 @@ def main():
         e2e = {"value": sum_over_ranks(P * T * S * reps, device=dev) / wall, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "reps": reps}
 
+    b.close()
+
+    # ---- the same rollouts with direct launches (no graphs, no events), a second number
+    direct = None
+    if not args.no_direct:
+        bd = Batch(w.specs, max_steps=T, use_graphs=False, device=local)
+        b = bd
+        one_step()
+        mpm.mpm_autotune(bd.ctx, trials=3)
+        one_step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            one_step()
+        e1.record(stream)
+        barrier()
+        dms = max_over_ranks(e0.elapsed_time(e1), device=dev)
+        direct = {"value": sum_over_ranks(P * T * S * args.steps, device=dev) / (dms / 1e3), "unit": UNIT,
+                  "ms_per_step": dms / args.steps, "launch": "direct, no per-launch events"}
+        bd.close()
+
+    legs = {}
+    if rank == 0 and not args.no_legs:
+        legs["cube_c1"] = cube_leg(local)
+        legs["dough_c2"] = dough_leg(local)
+
     serve = None
     if args.serve_requests > 0 and rank == 0:
         serve = serving_leg(args.serve_requests, [float(r) for r in args.serve_rate.split(",")], seed=11)
@@ -647,7 +794,10 @@ def main():
                        "envs_per_gpu": args.envs, "particles_per_env": args.particles, "grid": 64,
                        "control_steps": T, "substeps": S, "parallelism": f"env-shard x{world}",
                        "l2": "inputs larger than L2 (state and grids > 129 MB per pass)",
-                       "launch": "direct (per-class CUDA-event timing on)", "autotuned": tuned},
+                       "launch": "captured CUDA graphs replayed per control step and per reverse step",
+                       "autotuned": tuned},
+            "direct_launch": direct,
+            "legs": legs,
             "rollout_ms": {"p50": step_ms[len(step_ms) // 2], "p99": step_ms[-1], "what": "one batched fwd+adjoint rollout"},
             "per_env_launch": per_env,
             "serving": serve,

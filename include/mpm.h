@@ -352,6 +352,22 @@ mpm_status mpm_set_obs_adjoint(mpm_ctx* ctx, const float* obs_adj, void* stream)
  * Passage: none in the paper (launch-shape tuning of this library).
  */
 mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* ms_out);
+/*
+ * The rest of what mpm_autotune chose, after the scatter box and with the same trials (each
+ * trial writes only the grids and, for G2P, the first block of the checkpoint tape's substep
+ * ring, which is scratch between reverse passes; without a tape G2P keeps the default):
+ *   grid_blocks: CTAs of the persistent grid-update and grid-adjoint kernels, the fastest
+ *     grid update of 304, 608, 1216 and 2432 CTAs (2, 4, 8, 16 per SM); grid_ms: [4] their
+ *     mean times (ms);
+ *   g2p_stage: [4] by material, 1 if G2P stages each chunk's x and H in shared memory by
+ *     bulk copies, 0 if it loads them directly (-1 for absent materials); g2p_ms: [4][2]
+ *     mean G2P time (ms) without and with the staging.
+ * Before any mpm_autotune: the defaults (1216 CTAs, staging on) and zero times.  Any output
+ * may be NULL.
+ * Passage: none in the paper (launch-shape tuning of this library).
+ */
+mpm_status mpm_autotune_config(const mpm_ctx* ctx, int32_t* grid_blocks, float* grid_ms, int32_t* g2p_stage,
+                               float* g2p_ms);
 
 /* ------------------------------------------------------------------ instrumentation */
 

@@ -462,7 +462,7 @@ Launch group_launch(const Group& g, cudaStream_t st) {
   L.item_offset = 0;
   L.active = g.active;
   L.active_n = g.active_n;
-  L.grid_blocks = 152 * 8;
+  L.grid_blocks = g.grid_blocks;
   L.env0 = 0;
   L.n_env = g.n_envs;
   L.stream = st;
@@ -489,6 +489,7 @@ Launch mat_launch(const Launch& L, const MatGroup& m, int k) {
   Launch Lm = L;
   Lm.material = m.material;
   Lm.sc_box = m.sc_box;
+  Lm.g2p_stage = m.g2p_stage;
   Lm.item_offset = m.item0;
   Lm.n_items = m.n_gt[std::min(k, (int)m.n_gt.size() - 1)];
   return Lm;
@@ -564,7 +565,7 @@ void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, con
 
 }  // namespace
 
-cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, std::vector<std::vector<float>>* ms) {
+cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, TuneTimes* times) {
   if (g.n_envs == 0) return cudaSuccess;
   trials = std::max(trials, 1);
   Launch L = group_launch(g, st);
@@ -572,7 +573,17 @@ cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, std::vector<
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
-  if (ms) ms->assign(g.mats.size(), std::vector<float>());
+  if (times) {
+    times->p2g.assign(g.mats.size(), std::vector<float>());
+    times->g2p.assign(g.mats.size(), std::vector<float>());
+    times->grid.clear();
+  }
+  auto elapsed = [&](float* t_ms) {
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(t_ms, e0, e1);
+    return e;
+  };
+  // scatter box, per material: P2G of the live state, then the grid update clears the grid
   for (size_t mi = 0; mi < g.mats.size() && err == cudaSuccess; ++mi) {
     MatGroup& m = g.mats[mi];
     float best = 0.0f;
@@ -588,19 +599,83 @@ cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, std::vector<
         launch_p2g(Lm, StateRef{REF_LIVE, 0}, true, 0);
         cudaEventRecord(e1, st);
         launch_grid(L, 0, GRID_FWD, false);  // consumes and clears the grid and tile flags
-        err = cudaEventSynchronize(e1);
         float t_ms = 0.0f;
-        if (err == cudaSuccess) err = cudaEventElapsedTime(&t_ms, e0, e1);
+        err = elapsed(&t_ms);
         if (t > 0) sum += t_ms;
       }
       const float mean = sum / (float)trials;
-      if (ms) (*ms)[mi].push_back(mean);
+      if (times) times->p2g[mi].push_back(mean);
       if (bi == 0 || mean < best) {
         best = mean;
         best_box = box;
       }
     }
     if (err == cudaSuccess) m.sc_box = best_box;
+  }
+  // grid-update CTAs: P2G of every material, then the timed grid update with each choice
+  {
+    float best = 0.0f;
+    int best_blocks = g.grid_blocks;
+    for (int ci = 0; ci < 4 && err == cudaSuccess; ++ci) {
+      float sum = 0.0f;
+      for (int t = 0; t <= trials && err == cudaSuccess; ++t) {
+        cudaMemsetAsync(L.active_n, 0, sizeof(int), st);
+        for (auto& m : g.mats) launch_p2g(mat_launch(L, m, 0), StateRef{REF_LIVE, 0}, true, 0);
+        Launch Lg = L;
+        Lg.grid_blocks = kGridBlockChoices[ci];
+        cudaEventRecord(e0, st);
+        launch_grid(Lg, 0, GRID_FWD, false);
+        cudaEventRecord(e1, st);
+        float t_ms = 0.0f;
+        err = elapsed(&t_ms);
+        if (t > 0) sum += t_ms;
+      }
+      const float mean = sum / (float)trials;
+      if (times) times->grid.push_back(mean);
+      if (ci == 0 || mean < best) {
+        best = mean;
+        best_blocks = kGridBlockChoices[ci];
+      }
+    }
+    if (err == cudaSuccess) g.grid_blocks = best_blocks;
+    L.grid_blocks = g.grid_blocks;
+  }
+  // G2P staging, per material: one P2G + grid update gives grid velocities of the live
+  // state, then G2P reads the live state in place (binned order after any control step) and
+  // writes the first block of the substep ring (scratch between reverse passes), with and
+  // without the bulk-copy staging.  Only for contexts whose environments all keep a ring
+  // (a checkpoint tape) and run more than one substep; otherwise the default (staging) stays.
+  bool ring = true;
+  for (const auto& d : g.desc) ring = ring && d.ring != nullptr && d.S > 1;
+  if (err == cudaSuccess && ring) {
+    cudaMemsetAsync(L.active_n, 0, sizeof(int), st);
+    for (auto& m : g.mats) launch_p2g(mat_launch(L, m, 0), StateRef{REF_LIVE, 0}, true, 0);
+    launch_grid(L, 0, GRID_FWD, false);  // grid velocities of the active tiles; (m, p) cleared
+    for (size_t mi = 0; mi < g.mats.size() && err == cudaSuccess; ++mi) {
+      MatGroup& m = g.mats[mi];
+      float best = 0.0f;
+      int best_stage = m.g2p_stage;
+      for (int sg = 0; sg < 2 && err == cudaSuccess; ++sg) {
+        float sum = 0.0f;
+        for (int t = 0; t <= trials && err == cudaSuccess; ++t) {
+          Launch Lm = mat_launch(L, m, 1);
+          Lm.g2p_stage = sg;
+          cudaEventRecord(e0, st);
+          launch_g2p(Lm, StateRef{REF_LIVE, 0}, StateRef{REF_RING, 1}, false, 1);
+          cudaEventRecord(e1, st);
+          float t_ms = 0.0f;
+          err = elapsed(&t_ms);
+          if (t > 0) sum += t_ms;
+        }
+        const float mean = sum / (float)trials;
+        if (times) times->g2p[mi].push_back(mean);
+        if (sg == 0 || mean < best) {
+          best = mean;
+          best_stage = sg;
+        }
+      }
+      if (err == cudaSuccess) m.g2p_stage = best_stage;
+    }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

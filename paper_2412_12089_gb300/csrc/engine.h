@@ -52,6 +52,7 @@ struct MatGroup {
   int item0;               // first item of the material in the group's item list
   std::vector<int> n_gt;   // [k] = items of the material whose env runs more than k substeps
   int sc_box = 512;        // shared-box capacity of its scatter kernels (autotuned)
+  int g2p_stage = 1;       // G2P stages x and H by bulk copies (autotuned)
 };
 
 struct Group {
@@ -62,6 +63,7 @@ struct Group {
   std::vector<WorkItem> items, items_env;
   std::vector<MatGroup> mats;
   int wait_polls = -1;     // G2P's first bounded wait (test-only MPM_TEST_G2P_WAIT_POLLS; < 0: full)
+  int grid_blocks = 152 * 8;  // CTAs of the persistent grid kernels (autotuned)
   std::vector<int> env_item0, env_nitems;
   // FEM environments (their step kernels run one CTA per environment) and their extents
   std::vector<int> fem_envs;
@@ -100,11 +102,19 @@ Launch env_launch(const Group& g, int e, cudaStream_t st);
 // launch per stage per environment when per_env).
 void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in, int a_max, float* rew,
                      bool per_env);
-// Autotuner: time P2G of each material on the group's live state (binned first) with every
-// scatter-box capacity the kernels are built for, `trials` timed launches each after one
-// warm-up, and keep the fastest per material.  The grid is cleared after every trial, so
-// the state is unchanged.  ms[m][b]: mean time of material group m with capacity b.
-cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, std::vector<std::vector<float>>* ms);
+// Autotuner, on the group's live state (binned first), `trials` timed launches of each
+// choice after one warm-up, keeping the fastest:
+//   - per material, P2G with every scatter-box capacity the kernels are built for;
+//   - the persistent grid kernels' CTA count (kGridBlockChoices);
+//   - per material, G2P with and without the bulk-copy staging of x and H.
+// Every trial writes only the grids (cleared again) and the first ring block (G2P, contexts
+// with a tape only), so the state is unchanged.  ms[m][b]: mean P2G time of material group m with capacity b; grid_ms[c]: mean
+// grid-update time with CTA choice c; g2p_ms[m][s]: mean G2P time of material m, staging s.
+struct TuneTimes {
+  std::vector<std::vector<float>> p2g, g2p;
+  std::vector<float> grid;
+};
+cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, TuneTimes* t);
 // One reverse control step of every environment (step index from the device counters).
 // obs: adjoints of the task observations at the step boundaries, or NULL.
 void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env,

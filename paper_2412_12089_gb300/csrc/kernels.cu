@@ -783,10 +783,11 @@ __global__ void __launch_bounds__(256) k_restore(const EnvDesc* __restrict__ env
 
 template <int MAT>
 // wait_polls: polls of the first wait on the staged copies (< 0: kWaitLimit); a test sets it
-// to 0 to make that wait give up and exercise the status path.
+// to 0 to make that wait give up and exercise the status path.  use_stage: stage x and H by
+// bulk copies when the chunk is read in place (the autotuner's choice).
 __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items,
                                                 int item_off, StateRef src, StateRef dst, int use_perm, int rev,
-                                                int wait_polls) {
+                                                int wait_polls, int use_stage) {
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   // x and H of the chunk's particles, staged by bulk copies when they are read in place
@@ -800,7 +801,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
   const int sslot = step_slot(c, rev);
   const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
   const long long np = e.n_pad;
-  const bool staged = stageable(it, perm);
+  const bool staged = use_stage && stageable(it, perm);
   if (staged) {
     if (threadIdx.x == 0) {
       const int comps[12] = {0, 1, 2, 15, 16, 17, 18, 19, 20, 21, 22, 23};
@@ -2003,10 +2004,10 @@ void launch_g2p(const Launch& L, StateRef src, StateRef dst, bool use_perm, int 
   Timed tm_(KC_G2P, L.stream);
   const int rev = (dst.kind == REF_RING) ? 1 : 0;
   switch (L.material) {
-    case MAT_NEOHOOKEAN: k_g2p<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls); break;
-    case MAT_VONMISES: k_g2p<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls); break;
-    case MAT_FLUID: k_g2p<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls); break;
-    default: k_g2p<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls); break;
+    case MAT_NEOHOOKEAN: k_g2p<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls, L.g2p_stage); break;
+    case MAT_VONMISES: k_g2p<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls, L.g2p_stage); break;
+    case MAT_FLUID: k_g2p<MAT_FLUID><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls, L.g2p_stage); break;
+    default: k_g2p<MAT_MUSCLE><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls, L.g2p_stage); break;
   }
 }
 

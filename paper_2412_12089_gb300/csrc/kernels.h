@@ -38,7 +38,10 @@ struct Launch {
   cudaStream_t stream;
   int sc_box = 512;      // shared-box capacity (nodes) of the scatter kernels: 512 or 1024
   int wait_polls = -1;   // polls of G2P's first wait on its staged copies (< 0: the full limit)
+  int g2p_stage = 1;     // G2P stages a chunk's x and H by bulk copies (when read in place)
 };
+
+constexpr int kGridBlockChoices[4] = {152 * 2, 152 * 4, 152 * 8, 152 * 16};  // persistent grid CTAs
 
 constexpr int kScatterBoxes[2] = {512, 1024};  // capacities the scatter kernels are built for
 

@@ -37,6 +37,7 @@ struct mpm_ctx {
   bool use_graphs = false;
   std::vector<mpm_env_spec> specs;
   Group g;
+  TuneTimes tune;  // the last autotuning's trial times
   char* arena = nullptr;
   size_t arena_bytes = 0;
   float* act_in = nullptr;   // [n_envs][A_max]
@@ -661,12 +662,14 @@ mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* m
   if (!ctx || trials < 1 || trials > 1000) return MPM_ERR_INVALID_ARG;
   CK(cudaSetDevice(ctx->device));
   CK(cudaDeviceSynchronize());  // the state may still be in flight on the caller's stream
-  std::vector<std::vector<float>> ms;
+  TuneTimes tt;
   cudaError_t e;
   {
     Enqueue q(ctx);
-    e = autotune_scatter(ctx->g, ctx->cap_stream, trials, &ms);
+    e = autotune_scatter(ctx->g, ctx->cap_stream, trials, &tt);
   }
+  const auto& ms = tt.p2g;
+  ctx->tune = tt;
   if (e != cudaSuccess) return fail(ctx, MPM_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
   // captured graphs hold the old kernel choice: capture again on the next step
   for (auto& g : ctx->g_fwd)
@@ -689,6 +692,27 @@ mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* m
     if (ms_out && ms[i].size() == 2) {
       ms_out[2 * mat] = ms[i][0];
       ms_out[2 * mat + 1] = ms[i][1];
+    }
+  }
+  return MPM_OK;
+}
+
+mpm_status mpm_autotune_config(const mpm_ctx* ctx, int32_t* grid_blocks, float* grid_ms, int32_t* g2p_stage,
+                               float* g2p_ms) {
+  if (!ctx) return MPM_ERR_INVALID_ARG;
+  if (grid_blocks) *grid_blocks = ctx->g.grid_blocks;
+  for (int c = 0; c < 4 && grid_ms; ++c) grid_ms[c] = c < (int)ctx->tune.grid.size() ? ctx->tune.grid[c] : 0.0f;
+  for (int m = 0; m < 4; ++m) {
+    if (g2p_stage) g2p_stage[m] = -1;
+    if (g2p_ms) g2p_ms[2 * m] = g2p_ms[2 * m + 1] = 0.0f;
+  }
+  for (size_t i = 0; i < ctx->g.mats.size(); ++i) {
+    const int mat = ctx->g.mats[i].material;
+    if (mat < 0 || mat > 3) continue;
+    if (g2p_stage) g2p_stage[mat] = ctx->g.mats[i].g2p_stage;
+    if (g2p_ms && i < ctx->tune.g2p.size() && ctx->tune.g2p[i].size() == 2) {
+      g2p_ms[2 * mat] = ctx->tune.g2p[i][0];
+      g2p_ms[2 * mat + 1] = ctx->tune.g2p[i][1];
     }
   }
   return MPM_OK;

@@ -1,15 +1,21 @@
 // server.cu -- continuous-batching rollout server (mpm_server_* / mpm_submit / mpm_poll).
 //
 // Requests (an environment spec, its initial state, a horizon of actions, optionally the
-// reward adjoints for a gradient) arrive at any time.  A scheduler thread:
-//   1. admits queued requests in arrival order while a slot is free and the memory budget
-//      (a fraction of device memory) holds their buffers; admission uploads the request's
-//      state, actions and reward adjoints once, so its whole rollout stays on the device;
-//   2. each tick advances every resident environment in the forward phase by one control
-//      step (one launch per stage for all of them, stream A) and every environment in the
-//      reverse phase by one reverse control step (stream B), so the two phases overlap;
-//   3. retires finished requests: rewards, final positions and (if asked) action
-//      gradients go back to host memory, the device buffers are freed and waiters woken.
+// reward adjoints for a gradient) arrive at any time.  A scheduler thread, per tick:
+//   1. enqueues one control step of every resident environment in the forward phase (one
+//      launch per stage for all of them, stream A) and one reverse control step of every
+//      environment in the reverse phase (stream B), so the two phases overlap;
+//   2. while that runs, admits queued requests in arrival order as long as a slot is free
+//      and the memory budget (a fraction of device memory) holds their buffers: their
+//      buffers are carved from the server's device pool and their state, actions and reward
+//      adjoints uploaded on a third stream (C), once, so each whole rollout stays on the
+//      device; they join the resident set at the next tick;
+//   3. waits for the tick, then retires finished requests: rewards, final positions and (if
+//      asked) action gradients go back to host memory, the buffers go back to the pool and
+//      waiters are woken.
+// The pool grows by cudaMalloc up to the budget and is freed only when the server is
+// destroyed, so admissions and retirements make no cudaMalloc or cudaFree (a cudaFree
+// synchronises the whole device and would stall the streams of the running requests).
 // A request's result does not depend on what else is resident: every environment keeps its
 // own buffers and counters, and the batched kernels never mix environments.
 #include <cuda_runtime.h>
@@ -21,6 +27,7 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -39,6 +46,91 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Device memory of the admitted requests: chunks taken with cudaMalloc as needed, up to the
+// budget, carved first-fit into 256-byte aligned blocks and coalesced when given back.
+struct Pool {
+  struct Chunk {
+    char* base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free;  // offset -> bytes
+  };
+  std::vector<Chunk> chunks;
+  size_t reserved = 0;
+  static constexpr size_t kAlign = 256;
+  static constexpr size_t kMinChunk = size_t(1) << 30;
+
+  static size_t round(size_t n) { return (std::max<size_t>(n, 1) + kAlign - 1) / kAlign * kAlign; }
+
+  char* take(size_t n) {
+    n = round(n);
+    for (auto& c : chunks)
+      for (auto it = c.free.begin(); it != c.free.end(); ++it)
+        if (it->second >= n) {
+          const size_t off = it->first, left = it->second - n;
+          c.free.erase(it);
+          if (left) c.free[off + n] = left;
+          return c.base + off;
+        }
+    return nullptr;
+  }
+  void give(char* p, size_t n) {
+    n = round(n);
+    for (auto& c : chunks) {
+      if (p < c.base || p >= c.base + c.size) continue;
+      size_t off = (size_t)(p - c.base);
+      auto nx = c.free.lower_bound(off);
+      if (nx != c.free.end() && off + n == nx->first) {  // merge with the next block
+        n += nx->second;
+        nx = c.free.erase(nx);
+      }
+      if (nx != c.free.begin()) {  // merge with the previous block
+        auto pv = std::prev(nx);
+        if (pv->first + pv->second == off) {
+          pv->second += n;
+          return;
+        }
+      }
+      c.free[off] = n;
+      return;
+    }
+  }
+  // A new chunk that holds at least n bytes, if the budget allows it.
+  cudaError_t grow(size_t n, double budget) {
+    n = round(n);
+    size_t want = std::max(n, kMinChunk);
+    if ((double)(reserved + want) > budget) want = n;
+    if ((double)(reserved + want) > budget) return cudaErrorMemoryAllocation;
+    char* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e;
+    }
+    Chunk c;
+    c.base = p;
+    c.size = want;
+    c.free[0] = want;
+    chunks.push_back(std::move(c));
+    reserved += want;
+    return cudaSuccess;
+  }
+  char* alloc(size_t n, double budget) {
+    char* p = take(n);
+    if (!p && grow(n, budget) == cudaSuccess) p = take(n);
+    return p;
+  }
+  bool idle() const {
+    for (auto& c : chunks)
+      if (c.free.size() != 1 || c.free.begin()->second != c.size) return false;
+    return true;
+  }
+  void release() {  // only with nothing carved out and no work in flight
+    for (auto& c : chunks) cudaFree(c.base);
+    chunks.clear();
+    reserved = 0;
+  }
+};
+
 struct Req {
   uint64_t id = 0;
   mpm_env_spec spec{};
@@ -50,6 +142,8 @@ struct Req {
   std::vector<float> fem_rest;
   EnvLayout lay;
   char* mem = nullptr;
+  char* io = nullptr;  // upload staging (caller-order state), given back once uploaded
+  size_t io_bytes = 0;
   EnvDesc desc{};
   int phase = 0;  // 0 queued, 1 forward, 2 reverse, 3 done
   int steps = 0;  // steps done in the current phase
@@ -75,9 +169,8 @@ struct mpm_server {
   bool stop = false;
   std::thread th;
   Group gf, gb;
-  cudaStream_t sf = nullptr, sb = nullptr;
-  float* io = nullptr;
-  size_t io_cap = 0;
+  cudaStream_t sf = nullptr, sb = nullptr, su = nullptr;
+  Pool pool;  // scheduler thread only
   std::string err;
   uint64_t next_id = 1;
   Clock::time_point t0;
@@ -103,8 +196,10 @@ mpm_status sfail(mpm_server* s, mpm_status st, const char* fmt, ...) {
 }
 
 void finish(mpm_server* s, const std::shared_ptr<Req>& r, int status) {
-  if (r->mem) cudaFree(r->mem);
+  if (r->mem) s->pool.give(r->mem, r->lay.total);
   r->mem = nullptr;
+  if (r->io) s->pool.give(r->io, r->io_bytes);
+  r->io = nullptr;
   std::lock_guard<std::mutex> lk(s->mu);
   s->used -= (double)r->lay.total;
   r->status = status;
@@ -114,44 +209,44 @@ void finish(mpm_server* s, const std::shared_ptr<Req>& r, int status) {
   s->cv_done.notify_all();
 }
 
-// Device-side setup of an admitted request (scheduler thread): buffers, state, horizon.
+// Device-side setup of an admitted request (scheduler thread), enqueued on the upload
+// stream: buffers carved from the pool (the caller checked that they fit), zeroed, then
+// the state, horizon arrays and poses uploaded and the state laid into slot 0.  The caller
+// synchronises the upload stream.
 cudaError_t admit(mpm_server* s, Req& r, Group& scratch) {
-  cudaError_t e = cudaMalloc(&r.mem, r.lay.total);
-  if (e) return e;
-  if ((e = cudaMemset(r.mem, 0, r.lay.total))) return e;
-  env_fill(r.desc, r.spec, r.lay, r.mem, nullptr, nullptr);
   const size_t P = (size_t)r.spec.n_particles;
-  if (s->io_cap < P * (kComp + 1)) {
-    if (s->io) cudaFree(s->io);
-    s->io = nullptr;
-    s->io_cap = 0;
-    if ((e = cudaMalloc(&s->io, P * (kComp + 1) * sizeof(float)))) return e;
-    s->io_cap = P * (kComp + 1);
-  }
-  float* io = s->io;
-  cudaMemcpy(io, r.x.data(), P * 3 * 4, cudaMemcpyHostToDevice);
-  cudaMemcpy(io + P * 3, r.v.data(), P * 3 * 4, cudaMemcpyHostToDevice);
-  cudaMemcpy(io + P * 6, r.C.data(), P * 9 * 4, cudaMemcpyHostToDevice);
-  cudaMemcpy(io + P * 15, r.F.data(), P * 9 * 4, cudaMemcpyHostToDevice);
+  cudaStream_t su = s->su;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(r.mem, 0, r.lay.total, su))) return e;
+  env_fill(r.desc, r.spec, r.lay, r.mem, nullptr, nullptr);
+  float* io = reinterpret_cast<float*>(r.io);
+  if ((e = cudaMemcpyAsync(io, r.x.data(), P * 3 * 4, cudaMemcpyHostToDevice, su)) ||
+      (e = cudaMemcpyAsync(io + P * 3, r.v.data(), P * 3 * 4, cudaMemcpyHostToDevice, su)) ||
+      (e = cudaMemcpyAsync(io + P * 6, r.C.data(), P * 9 * 4, cudaMemcpyHostToDevice, su)) ||
+      (e = cudaMemcpyAsync(io + P * 15, r.F.data(), P * 9 * 4, cudaMemcpyHostToDevice, su)))
+    return e;
   int* gbuf = nullptr;
   if (!r.group.empty()) {
     gbuf = (int*)(io + P * kComp);
-    cudaMemcpy(gbuf, r.group.data(), P * 4, cudaMemcpyHostToDevice);
+    if ((e = cudaMemcpyAsync(gbuf, r.group.data(), P * 4, cudaMemcpyHostToDevice, su))) return e;
   }
-  {
-    float q0[kPose];
-    initial_pose(r.spec, q0);
-    cudaMemcpy(r.desc.pose, q0, sizeof q0, cudaMemcpyHostToDevice);
-  }
+  float q0[kPose];
+  initial_pose(r.spec, q0);
+  if ((e = cudaMemcpyAsync(r.desc.pose, q0, sizeof q0, cudaMemcpyHostToDevice, su))) return e;
+  if (r.A > 0 &&
+      (e = cudaMemcpyAsync((void*)r.desc.act_env, r.actions.data(), (size_t)r.T * r.A * 4, cudaMemcpyHostToDevice, su)))
+    return e;
+  if ((e = cudaMemcpyAsync((void*)r.desc.rbar_env, r.rbar.data(), (size_t)r.T * 4, cudaMemcpyHostToDevice, su)))
+    return e;
+  // q0 lives on this stack frame: the copies must finish before it goes
+  if ((e = cudaStreamSynchronize(su))) return e;
   if ((e = fem_upload(r.spec, r.desc))) return e;
-  if (r.A > 0) cudaMemcpy((void*)r.desc.act_env, r.actions.data(), (size_t)r.T * r.A * 4, cudaMemcpyHostToDevice);
-  cudaMemcpy((void*)r.desc.rbar_env, r.rbar.data(), (size_t)r.T * 4, cudaMemcpyHostToDevice);
   // a one-environment group writes the state into slot 0
   std::vector<EnvDesc> d{r.desc};
   std::vector<mpm_env_spec> sp{r.spec};
   if ((e = group_build(scratch, d, sp))) return e;
-  launch_set_state(env_launch(scratch, 0, 0), io, io + P * 3, io + P * 6, io + P * 15, gbuf);
-  return cudaDeviceSynchronize();
+  launch_set_state(env_launch(scratch, 0, su), io, io + P * 3, io + P * 6, io + P * 15, gbuf);
+  return cudaStreamSynchronize(su);
 }
 
 // Results of a request whose forward phase ended (final positions, rewards, status bits).
@@ -162,8 +257,8 @@ cudaError_t collect_forward(mpm_server* s, Req& r, Group& scratch, int* status_b
   cudaError_t e = group_build(scratch, d, sp);
   if (e) return e;
   float* xout = (float*)(r.mem + r.lay.xout);
-  launch_get_state(env_launch(scratch, 0, 0), StateRef{REF_LIVE, 0}, xout, nullptr, nullptr, nullptr);
-  if ((e = cudaDeviceSynchronize())) return e;
+  launch_get_state(env_launch(scratch, 0, s->su), StateRef{REF_LIVE, 0}, xout, nullptr, nullptr, nullptr);
+  if ((e = cudaStreamSynchronize(s->su))) return e;
   r.xfinal.resize(P * 3);
   r.rewards.resize(r.T);
   cudaMemcpy(r.xfinal.data(), xout, P * 3 * 4, cudaMemcpyDeviceToHost);
@@ -171,7 +266,6 @@ cudaError_t collect_forward(mpm_server* s, Req& r, Group& scratch, int* status_b
   EnvCtr c;
   cudaMemcpy(&c, r.desc.ctr, sizeof c, cudaMemcpyDeviceToHost);
   *status_bits = c.status;
-  (void)s;
   return cudaGetLastError();
 }
 
@@ -181,41 +275,90 @@ int status_of(int bits) {
   return MPM_OK;
 }
 
+// Take queued requests (arrival order; the head waits until it fits) and upload them on
+// stream C while the tick runs.  Returns the requests that will join at the next tick.
+std::vector<std::shared_ptr<Req>> admit_pending(mpm_server* s, Group& scratch, size_t resident) {
+  std::vector<std::shared_ptr<Req>> admitted;
+  for (;;) {
+    std::shared_ptr<Req> r;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->pending.empty() || resident + admitted.size() >= (size_t)s->max_resident) break;
+      r = s->pending.front();
+      if (s->used + (double)r->lay.total > s->budget) break;
+    }
+    const size_t P = (size_t)r->spec.n_particles;
+    r->io_bytes = P * (kComp + 1) * sizeof(float);
+    r->mem = s->pool.alloc(r->lay.total, s->budget + (double)r->io_bytes);
+    r->io = r->mem ? s->pool.alloc(r->io_bytes, s->budget + (double)r->io_bytes) : nullptr;
+    if (!r->mem || !r->io) {  // no contiguous room now: wait for retirements
+      if (r->mem) s->pool.give(r->mem, r->lay.total);
+      if (r->io) s->pool.give(r->io, r->io_bytes);
+      r->mem = r->io = nullptr;
+      if (resident + admitted.size() == 0 && s->pool.idle()) {
+        // nothing runs and the pool is empty, yet fragmented or too small: start it over
+        s->pool.release();
+        r->mem = s->pool.alloc(r->lay.total, s->budget + (double)r->io_bytes);
+        r->io = r->mem ? s->pool.alloc(r->io_bytes, s->budget + (double)r->io_bytes) : nullptr;
+      }
+      if (!r->mem || !r->io) {
+        if (r->mem) s->pool.give(r->mem, r->lay.total);
+        r->mem = nullptr;
+        if (resident + admitted.size() == 0) {  // it can never be placed
+          {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->pending.pop_front();
+            s->used += (double)r->lay.total;
+          }
+          finish(s, r, MPM_ERR_OOM);
+          continue;
+        }
+        break;
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->pending.pop_front();
+      s->used += (double)r->lay.total;
+    }
+    cudaError_t e = admit(s, *r, scratch);
+    s->pool.give(r->io, r->io_bytes);  // uploaded (or failed): the staging goes back
+    r->io = nullptr;
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      finish(s, r, MPM_ERR_CUDA);
+      continue;
+    }
+    r->t_admit = now_ms(s);
+    admitted.push_back(r);
+  }
+  return admitted;
+}
+
 void scheduler(mpm_server* s) {
   cudaSetDevice(s->device);
   Group scratch;
   bool layout_changed = true;
+  std::vector<std::shared_ptr<Req>> incoming;  // uploaded, joining at the next tick
   for (;;) {
-    // ---- admission (arrival order; the head waits until it fits)
-    std::vector<std::shared_ptr<Req>> admitted;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      if (s->resident.empty() && s->pending.empty() && !s->stop)
+      if (s->resident.empty() && incoming.empty() && s->pending.empty() && !s->stop)
         s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
       if (s->stop) break;
-      while (!s->pending.empty() && (int)(s->resident.size() + admitted.size()) < s->max_resident) {
-        auto& r = s->pending.front();
-        if (s->used + (double)r->lay.total > s->budget) break;
-        s->used += (double)r->lay.total;
-        admitted.push_back(r);
-        s->pending.pop_front();
-      }
     }
-    for (auto& r : admitted) {
-      cudaError_t e = admit(s, *r, scratch);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        finish(s, r, e == cudaErrorMemoryAllocation ? MPM_ERR_OOM : MPM_ERR_CUDA);
-        continue;
-      }
-      r->t_admit = now_ms(s);
+    for (auto& r : incoming) {
       r->phase = 1;
       r->steps = 0;
       s->resident.push_back(r);
       layout_changed = true;
     }
-    if (s->resident.empty()) continue;
-    // ---- groups: forward-phase and reverse-phase environments
+    incoming.clear();
+    if (s->resident.empty()) {  // nothing to run: admit, and start at the next tick
+      incoming = admit_pending(s, scratch, 0);
+      continue;
+    }
+    // ---- groups: forward-phase and reverse-phase environments (no work in flight here)
     std::vector<std::shared_ptr<Req>> fw, bw;
     for (auto& r : s->resident) (r->phase == 1 ? fw : bw).push_back(r);
     if (layout_changed) {
@@ -243,6 +386,8 @@ void scheduler(mpm_server* s) {
         }
       enqueue_reverse(s->gb, s->sb, nullptr, nullptr, s->gb.n_envs, s->gb.A_max, false);
     }
+    // ---- admissions upload on stream C while the tick runs
+    incoming = admit_pending(s, scratch, s->resident.size());
     cudaError_t ef = cudaStreamSynchronize(s->sf);
     cudaError_t eb = cudaStreamSynchronize(s->sb);
     if (ef != cudaSuccess || eb != cudaSuccess) {
@@ -290,6 +435,7 @@ void scheduler(mpm_server* s) {
     }
     s->resident.swap(keep);
   }
+  for (auto& r : incoming) finish(s, r, MPM_ERR_STATE);
   for (auto& r : s->resident) finish(s, r, MPM_ERR_STATE);
   s->resident.clear();
   scratch.release();
@@ -321,7 +467,8 @@ mpm_status mpm_server_create(const mpm_server_options* opt, mpm_server** out) {
   }
   s->budget = o.mem_fraction * (double)tot;
   if (cudaStreamCreateWithFlags(&s->sf, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->sb, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&s->sb, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->su, cudaStreamNonBlocking) != cudaSuccess) {
     delete s;
     return MPM_ERR_CUDA;
   }
@@ -346,9 +493,10 @@ void mpm_server_destroy(mpm_server* s) {
   cudaSetDevice(s->device);
   s->gf.release();
   s->gb.release();
-  if (s->io) cudaFree(s->io);
+  s->pool.release();
   if (s->sf) cudaStreamDestroy(s->sf);
   if (s->sb) cudaStreamDestroy(s->sb);
+  if (s->su) cudaStreamDestroy(s->su);
   delete s;
 }
 

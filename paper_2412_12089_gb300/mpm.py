@@ -105,6 +105,8 @@ def lib():
         "mpm_bin": (i32, [_P, i32, i32, _P, _P, _P]),
         "mpm_bin_static": (i32, [_P, i32, i32, _P, _P, _P]),
         "mpm_autotune": (i32, [_P, i32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_float)]),
+        "mpm_autotune_config": (i32, [_P, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_float), ct.POINTER(ct.c_int32),
+                                      ct.POINTER(ct.c_float)]),
         "mpm_obs_dim": (i32, [_P]),
         "mpm_observe": (i32, [_P, _P, _P]),
         "mpm_set_obs_adjoint": (i32, [_P, _P, _P]),
@@ -307,6 +309,20 @@ def mpm_autotune(ctx, trials=3):
     chosen = {names[m]: int(box[m]) for m in range(4) if box[m]}
     times = {names[m]: (float(ms[2 * m]), float(ms[2 * m + 1])) for m in range(4) if box[m]}
     return chosen, times
+
+
+def mpm_autotune_config(ctx):
+    """The rest of the autotuner's choice: {"grid_blocks", "grid_ms" (per CTA choice),
+    "g2p_stage" {material: 0/1}, "g2p_ms" {material: (ms without, ms with staging)}}."""
+    gb = ct.c_int32()
+    gms = (ct.c_float * 4)()
+    st = (ct.c_int32 * 4)()
+    sms = (ct.c_float * 8)()
+    check(lib().mpm_autotune_config(ctx, ct.byref(gb), gms, st, sms), ctx=ctx)
+    names = ("neohookean", "vonmises", "fluid", "muscle")
+    return {"grid_blocks": int(gb.value), "grid_ms_304_608_1216_2432": [float(v) for v in gms],
+            "g2p_stage": {names[m]: int(st[m]) for m in range(4) if st[m] >= 0},
+            "g2p_ms_plain_staged": {names[m]: (float(sms[2 * m]), float(sms[2 * m + 1])) for m in range(4) if st[m] >= 0}}
 
 
 def mpm_obs_dim(ctx):

@@ -196,7 +196,7 @@ calls = {
     "mpm_backward": (N,) * 13, "mpm_backward_begin": (N,) * 6, "mpm_backward_step": (N,) * 6,
     "mpm_backward_end": (N,) * 8, "mpm_reset_tape": (N,), "mpm_check_status": (N, N),
     "mpm_time_kernel": (N, 0), "mpm_kernel_time": (N, N, N), "mpm_observe": (N, N, N),
-    "mpm_set_obs_adjoint": (N, N, N), "mpm_autotune": (N, 3, N, N),
+    "mpm_set_obs_adjoint": (N, N, N), "mpm_autotune": (N, 3, N, N), "mpm_autotune_config": (N, N, N, N, N),
     "mpm_submit": (N, N, N), "mpm_poll": (N, 0, N), "mpm_wait": (N, 0, 1.0, N), "mpm_release": (N, 0),
 }
 bad = {k: getattr(L, k)(*a) for k, a in calls.items()}

@@ -375,9 +375,26 @@ def test_autotune_picks_a_box_and_keeps_results():
     assert set(chosen) == {"vonmises"} and chosen["vonmises"] in (512, 1024)
     assert all(t > 0 for pair in times.values() for t in pair)
     assert chosen["vonmises"] == (512 if times["vonmises"][0] <= times["vonmises"][1] else 1024)
+    cfg = mpm.mpm_autotune_config(b.ctx)
+    assert cfg["grid_blocks"] in (304, 608, 1216, 2432)
+    assert cfg["grid_blocks"] == (304, 608, 1216, 2432)[int(np.argmin(cfg["grid_ms_304_608_1216_2432"]))]
+    assert cfg["g2p_stage"] == {"vonmises": 1}  # no tape: G2P staging keeps its default
     rews = [b.step(torch.as_tensor(w.actions[t]).cuda()).clone() for t in range(2)]
     st = {k: v.cpu().numpy() for k, v in b.get_state().items()}
     assert rel_err(st["x"], st0["x"]) < 1e-5  # the tuning trials left the state unchanged
     assert np.allclose(torch.stack(rews).cpu().numpy(), rew0, rtol=1e-5, atol=1e-7)
     with pytest.raises(mpm.MpmError):
         mpm.mpm_autotune(b.ctx, trials=0)
+    # with a checkpoint tape the G2P staging is tuned as well, on the ring's first block,
+    # and the recorded steps and their gradients are unchanged by the trials
+    bt = Batch(w.specs, max_steps=2)
+    bt.set_inits(w.inits)
+    mpm.mpm_autotune(bt.ctx, trials=2)
+    cfg = mpm.mpm_autotune_config(bt.ctx)
+    plain, staged = cfg["g2p_ms_plain_staged"]["vonmises"]
+    assert plain > 0 and staged > 0 and cfg["g2p_stage"]["vonmises"] == (0 if plain < staged else 1)
+    rews_t = [bt.step(torch.as_tensor(w.actions[t]).cuda(), record=True).clone() for t in range(2)]
+    st_t = {k: v.cpu().numpy() for k, v in bt.get_state().items()}
+    assert rel_err(st_t["x"], st0["x"]) < 1e-5
+    assert np.allclose(torch.stack(rews_t).cpu().numpy(), rew0, rtol=1e-5, atol=1e-7)
+    bt.close()
