@@ -612,7 +612,7 @@ def main():
             # autotune the scatter kernels' shared-box capacity on a binned state (the captured
             # graphs are dropped and captured again with the choice)
             chosen, p2g_ms = mpm.mpm_autotune(b.ctx, trials=3)
-            tuned = {"scatter_box_nodes": chosen, "p2g_trial_ms_512_1024": p2g_ms, **mpm.mpm_autotune_config(b.ctx)}
+            tuned = {"scatter_box_nodes": chosen, "p2g_trial_ms_512_1024_256w": p2g_ms, **mpm.mpm_autotune_config(b.ctx)}
     torch.cuda.synchronize()
     tiles = max(mpm.mpm_last_active_tiles(b.ctx), 0)
 

@@ -341,13 +341,15 @@ mpm_status mpm_set_obs_adjoint(mpm_ctx* ctx, const float* obs_adj, void* stream)
 /*
  * Autotuner for the scatter kernels (P2G and its adjoint's scatter half; the batching
  * scheme these shapes belong to has no counterpart in the paper).  On the context's
- * current state, times P2G of every material present with each shared-box capacity the
- * kernels are built for (512 and 1024 nodes), `trials` timed launches each after one
- * warm-up, and keeps the fastest per material for every later step (captured graphs are
- * dropped and captured again).  The state is not changed.  Call it after mpm_set_state,
+ * current state, times P2G of every material present with each scatter shape the kernels
+ * are built for, `trials` timed launches each after one warm-up, and keeps the fastest per
+ * material for every later step (captured graphs are dropped and captured again).  The
+ * shapes, named by their shared-box capacity: 512 and 1024 nodes for 256-particle CTAs of
+ * four warps, 256 nodes for 64-particle CTAs of one warp.  It then tunes the grid kernels
+ * and G2P (mpm_autotune_config).  The state is not changed.  Call it after mpm_set_state,
  * between steps.
  *   box_out: [4] host, chosen capacity by material (MPM_MAT_*), 0 for absent materials;
- *   ms_out:  [4][2] host, mean P2G time (ms) per material with 512 and 1024 nodes;
+ *   ms_out:  [4][3] host, mean P2G time (ms) per material with 512, 1024 and 256 nodes;
  *   either may be NULL.  trials in [1, 1000], else MPM_ERR_INVALID_ARG.  Synchronises.
  * Passage: none in the paper (launch-shape tuning of this library).
  */

@@ -365,7 +365,8 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
   int box0 = 512;
   if (const char* b = std::getenv("MPM_SCATTER_BOX")) {
     const int v = std::atoi(b);
-    if (v == kScatterBoxes[0] || v == kScatterBoxes[1]) box0 = v;
+    for (int b = 0; b < kNScatterBoxes; ++b)
+      if (v == kScatterBoxes[b]) box0 = v;
   }
   // test-only: shorten G2P's first bounded wait so that it gives up (the status path)
   g.wait_polls = -1;
@@ -588,7 +589,7 @@ cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, TuneTimes* t
     MatGroup& m = g.mats[mi];
     float best = 0.0f;
     int best_box = m.sc_box;
-    for (int bi = 0; bi < 2 && err == cudaSuccess; ++bi) {
+    for (int bi = 0; bi < kNScatterBoxes && err == cudaSuccess; ++bi) {
       const int box = kScatterBoxes[bi];
       float sum = 0.0f;
       for (int t = 0; t <= trials && err == cudaSuccess; ++t) {

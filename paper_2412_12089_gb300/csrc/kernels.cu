@@ -235,27 +235,50 @@ __device__ __forceinline__ unsigned cell_pack(int b0, int b1, int b2) {
 // cell order (ordering them by size to balance a warp's lanes cost more than it saved).
 // (3) The box is flushed to the grid with float4 atomics.
 
-// Box capacities the scatter kernels are built for (nodes); the autotuner picks one per
-// material.  A 256-particle chunk of a dense body spans 150-400 nodes.
+// Scatter shapes the kernels are built for, by shared-box capacity (nodes): 256-particle
+// chunks on four-warp CTAs with a 512- or 1024-node box, or the same chunks split into four
+// 64-particle CTAs of one warp each with a 256-node box (kScBoxWarp), whose barriers are
+// warp-wide only.  The autotuner picks one per material.  A 256-particle chunk of a dense
+// body spans 150-400 nodes, a 64-particle one 60-200.
 constexpr int kScBoxSmall = 512;
 constexpr int kScBoxLarge = 1024;
+constexpr int kScBoxWarp = 256;
 constexpr int kRec = 24;  // floats per particle record
+
+// Threads per CTA of the scatter kernels built for a box capacity.
+template <int kScBox>
+struct ScatterThreads {
+  static constexpr int value = kScBox == kScBoxWarp ? 32 : kBlock;
+};
 
 template <int kScBox>
 struct ScatterShared {
-  float4 rec[kRec / 4 * kBlock * kPPT];      // particle records (24 KB): quad j of particle l at
-                                             // rec[j * kRecStride + l], so the lanes of a warp
-                                             // reading different particles hit different banks
-  float box[4 * kScBox];                     // box nodes, component-major (8 or 16 KB)
-  unsigned key[kBlock * kPPT];               // packed cell base per particle (~0u: none)
-  unsigned short gstart[kBlock * kPPT + 1];  // first particle of each group, then the end
-  unsigned short sidx[kBlock * kPPT];        // grouped position -> particle record
-  int seg[kPPT * kBlock / 32];               // group heads per (particle slot, warp)
+  static constexpr int NT = ScatterThreads<kScBox>::value;
+  float4 rec[kRec / 4 * NT * kPPT];       // particle records (96 B each): quad j of particle l at
+                                          // rec[j * NT * kPPT + l], so the lanes of a warp
+                                          // reading different particles hit different banks
+  float box[4 * kScBox];                  // box nodes, component-major
+  unsigned key[NT * kPPT];                // packed cell base per particle (~0u: none)
+  unsigned short gstart[NT * kPPT + 1];   // first particle of each group, then the end
+  unsigned short sidx[NT * kPPT];         // grouped position -> particle record
+  int seg[kPPT * NT / 32];                // group heads per (particle slot, warp)
 };
+
+// The part of work item `it0` that CTA `blockIdx.x` of a scatter kernel with NT threads takes:
+// 256-particle items are split into 128 / NT consecutive parts.  Returns false for an empty part.
+template <int NT>
+__device__ __forceinline__ bool scatter_part(const WorkItem& it0, WorkItem& it) {
+  constexpr int kParts = kBlock / NT;
+  const int sub = kParts > 1 ? (int)(blockIdx.x % kParts) : 0;
+  it = it0;
+  it.start += sub * NT * kPPT;
+  it.count = min(max(it0.count - sub * NT * kPPT, 0), NT * kPPT);
+  return it.count > 0;
+}
 
 // Record quads: (q0 q1 q2 gx) (gy gz wx0 wx1) (wx2 wy0 wy1 wy2) (wz0 wz1 wz2 A00)
 // (A01 A02 A10 A11) (A12 A20 A21 A22), quad j at r[j * kRecStride] (r = rec + particle).
-constexpr int kRecStride = kBlock * kPPT;
+template <int kRecStride>
 __device__ __forceinline__ void write_record(float4* r, const float* q, const float* g, const float* wx,
                                              const float* wy, const float* wz, const float* A) {
   r[0] = make_float4(q[0], q[1], q[2], g[0]);
@@ -273,6 +296,8 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
                                                const bool* valid, const int (*base)[3], const int* sred,
                                                const Box& bx, float pm, float4* grid, uint2* active,
                                                int* active_n) {
+  constexpr int NT = ScatterThreads<kScBox>::value;
+  constexpr int kRecStride = NT * kPPT;
   const bool fits = sred[3] >= 0 && bx.nx * bx.ny * bx.nz <= kScBox;
   const int cnx = bx.nx - 2, cny = bx.ny - 2;
   // per cell of the box: particles, then offsets.  It lives in the box's fourth component,
@@ -280,12 +305,12 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
   unsigned* cnt = reinterpret_cast<unsigned*>(sh.box + 3 * kScBox);
   if (fits) {
     const int vol = bx.nx * bx.ny * bx.nz, cvol = cnx * cny * (bx.nz - 2);
-    for (int q = threadIdx.x; q < vol; q += kBlock) {
+    for (int q = threadIdx.x; q < vol; q += NT) {
       sh.box[q] = 0.f;
       sh.box[kScBox + q] = 0.f;
       sh.box[2 * kScBox + q] = 0.f;
     }
-    for (int q = threadIdx.x; q < cvol; q += kBlock) cnt[q] = 0u;
+    for (int q = threadIdx.x; q < cvol; q += NT) cnt[q] = 0u;
   } else if (kMass) {
 #pragma unroll
     for (int p = 0; p < kPPT; ++p)
@@ -314,7 +339,7 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
     }
     __syncthreads();
     // exclusive scan of (particles | non-empty << 16) over the cells: offsets and group numbers
-    const int per = (cvol + kBlock - 1) / kBlock;
+    const int per = (cvol + NT - 1) / NT;
     const int c0 = threadIdx.x * per;
     unsigned loc = 0;
     for (int q = 0; q < per && c0 + q < cvol; ++q) {
@@ -331,7 +356,7 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
     __syncthreads();
     unsigned run = incl - loc;
     unsigned total = 0;
-    for (int w = 0; w < kBlock / 32; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
       const unsigned t = (unsigned)sh.seg[w];
       if (w < warp) run += t;
       total += t;
@@ -346,40 +371,40 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < kPPT; ++p)
-      if (valid[p]) sh.sidx[(cnt[ci[p]] & 0xffffu) + rk[p]] = (unsigned short)(threadIdx.x + p * kBlock);
+      if (valid[p]) sh.sidx[(cnt[ci[p]] & 0xffffu) + rk[p]] = (unsigned short)(threadIdx.x + p * NT);
   } else {
     // groups = runs of equal keys in chunk order, numbered by a scan over (slot, warp) segments
     unsigned heads[kPPT];
 #pragma unroll
     for (int p = 0; p < kPPT; ++p) {
-      const int l = threadIdx.x + p * kBlock;
+      const int l = threadIdx.x + p * NT;
       const bool h = valid[p] && (l == 0 || sh.key[l - 1] != sh.key[l]);
       heads[p] = __ballot_sync(0xffffffffu, h);
-      if (lane == 0) sh.seg[p * (kBlock / 32) + warp] = __popc(heads[p]);
+      if (lane == 0) sh.seg[p * (NT / 32) + warp] = __popc(heads[p]);
       sh.sidx[l] = (unsigned short)l;
     }
     __syncthreads();
 #pragma unroll
     for (int p = 0; p < kPPT; ++p) {
-      const int sg = p * (kBlock / 32) + warp;
+      const int sg = p * (NT / 32) + warp;
       int off = 0;
       for (int q = 0; q < sg; ++q) off += sh.seg[q];
       if (heads[p] >> lane & 1u)
-        sh.gstart[off + __popc(heads[p] & ((1u << lane) - 1u))] = (unsigned short)(threadIdx.x + p * kBlock);
+        sh.gstart[off + __popc(heads[p] & ((1u << lane) - 1u))] = (unsigned short)(threadIdx.x + p * NT);
     }
-    for (int q = 0; q < kPPT * (kBlock / 32); ++q) ngrp += sh.seg[q];
+    for (int q = 0; q < kPPT * (NT / 32); ++q) ngrp += sh.seg[q];
   }
   if (threadIdx.x == 0) sh.gstart[ngrp] = (unsigned short)count;
   __syncthreads();  // the grouped positions are written (they read the counts) before the clear
   if (kMass && fits) {  // the cell counts are no longer read: clear the mass component
     const int vol = bx.nx * bx.ny * bx.nz;
-    for (int q = threadIdx.x; q < vol; q += kBlock) sh.box[3 * kScBox + q] = 0.f;
+    for (int q = threadIdx.x; q < vol; q += NT) sh.box[3 * kScBox + q] = 0.f;
   }
   __syncthreads();
   const float dx = e.dx;
   // units: (group, z offset c), each summing the nine nodes base + (0..2, 0..2, c)
   const int nunits = ngrp * 3;
-  for (int u = threadIdx.x; u < nunits; u += kBlock) {
+  for (int u = threadIdx.x; u < nunits; u += NT) {
     const int g = u / 3, oc = u - 3 * g;
     const int q0 = sh.gstart[g], q1 = sh.gstart[g + 1];
     const unsigned key = sh.key[sh.sidx[q0]];
@@ -455,15 +480,17 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
 // Grouped scatter of mass and APIC momentum (q = m v, A = m C - dt V D^-1 tau).
 
 template <int MAT, int BOX>
-__global__ void __launch_bounds__(kBlock, BOX == kScBoxSmall ? 6 : 5) k_p2g(const EnvDesc* __restrict__ envs,
-                                                   const WorkItem* __restrict__ items, int item_off, StateRef src,
-                                                   int use_perm, int k, int rev, uint2* active, int* active_n,
-                                                   const int2* __restrict__ skip_slot, int tape_T, int tape_S) {
+__global__ void __launch_bounds__(ScatterThreads<BOX>::value, BOX == kScBoxWarp ? 20 : (BOX == kScBoxSmall ? 6 : 5))
+    k_p2g(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items, int item_off, StateRef src,
+          int use_perm, int k, int rev, uint2* active, int* active_n, const int2* __restrict__ skip_slot,
+          int tape_T, int tape_S) {
+  constexpr int NT = ScatterThreads<BOX>::value;
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   __shared__ int sred[6];
   __shared__ ScatterShared<BOX> sh;
-  const WorkItem it = items[item_off + blockIdx.x];
+  WorkItem it;
+  if (!scatter_part<NT>(items[item_off + blockIdx.x / (kBlock / NT)], it)) return;
   // in the reverse pass, the grid tape restores this substep's grid when it was kept
   if (skip_slot != nullptr) {
     const int t = envs[it.env].ctr->rev;
@@ -486,7 +513,7 @@ __global__ void __launch_bounds__(kBlock, BOX == kScBoxSmall ? 6 : 5) k_p2g(cons
   int oob = 0;
 #pragma unroll
   for (int p = 0; p < kPPT; ++p) {
-    const int l = threadIdx.x + p * kBlock;
+    const int l = threadIdx.x + p * NT;
     valid[p] = l < it.count;
     sh.key[l] = 0xffffffffu;
     if (!valid[p]) continue;
@@ -513,7 +540,7 @@ __global__ void __launch_bounds__(kBlock, BOX == kScBoxSmall ? 6 : 5) k_p2g(cons
     bspline(f2, wz, dw);
     const float mv[3] = {pm * s[3], pm * s[4], pm * s[5]};
     const float g[3] = {f0 * dx, f1 * dx, f2 * dx};
-    write_record(sh.rec + l, mv, g, wx, wy, wz, A);
+    write_record<NT * kPPT>(sh.rec + l, mv, g, wx, wy, wz, A);
   }
   if (oob) atomicOr(&e.ctr->status, 1);
   const Box bx = make_box(base, valid, sred);
@@ -1039,14 +1066,16 @@ __global__ void __launch_bounds__(256) k_reward_end(const EnvDesc* __restrict__ 
 // ------------------------------------------------------------------ adjoint: G2P^T
 
 template <int MAT, int BOX>
-__global__ void __launch_bounds__(kBlock, 5) k_g2p_adj(const EnvDesc* __restrict__ envs,
-                                                       const WorkItem* __restrict__ items, int item_off, StateRef src,
-                                                       StateRef nxt, int use_perm, int k) {
+__global__ void __launch_bounds__(ScatterThreads<BOX>::value, BOX == kScBoxWarp ? 20 : 5)
+    k_g2p_adj(const EnvDesc* __restrict__ envs, const WorkItem* __restrict__ items, int item_off, StateRef src,
+              StateRef nxt, int use_perm, int k) {
+  constexpr int NT = ScatterThreads<BOX>::value;
   __shared__ EnvDesc e;
   __shared__ EnvCtr c;
   __shared__ int sred[6];
   __shared__ ScatterShared<BOX> sh;
-  const WorkItem it = items[item_off + blockIdx.x];
+  WorkItem it;
+  if (!scatter_part<NT>(items[item_off + blockIdx.x / (kBlock / NT)], it)) return;
   load_env(envs, it.env, e, c);
   const float* b = ref_block(e, c, src);
   const float* bn = ref_block(e, c, nxt);  // the substep's end state: holds v' and C'
@@ -1069,7 +1098,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_g2p_adj(const EnvDesc* __restrict
   int oob = 0;
 #pragma unroll 1
   for (int p = 0; p < kPPT; ++p) {
-    const int l = threadIdx.x + p * kBlock;
+    const int l = threadIdx.x + p * NT;
     valid[p] = l < it.count;
     sh.key[l] = 0xffffffffu;
     if (!valid[p]) continue;
@@ -1136,7 +1165,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_g2p_adj(const EnvDesc* __restrict
     {
       const float q[3] = {vnb[0] - vref[0], vnb[1] - vref[1], vnb[2] - vref[2]};
       const float g[3] = {fx[0] * dx, fx[1] * dx, fx[2] * dx};
-      write_record(sh.rec + l, q, g, w[0], w[1], w[2], Ab);
+      write_record<NT * kPPT>(sh.rec + l, q, g, w[0], w[1], w[2], Ab);
     }
     // gather: x-bar += sum_i (g_i . (v-bar' + A' r_i)) grad w_i - A'^T sum_i w_i g_i with
     // g_i = v_i - v_c (the stencil-uniform part of v_i adds nothing: sum grad w = 0 and
@@ -1939,6 +1968,7 @@ static void p2g_carveout(int pct) {
 static bool scatter_carveout() {
   p2g_carveout<kScBoxSmall>(cudaSharedmemCarveoutMaxShared);
   p2g_carveout<kScBoxLarge>(cudaSharedmemCarveoutMaxShared);
+  p2g_carveout<kScBoxWarp>(cudaSharedmemCarveoutMaxShared);
   return true;
 }
 
@@ -1948,10 +1978,10 @@ static void p2g_dispatch(const Launch& L, StateRef src, bool use_perm, int k, in
   const int tT = skip ? skip->T : 0, tS = skip ? skip->S : 0;
   const int pm = use_perm ? 1 : 0;
   switch (L.material) {
-    case MAT_NEOHOOKEAN: k_p2g<MAT_NEOHOOKEAN, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
-    case MAT_VONMISES: k_p2g<MAT_VONMISES, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
-    case MAT_FLUID: k_p2g<MAT_FLUID, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
-    default: k_p2g<MAT_MUSCLE, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
+    case MAT_NEOHOOKEAN: k_p2g<MAT_NEOHOOKEAN, BOX><<<L.n_items * (kBlock / ScatterThreads<BOX>::value), ScatterThreads<BOX>::value, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
+    case MAT_VONMISES: k_p2g<MAT_VONMISES, BOX><<<L.n_items * (kBlock / ScatterThreads<BOX>::value), ScatterThreads<BOX>::value, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
+    case MAT_FLUID: k_p2g<MAT_FLUID, BOX><<<L.n_items * (kBlock / ScatterThreads<BOX>::value), ScatterThreads<BOX>::value, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
+    default: k_p2g<MAT_MUSCLE, BOX><<<L.n_items * (kBlock / ScatterThreads<BOX>::value), ScatterThreads<BOX>::value, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, pm, k, rev, L.active, L.active_n, skip_slot, tT, tS); break;
   }
 }
 
@@ -1959,10 +1989,10 @@ template <int BOX>
 static void g2p_adj_dispatch(const Launch& L, StateRef src, StateRef nxt, bool use_perm, int k) {
   const int pm = use_perm ? 1 : 0;
   switch (L.material) {
-    case MAT_NEOHOOKEAN: k_g2p_adj<MAT_NEOHOOKEAN, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
-    case MAT_VONMISES: k_g2p_adj<MAT_VONMISES, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
-    case MAT_FLUID: k_g2p_adj<MAT_FLUID, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
-    default: k_g2p_adj<MAT_MUSCLE, BOX><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
+    case MAT_NEOHOOKEAN: k_g2p_adj<MAT_NEOHOOKEAN, BOX><<<L.n_items * (kBlock / ScatterThreads<BOX>::value), ScatterThreads<BOX>::value, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
+    case MAT_VONMISES: k_g2p_adj<MAT_VONMISES, BOX><<<L.n_items * (kBlock / ScatterThreads<BOX>::value), ScatterThreads<BOX>::value, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
+    case MAT_FLUID: k_g2p_adj<MAT_FLUID, BOX><<<L.n_items * (kBlock / ScatterThreads<BOX>::value), ScatterThreads<BOX>::value, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
+    default: k_g2p_adj<MAT_MUSCLE, BOX><<<L.n_items * (kBlock / ScatterThreads<BOX>::value), ScatterThreads<BOX>::value, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, nxt, pm, k); break;
   }
 }
 
@@ -1979,6 +2009,7 @@ void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k, const GridT
   Timed tm_(skip_kept ? KC_OTHER : KC_P2G, L.stream);
   const int rev = src.kind == REF_RING || src.kind == REF_REV ? 1 : 0;
   if (L.sc_box == kScBoxLarge) p2g_dispatch<kScBoxLarge>(L, src, use_perm, k, rev, skip_kept);
+  else if (L.sc_box == kScBoxWarp) p2g_dispatch<kScBoxWarp>(L, src, use_perm, k, rev, skip_kept);
   else p2g_dispatch<kScBoxSmall>(L, src, use_perm, k, rev, skip_kept);
 }
 
@@ -2026,6 +2057,7 @@ void launch_g2p_adj(const Launch& L, StateRef src, StateRef nxt, bool use_perm, 
   ensure_carveout();
   Timed tm_(KC_G2P_ADJ, L.stream);
   if (L.sc_box == kScBoxLarge) g2p_adj_dispatch<kScBoxLarge>(L, src, nxt, use_perm, k);
+  else if (L.sc_box == kScBoxWarp) g2p_adj_dispatch<kScBoxWarp>(L, src, nxt, use_perm, k);
   else g2p_adj_dispatch<kScBoxSmall>(L, src, nxt, use_perm, k);
 }
 

@@ -36,14 +36,16 @@ struct Launch {
   int grid_blocks;       // CTAs of the persistent grid kernels
   int env0, n_env;       // environment range of the per-env kernels
   cudaStream_t stream;
-  int sc_box = 512;      // shared-box capacity (nodes) of the scatter kernels: 512 or 1024
+  int sc_box = 512;      // scatter shape by shared-box capacity (nodes): 512 or 1024 (256-particle
+                         // CTAs of four warps) or 256 (64-particle CTAs of one warp)
   int wait_polls = -1;   // polls of G2P's first wait on its staged copies (< 0: the full limit)
   int g2p_stage = 1;     // G2P stages a chunk's x and H by bulk copies (when read in place)
 };
 
 constexpr int kGridBlockChoices[4] = {152 * 2, 152 * 4, 152 * 8, 152 * 16};  // persistent grid CTAs
 
-constexpr int kScatterBoxes[2] = {512, 1024};  // capacities the scatter kernels are built for
+constexpr int kNScatterBoxes = 3;
+constexpr int kScatterBoxes[kNScatterBoxes] = {512, 1024, 256};  // shapes the scatter kernels are built for
 
 enum GridMode { GRID_FWD = 0, GRID_KEEP = 1 };
 

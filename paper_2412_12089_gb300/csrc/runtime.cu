@@ -683,16 +683,14 @@ mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* m
   }
   for (int m = 0; m < 4; ++m) {
     if (box_out) box_out[m] = 0;
-    if (ms_out) ms_out[2 * m] = ms_out[2 * m + 1] = 0.0f;
+    for (int b = 0; b < kNScatterBoxes && ms_out; ++b) ms_out[kNScatterBoxes * m + b] = 0.0f;
   }
   for (size_t i = 0; i < ctx->g.mats.size(); ++i) {
     const int mat = ctx->g.mats[i].material;
     if (mat < 0 || mat > 3) continue;
     if (box_out) box_out[mat] = ctx->g.mats[i].sc_box;
-    if (ms_out && ms[i].size() == 2) {
-      ms_out[2 * mat] = ms[i][0];
-      ms_out[2 * mat + 1] = ms[i][1];
-    }
+    for (int b = 0; b < kNScatterBoxes && ms_out && (int)ms[i].size() == kNScatterBoxes; ++b)
+      ms_out[kNScatterBoxes * mat + b] = ms[i][b];
   }
   return MPM_OK;
 }

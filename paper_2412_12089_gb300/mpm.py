@@ -300,14 +300,14 @@ def mpm_bin_static_max():
 
 
 def mpm_autotune(ctx, trials=3):
-    """Pick the scatter-box capacity per material on the current state; returns
-    ({material: capacity}, {material: (ms with 512, ms with 1024)}) for materials present."""
+    """Pick the scatter shape per material on the current state; returns
+    ({material: capacity}, {material: (ms with 512, 1024, 256)}) for materials present."""
     box = (ct.c_int32 * 4)()
-    ms = (ct.c_float * 8)()
+    ms = (ct.c_float * 12)()
     check(lib().mpm_autotune(ctx, trials, box, ms), ctx=ctx)
     names = ("neohookean", "vonmises", "fluid", "muscle")
     chosen = {names[m]: int(box[m]) for m in range(4) if box[m]}
-    times = {names[m]: (float(ms[2 * m]), float(ms[2 * m + 1])) for m in range(4) if box[m]}
+    times = {names[m]: tuple(float(ms[3 * m + b]) for b in range(3)) for m in range(4) if box[m]}
     return chosen, times
 
 
