@@ -349,7 +349,7 @@ mpm_status mpm_set_obs_adjoint(mpm_ctx* ctx, const float* obs_adj, void* stream)
  * and G2P (mpm_autotune_config).  The state is not changed.  Call it after mpm_set_state,
  * between steps.
  *   box_out: [4] host, chosen capacity by material (MPM_MAT_*), 0 for absent materials;
- *   ms_out:  [4][3] host, mean P2G time (ms) per material with 512, 1024 and 256 nodes;
+ *   ms_out:  [4][3] host, fastest trial's P2G time (ms) per material with 512, 1024 and 256 nodes;
  *   either may be NULL.  trials in [1, 1000], else MPM_ERR_INVALID_ARG.  Synchronises.
  * Passage: none in the paper (launch-shape tuning of this library).
  */
@@ -360,10 +360,10 @@ mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* m
  * ring, which is scratch between reverse passes; without a tape G2P keeps the default):
  *   grid_blocks: CTAs of the persistent grid-update and grid-adjoint kernels, the fastest
  *     grid update of 304, 608, 1216 and 2432 CTAs (2, 4, 8, 16 per SM); grid_ms: [4] their
- *     mean times (ms);
+ *     fastest trials' times (ms);
  *   g2p_stage: [4] by material, 1 if G2P stages each chunk's x and H in shared memory by
  *     bulk copies, 0 if it loads them directly (-1 for absent materials); g2p_ms: [4][2]
- *     mean G2P time (ms) without and with the staging.
+ *     fastest trial's G2P time (ms) without and with the staging.
  * Before any mpm_autotune: the defaults (1216 CTAs, staging on) and zero times.  Any output
  * may be NULL.
  * Passage: none in the paper (launch-shape tuning of this library).

@@ -103,13 +103,14 @@ Launch env_launch(const Group& g, int e, cudaStream_t st);
 void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in, int a_max, float* rew,
                      bool per_env);
 // Autotuner, on the group's live state (binned first), `trials` timed launches of each
-// choice after one warm-up, keeping the fastest:
-//   - per material, P2G with every scatter-box capacity the kernels are built for;
+// choice after one warm-up, keeping the choice with the fastest trial:
+//   - per material, P2G with every scatter shape the kernels are built for;
 //   - the persistent grid kernels' CTA count (kGridBlockChoices);
 //   - per material, G2P with and without the bulk-copy staging of x and H.
 // Every trial writes only the grids (cleared again) and the first ring block (G2P, contexts
-// with a tape only), so the state is unchanged.  ms[m][b]: mean P2G time of material group m with capacity b; grid_ms[c]: mean
-// grid-update time with CTA choice c; g2p_ms[m][s]: mean G2P time of material m, staging s.
+// with a tape only), so the state is unchanged.  Times (the fastest trial of each choice):
+// p2g[m][b] of material group m with shape b, grid[c] with CTA choice c, g2p[m][s] of
+// material group m without (s = 0) and with staging.
 struct TuneTimes {
   std::vector<std::vector<float>> p2g, g2p;
   std::vector<float> grid;

@@ -199,19 +199,22 @@ def dough(n_envs: int = 512, seed: int = 0, n_range=(2000, 16000), G: int = 48, 
 # ----------------------------------------------------------------------------- C3
 
 def fluid(n_envs: int = 1024, seed: int = 0, n: int = 8192, G: int = 64, substeps: int = 25,
-          T: int = 16, action_std: float = 0.5, dt: float = 5e-4) -> Workload:
+          T: int = 16, action_std: float = 0.5, dt: float = 5e-4, floor_cells: float = 2.37,
+          az: float = 0.1) -> Workload:
     """Weakly compressible fluid (bulk 1e4, viscosity 1e-3, rho=1e3), n particles filling
     the lower half of an open-top container (inner 0.2^3, wall 2 dx) that follows
-    3-DoF translation actions ~ N(0, 0.5); reward = FluidMove's R_d to a seeded target."""
+    3-DoF translation actions ~ N(0, 0.5); reward = FluidMove's R_d to a seeded target.
+    The container floor's top face starts floor_cells cells above the wall layer (3 dx) plus
+    the wall thickness: the default keeps it off the node lattice; an integer, with an inner
+    half-height az that is a whole number of cells, puts it on it exactly in FP32."""
     rng = np.random.default_rng(seed)
     dx = 1.0 / G
-    a, w, az = 0.1, 2 * dx, 0.1
+    a, w = 0.1, 2 * dx
     specs, inits, acts = [], [], []
     for e in range(n_envs):
-        # cavity centre; z is kept off the node lattice (0.37 dx) so no node lies exactly on
-        # the floor's top face
+        # cavity centre
         c = np.array([0.5 + rng.uniform(-0.05, 0.05), 0.5 + rng.uniform(-0.05, 0.05),
-                      3 * dx + w + az + 2.37 * dx])
+                      3 * dx + w + az + floor_cells * dx])
         m = 0.5 * dx
         lo = np.array([c[0] - a + m, c[1] - a + m, c[2] - az + m])
         hi = np.array([c[0] + a - m, c[1] + a - m, c[2] - az + m + 0.1])

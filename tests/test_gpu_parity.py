@@ -138,6 +138,40 @@ def test_horizon_parity(name, T, S):
         assert np.allclose(rew[:, e], r, rtol=1e-3, atol=1e-5), (name, e, rew[:, e], r)
 
 
+def test_container_floor_on_node_lattice():
+    """The fluid container with its floor's top face exactly on a plane of grid nodes (and no
+    vertical actions, so it stays there): nodes with zero signed distance take the full
+    contact projection on both sides.  One substep at 1e-5 and a two-control-step horizon and
+    its action gradients at 1e-3 against the oracle."""
+    w = wl.fluid(n_envs=2, seed=23, n=1500, substeps=1, T=1, floor_cells=2.0, az=6 / 64)
+    w.actions[:, :, 2] = 0.0
+    for e, s in enumerate(w.specs):  # the floor's top face: a whole number of cells
+        zf = (np.float32(s.pose0[2]) - np.float32(s.coll_dims[2])) * np.float32(s.grid_res)
+        assert zf == 7.0, zf
+    w = perturb(w, seed=4, v_std=0.5)
+    for i in w.inits:  # particles moving down onto the floor
+        i.v[:, 2] = -np.abs(i.v[:, 2])
+    b, rew, st = gpu_run(w, 1)
+    for e in range(w.n_envs):
+        o, q, r = oracle_run(w, e, 1)
+        for k, tol in (("x", 1e-5), ("v", 1e-5), ("F", 1e-5)):
+            assert rel_err(split(w, st[k])[e], getattr(o, k)) < tol, (e, k, rel_err(split(w, st[k])[e], getattr(o, k)))
+    b.close()
+    T = 2
+    w2 = wl.fluid(n_envs=2, seed=23, n=1500, substeps=25, T=T, floor_cells=2.0, az=6 / 64)
+    w2.actions[:, :, 2] = 0.0
+    g, st2 = _gpu_grads(w2, T, rbar=np.ones((T, 2), np.float32))
+    for e in range(2):
+        s = w2.specs[e]
+        sp = orc.make_spec(s)
+        so = orc.State.from_init(w2.inits[e])
+        acts = w2.actions[:T, e, :3].astype(np.float64)
+        o, _, _, _ = orc.rollout(sp, so, orc.initial_pose(s), acts)
+        assert rel_err(split(w2, st2["x"].cpu().numpy())[e], o.x) < 1e-3
+        ag, _, _ = orc.rollout_adj(sp, so, orc.initial_pose(s), acts, rbar=np.ones(T))
+        assert rel_err(g["action_grad"][:, e, :3], ag) < 1e-3, (e, rel_err(g["action_grad"][:, e, :3], ag))
+
+
 # ------------------------------------------------------------------ batching
 
 def test_batched_equals_alone_and_per_env_launch():
