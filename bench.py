@@ -51,10 +51,11 @@ STEP_BYTES_PER_PARTICLE_SUBSTEP = 768
 # capture (kernel source hash at capture time).  Reported only
 # while the kernel sources are unchanged.
 MEASURED_TRAFFIC = {
-    # ncu captures of one launch over 1,310,720 binned fluid particles (160 envs, 64^3), in
-    # dram__bytes_read.sum + dram__bytes_write.sum per particle; scaled by particle count
-    "g2p_adj": (200.1, "d89daff75e39d176"),  # 214.5 MB read + 47.7 MB written, adjoint substep 4
-    "g2p": (104.7, "d89daff75e39d176"),      # 70.5 MB read + 66.8 MB written, forward substep 1
+    # ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of launches over 2,097,152
+    # binned fluid particles (256 envs x 8192, 64^3; state 210 MB, above L2), in bytes per
+    # particle, scaled by particle count
+    "g2p_adj": (210.2, "be5d8ba9f948872c"),  # 512-node box, mean of 2 adjoint-substep launches
+    "p2g": (95.4, "be5d8ba9f948872c"),       # 512-node box, mean of 18 launches
 }
 
 
