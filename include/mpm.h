@@ -344,6 +344,9 @@ mpm_status mpm_set_obs_adjoint(mpm_ctx* ctx, const float* obs_adj, void* stream)
  * current state, times P2G of every material present with each scatter shape the kernels
  * are built for, `trials` timed launches each after one warm-up, and keeps the fastest per
  * material for every later step (captured graphs are dropped and captured again).  The
+ * choices are also kept for the process, per (material, grid resolution, particles per cell
+ * rounded to a power of two) and, for the grid kernels, as one CTA count: every context and
+ * server group built later starts from them.  The
  * shapes, named by their shared-box capacity: 512 and 1024 nodes for 256-particle CTAs of
  * four warps, 256 nodes for 64-particle CTAs of one warp.  It then tunes the grid kernels
  * and G2P (mpm_autotune_config).  The state is not changed.  Call it after mpm_set_state,

@@ -7,13 +7,38 @@
 #include "engine.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace mpm {
 
 namespace {
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// The autotuner's choices, kept for the process: per (material, grid resolution, bucket of
+// particles per cell = round(log2(dx^3 / p_vol))) the scatter shape and G2P's staging, and
+// one CTA count for the grid kernels.  Every group built later (batch contexts and the
+// server's groups alike) starts from them.
+struct TuneKey {
+  int material, G, ppc;
+  bool operator<(const TuneKey& o) const { return std::tie(material, G, ppc) < std::tie(o.material, o.G, o.ppc); }
+};
+struct TuneVal {
+  int sc_box, g2p_stage;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+int g_tune_grid_blocks = 0;
+
+TuneKey tune_key(const mpm_env_spec& s) {
+  const double dx = 1.0 / (double)s.grid_res;
+  const double ppc = dx * dx * dx / std::max((double)s.p_vol, 1e-30);
+  return {s.material, s.grid_res, (int)std::floor(std::log2(std::max(ppc, 1.0)) + 0.5)};
+}
 int bits_for(unsigned long long v) {
   int b = 0;
   while (b < 64 && (v >> b) != 0ull) ++b;
@@ -375,14 +400,26 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
     if (v >= 0) g.wait_polls = v;
   }
   g.mats.clear();
-  for (size_t i = 0; i < g.items.size(); ++i) {
-    const int mat = specs[g.items[i].env].material;
-    if (mat == kMatFem) break;  // FEM items sort last; their envs run the FEM step kernels
-    if (g.mats.empty() || g.mats.back().material != mat)
-      g.mats.push_back({mat, (int)i, std::vector<int>(g.S_max + 1, 0), box0});
-    auto& m = g.mats.back();
-    for (int k = 0; k <= g.S_max; ++k)
-      if (specs[g.items[i].env].substeps > k) m.n_gt[k] += 1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (size_t i = 0; i < g.items.size(); ++i) {
+      const int mat = specs[g.items[i].env].material;
+      if (mat == kMatFem) break;  // FEM items sort last; their envs run the FEM step kernels
+      if (g.mats.empty() || g.mats.back().material != mat) {
+        g.mats.push_back({mat, (int)i, std::vector<int>(g.S_max + 1, 0), box0});
+        // the autotuner's earlier choice for this kind of environment (the variable set by
+        // tests to force a shape wins)
+        auto t = g_tune.find(tune_key(specs[g.items[i].env]));
+        if (t != g_tune.end()) {
+          if (!std::getenv("MPM_SCATTER_BOX")) g.mats.back().sc_box = t->second.sc_box;
+          g.mats.back().g2p_stage = t->second.g2p_stage;
+        }
+      }
+      auto& m = g.mats.back();
+      for (int k = 0; k <= g.S_max; ++k)
+        if (specs[g.items[i].env].substeps > k) m.n_gt[k] += 1;
+    }
+    if (g_tune_grid_blocks > 0) g.grid_blocks = g_tune_grid_blocks;
   }
   cudaError_t e;
   size_t cap;
@@ -677,6 +714,11 @@ cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, TuneTimes* t
       }
       if (err == cudaSuccess) m.g2p_stage = best_stage;
     }
+  }
+  if (err == cudaSuccess) {  // keep the choices for groups built later in the process
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& m : g.mats) g_tune[tune_key(g.spec[g.items[m.item0].env])] = {m.sc_box, m.g2p_stage};
+    g_tune_grid_blocks = g.grid_blocks;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

@@ -436,6 +436,7 @@ def test_autotune_picks_a_box_and_keeps_results():
     _, rew0, st0 = gpu_run(w, 2)
     b = Batch(w.specs, max_steps=0)
     b.set_inits(w.inits)
+    stage0 = mpm.mpm_autotune_config(b.ctx)["g2p_stage"]
     chosen, times = mpm.mpm_autotune(b.ctx, trials=2)
     assert set(chosen) == {"vonmises"} and chosen["vonmises"] in (512, 1024, 256)
     assert all(t > 0 for trio in times.values() for t in trio)
@@ -443,7 +444,7 @@ def test_autotune_picks_a_box_and_keeps_results():
     cfg = mpm.mpm_autotune_config(b.ctx)
     assert cfg["grid_blocks"] in (304, 608, 1216, 2432)
     assert cfg["grid_blocks"] == (304, 608, 1216, 2432)[int(np.argmin(cfg["grid_ms_304_608_1216_2432"]))]
-    assert cfg["g2p_stage"] == {"vonmises": 1}  # no tape: G2P staging keeps its default
+    assert cfg["g2p_stage"] == stage0  # no tape: G2P staging is not tuned, it keeps its value
     rews = [b.step(torch.as_tensor(w.actions[t]).cuda()).clone() for t in range(2)]
     st = {k: v.cpu().numpy() for k, v in b.get_state().items()}
     assert rel_err(st["x"], st0["x"]) < 1e-5  # the tuning trials left the state unchanged
@@ -454,6 +455,10 @@ def test_autotune_picks_a_box_and_keeps_results():
     # and the recorded steps and their gradients are unchanged by the trials
     bt = Batch(w.specs, max_steps=2)
     bt.set_inits(w.inits)
+    # a context built after a tuning starts from its choices (kept for the process: the
+    # grid kernels' CTA count, and per material, grid resolution and particles-per-cell
+    # bucket the scatter shape and G2P staging)
+    assert mpm.mpm_autotune_config(bt.ctx)["grid_blocks"] == cfg["grid_blocks"]
     mpm.mpm_autotune(bt.ctx, trials=2)
     cfg = mpm.mpm_autotune_config(bt.ctx)
     plain, staged = cfg["g2p_ms_plain_staged"]["vonmises"]
