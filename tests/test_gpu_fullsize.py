@@ -1,8 +1,10 @@
-"""Parity at full benchmark sizes, in the launch configuration the benchmark times (batched
-direct launches, no graphs): every environment of the batch is stepped on the GPU, and
-sampled environments (the smallest, the largest and one in between) are recomputed one by
-one by the FP64 oracle.  Environments are independent, so a sampled environment's oracle
-run is its exact reference even inside the full batch.
+"""Parity at full benchmark sizes, in the launch configuration the benchmark times: every
+environment of the batch is stepped on the GPU, and sampled environments (the smallest, the
+largest and one in between) are recomputed one by one by the FP64 oracle.  Environments are
+independent, so a sampled environment's oracle run is its exact reference even inside the
+full batch.  The fluid and dough batches run their whole benchmark horizons (16 x 25 and
+32 x 20 substeps) replaying captured CUDA graphs, as the benchmark does; the other batches
+run short horizons with direct launches.
 
 Tolerances: horizon 1e-3 on x and v, rewards 1e-3 relative, gradients 1e-3 relative.
 """
@@ -18,12 +20,12 @@ from gpu_helpers import rel_err, split
 pytestmark = pytest.mark.gpu
 
 
-def run_batch(w, T, grad):
+def run_batch(w, T, grad, use_graphs=False):
     import torch
 
     from paper_2412_12089_gb300.batch import Batch
 
-    b = Batch(w.specs, max_steps=T if grad else 0, use_graphs=False)
+    b = Batch(w.specs, max_steps=T if grad else 0, use_graphs=use_graphs)
     b.set_inits(w.inits)
     rews = []
     for t in range(T):
@@ -62,23 +64,92 @@ def check_env(w, e, T, out, rew, g):
         assert rel_err(split(w, g["xb0"])[e], xb) < 1e-3, (e, "xb0")
 
 
-def test_fullsize_fluid_1024_envs_fwd_adjoint():
-    """1024 fluid envs x 8192 particles, 64^3 grids, one control step of 25 substeps forward
-    and reversed, as in the benchmark."""
-    w = wl.fluid(n_envs=1024, seed=0, T=1)
-    out, rew, g, code = run_batch(w, 1, grad=True)
+# Collider pose offsets at the level of FP32 rounding of the pose (the GPU integrates the
+# pose in FP32): each one is an equally valid reference for a trajectory that passes a point
+# where the result jumps with the pose, such as a grid node on the surface where two of the
+# container's boxes are equally near (the nearest box, and with it the contact normal, switches
+# there).
+POSE_JITTER = [None, (0.0, 0.0, 5e-8), (0.0, 0.0, -5e-8), (5e-8, 0.0, 0.0), (0.0, 5e-8, 0.0)]
+
+
+def _oracle_env(job):
+    """Pool worker: the oracle's rollout (and, with grad, its reverse pass for sum_t r_t) of
+    env e of a workload rebuilt from its maker and arguments, with the collider's initial
+    pose offset by `dq` (or not)."""
+    maker, kw, e, T, grad, dq = job
+    w = getattr(wl, maker)(**kw)
+    s = w.specs[e]
+    sp = orc.make_spec(s)
+    st = orc.State.from_init(w.inits[e])
+    A = s.action_dim
+    acts = w.actions[:T, e, :max(A, 1)].astype(np.float64)
+    q0 = orc.initial_pose(s).copy()
+    if dq is not None:
+        q0[:3] += np.array(dq)
+    o, q, r, status = orc.rollout(sp, st, q0, acts)
+    ag = xb = None
+    if grad and A:
+        ag, (xb, _, _, _), _ = orc.rollout_adj(sp, st, q0, acts[:, :A], rbar=np.ones(T))
+    return e, dq, o.x, o.v, r, status, ag, xb
+
+
+def check_full_horizon(maker, kw, T, grad, envs):
+    """Sampled envs against the oracle at 1e-3.  An env that misses the exact-input reference
+    is accepted only where the oracle itself jumps under FP32-level pose offsets (spread of
+    the offset runs above 1e-4, a discrete switch along the trajectory) and the GPU result
+    then matches one of those equally valid references at 1e-3, gradients included."""
+    from gpu_helpers import oracle_pool
+
+    w = getattr(wl, maker)(**kw)
+    jobs = [(maker, kw, e, T, grad, dq) for e in envs for dq in POSE_JITTER]
+    pool = oracle_pool(len(jobs))
+    try:
+        pending = pool.map_async(_oracle_env, jobs)
+        out, rew, g, code = run_batch(w, T, grad=grad, use_graphs=True)
+        res = pending.get()
+    finally:
+        pool.close()
+        pool.join()
     assert code == 0
-    for e in sampled(w) + [1023]:
-        check_env(w, e, 1, out, rew, g)
+
+    def errors(e, ox, ov, r, ag, xb):
+        er = {"x": rel_err(split(w, out["x"])[e], ox), "v": rel_err(split(w, out["v"])[e], ov),
+              "r": float(np.abs(rew[:, e] - r).max() / max(np.abs(r).max(), 1e-6))}
+        A = w.specs[e].action_dim
+        if ag is not None:
+            er["action"] = rel_err(g["action_grad"][:, e, :A], ag)
+            er["xb0"] = rel_err(split(w, g["xb0"])[e], xb)
+        return er
+
+    for e in envs:
+        runs = [rr for rr in res if rr[0] == e]
+        assert all(rr[5] == 0 for rr in runs)
+        exact = next(rr for rr in runs if rr[1] is None)
+        err = errors(e, exact[2], exact[3], exact[4], exact[6], exact[7])
+        print(f"\nenv {e}: " + " ".join(f"{k} {v:.2e}" for k, v in err.items()))
+        if max(err.values()) < 1e-3:
+            continue
+        spread = max(max(rel_err(rr[3], exact[3]), rel_err(rr[2], exact[2])) for rr in runs)
+        best = min((errors(e, rr[2], rr[3], rr[4], rr[6], rr[7]) for rr in runs), key=lambda d: max(d.values()))
+        print(f"env {e}: oracle spread under FP32-level pose offsets {spread:.2e}; nearest reference: "
+              + " ".join(f"{k} {v:.2e}" for k, v in best.items()))
+        assert spread > 1e-4, (e, err, spread)
+        assert max(best.values()) < 1e-3, (e, best)
+
+
+def test_fullsize_fluid_1024_envs_fwd_adjoint():
+    """The benchmark's batch at its full horizon: 1024 fluid envs x 8192 particles, 64^3
+    grids, 16 control steps of 25 substeps recorded, replayed from captured graphs, and the
+    whole reverse pass; three sampled environments against the oracle's rollout and exact
+    adjoint."""
+    check_full_horizon("fluid", dict(n_envs=1024, seed=0, T=16), 16, True, [0, 511, 1023])
 
 
 def test_fullsize_dough_512_envs_forward():
-    """512 dough envs of 2k-16k particles, 48^3 grids, two control steps of 20 substeps."""
-    w = wl.dough(n_envs=512, seed=0, T=2)
-    out, rew, _, code = run_batch(w, 2, grad=False)
-    assert code == 0
-    for e in sampled(w):
-        check_env(w, e, 2, out, rew, None)
+    """512 dough envs of 2k-16k particles, 48^3 grids, the whole 32 x 20-substep horizon,
+    forward, replayed from captured graphs."""
+    w = wl.dough(n_envs=512, seed=0, T=32)
+    check_full_horizon("dough", dict(n_envs=512, seed=0, T=32), 32, False, sampled(w))
 
 
 def test_fullsize_jumper_64_envs_fwd_adjoint():
