@@ -16,6 +16,13 @@
 // forces f_{c+1} = -V0 (P Dm^-T)[:, c], f_0 = -sum_c f_{c+1}.  Vertices: w = v + dt (f / m + g);
 // at or below the ground and moving down, w_z = 0 and w_t *= max(0, 1 + mu_g w_z / |w_t|);
 // then v = w, x += dt w.  The reverse kernel is the exact adjoint of these steps.
+//
+// Within a control step each position is carried as an unevaluated FP32 sum hi + lo
+// (compensated summation of the x += dt w updates): an update is a few 1e-5 of a position of
+// order 0.5, so a plain FP32 sum would drop most of each update's low bits, and the elements'
+// edge vectors, whose relative changes are the strain, would inherit that error.  The edge
+// vectors are formed from the hi differences (exact for nearby vertices) plus the lo
+// differences.  Positions are rounded to FP32 at control-step ends (the stored state).
 #include <algorithm>
 
 #include "kernels.h"
@@ -53,6 +60,26 @@ __device__ __forceinline__ void edge_mat(const float* P, int ns, int4 t, float* 
 #pragma unroll
     for (int c = 0; c < 3; ++c) D[3 * k + c] = P[k * ns + vi[c]] - p0;
   }
+}
+
+// Edge matrix of positions held as hi + lo: (hi_j - hi_0) + (lo_j - lo_0).
+__device__ __forceinline__ void edge_mat_x(const float* X, const float* XL, int ns, int4 t, float* D) {
+  const int vi[3] = {t.y, t.z, t.w};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float h0 = X[k * ns + t.x], l0 = XL[k * ns + t.x];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      D[3 * k + c] = __fsub_rn(X[k * ns + vi[c]], h0) + __fsub_rn(XL[k * ns + vi[c]], l0);
+  }
+}
+
+// hi + lo += d, keeping hi + lo an unevaluated sum with |lo| <= ulp(hi) / 2 (|d| << |hi|).
+__device__ __forceinline__ void add_compensated(float& hi, float& lo, float d) {
+  const float y = __fadd_rn(d, lo);
+  const float t = __fadd_rn(hi, y);
+  lo = __fsub_rn(y, __fsub_rn(t, hi));
+  hi = t;
 }
 
 __device__ __forceinline__ void mul3(const float* A, const float* B, float* C) {  // C = A B
@@ -154,16 +181,17 @@ __device__ __forceinline__ void gather_corners(const float* T, int nts, const in
   out[2] = a2;
 }
 
-// Corner forces of every element at (X, V) into EF (element stride nts); J <= 0 sets status 4.
-__device__ void element_forces(const EnvDesc& e, const FemLaw& m, const float* act, const float* X, const float* V,
-                               int ns, int nts, float* EF, int& status) {
+// Corner forces of every element at (X + XL, V) into EF (element stride nts); J <= 0 sets
+// status 4.
+__device__ void element_forces(const EnvDesc& e, const FemLaw& m, const float* act, const float* X, const float* XL,
+                               const float* V, int ns, int nts, float* EF, int& status) {
   for (int el = threadIdx.x; el < e.n_tets; el += blockDim.x) {
     const int4 t = e.fem_tet[el];
     const float* Dmi = e.fem_dminv + 9 * el;
     float Dm[9], Ds[9], F[9], P[9], H[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Dm[q] = Dmi[q];
-    edge_mat(X, ns, t, Ds);
+    edge_mat_x(X, XL, ns, t, Ds);
     mul3(Ds, Dm, F);
     const float J = stress(m, F, elem_act(e, act, el), P);
     if (!(J > 0.0f)) status |= 4;
@@ -186,14 +214,15 @@ __device__ __forceinline__ bool on_ground(const EnvDesc& e, float z, const float
 
 // Shared-memory layout of one environment's step (floats; ints share the 4-byte slots).
 struct FemSmem {
-  float *X, *V, *Fv, *XB, *VB, *EA, *EB, *ABE;
+  float *X, *XL, *V, *Fv, *XB, *VB, *EA, *EB, *ABE;
   int *voff, *vinc, *goff, *ginc;
 };
 
 __device__ FemSmem carve(float* sm, int ns, int nts, int gs, bool reverse) {
   FemSmem s;
   s.X = sm;
-  s.V = s.X + 3 * ns;
+  s.XL = s.X + 3 * ns;
+  s.V = s.XL + 3 * ns;
   s.Fv = s.V + 3 * ns;
   float* p = s.Fv + 3 * ns;
   if (reverse) {
@@ -232,7 +261,7 @@ __device__ void stage_incidence(const EnvDesc& e, const FemSmem& s, bool groups)
 
 __device__ void fem_substep(const EnvDesc& e, const FemLaw& m, const float* act, const FemSmem& s, int ns, int nts,
                             int& status) {
-  element_forces(e, m, act, s.X, s.V, ns, nts, s.EA, status);
+  element_forces(e, m, act, s.X, s.XL, s.V, ns, nts, s.EA, status);
   __syncthreads();
   const float dt = e.dt;
   for (int i = threadIdx.x; i < e.n; i += blockDim.x) {
@@ -251,27 +280,37 @@ __device__ void fem_substep(const EnvDesc& e, const FemLaw& m, const float* act,
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       s.V[k * ns + i] = w[k];
-      s.X[k * ns + i] += dt * w[k];
+      add_compensated(s.X[k * ns + i], s.XL[k * ns + i], dt * w[k]);
       if (!isfinite(s.X[k * ns + i])) status |= 2;
     }
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ void load_xv(const float* b, long long np, int nv, int ns, float* X, float* V) {
+// x, v of a state block into shared memory; with XL, the positions' low parts too: from
+// components 6..8 of the block (ring blocks of the reverse pass keep them there), or zero
+// when with_lo is false (a stored state is plain FP32).
+__device__ __forceinline__ void load_xv(const float* b, long long np, int nv, int ns, float* X, float* V,
+                                        float* XL = nullptr, bool with_lo = false) {
   for (int i = threadIdx.x; i < nv; i += blockDim.x)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       X[k * ns + i] = b[k * np + i];
       V[k * ns + i] = b[(3 + k) * np + i];
+      if (XL) XL[k * ns + i] = with_lo ? b[(6 + k) * np + i] : 0.0f;
     }
 }
 
-__device__ __forceinline__ void store_xv(float* b, long long np, int nv, int ns, const float* X, const float* V) {
+// x, v from shared memory into a state block: with XL and keep_lo, the hi parts as x and the
+// low parts in components 6..8 (ring blocks); with XL alone, x rounded from hi + lo.
+__device__ __forceinline__ void store_xv(float* b, long long np, int nv, int ns, const float* X, const float* V,
+                                         const float* XL = nullptr, bool keep_lo = false) {
   for (int i = threadIdx.x; i < nv; i += blockDim.x)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      b[k * np + i] = X[k * ns + i];
+      const float hi = X[k * ns + i];
+      b[k * np + i] = (XL && !keep_lo) ? __fadd_rn(hi, XL[k * ns + i]) : hi;
+      if (XL && keep_lo) b[(6 + k) * np + i] = XL[k * ns + i];
       b[(3 + k) * np + i] = V[k * ns + i];
     }
 }
@@ -289,13 +328,13 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_forward(const EnvDesc* __re
   const float* src = e.slots + (long long)c.live * e.block;
   float* dst = e.slots + (long long)c.next * e.block;
   const float* act = e.act + (long long)c.live * e.A;
-  load_xv(src, np, nv, ns, s.X, s.V);
+  load_xv(src, np, nv, ns, s.X, s.V, s.XL, false);
   stage_incidence(e, s, false);
   __syncthreads();
   const FemLaw m = law_of(e);
   int status = 0;
   for (int k = 0; k < e.S; ++k) fem_substep(e, m, act, s, ns, nts, status);
-  store_xv(dst, np, nv, ns, s.X, s.V);
+  store_xv(dst, np, nv, ns, s.X, s.V, s.XL, false);
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
 #pragma unroll
     for (int q = 6; q < kComp; ++q) dst[q * np + i] = 0.0f;
@@ -323,14 +362,14 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
   const float* act = e.act + (long long)slot * e.A;
   const FemLaw m = law_of(e);
   int status = 0;
-  // recompute substep states 1..S-1 into ring blocks 0..S-2
-  load_xv(src, np, nv, ns, s.X, s.V);
+  // recompute substep states 1..S-1 into ring blocks 0..S-2 (positions as hi and lo)
+  load_xv(src, np, nv, ns, s.X, s.V, s.XL, false);
   stage_incidence(e, s, true);
   for (int el = threadIdx.x; el < e.n_tets; el += blockDim.x) s.ABE[el] = 0.0f;
   __syncthreads();
   for (int k = 0; k + 1 < S; ++k) {
     fem_substep(e, m, act, s, ns, nts, status);
-    store_xv(e.ring + (long long)k * e.block, np, nv, ns, s.X, s.V);
+    store_xv(e.ring + (long long)k * e.block, np, nv, ns, s.X, s.V, s.XL, true);
   }
   const float* adj = c.par ? e.adj1 : e.adj0;
   float* adj_out = c.par ? e.adj0 : e.adj1;
@@ -338,9 +377,9 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
   const float dt = e.dt;
   for (int k = S - 1; k >= 0; --k) {
     // every thread reads back the ring vertices it wrote itself
-    load_xv(k == 0 ? src : e.ring + (long long)(k - 1) * e.block, np, nv, ns, s.X, s.V);
+    load_xv(k == 0 ? src : e.ring + (long long)(k - 1) * e.block, np, nv, ns, s.X, s.V, s.XL, k > 0);
     __syncthreads();
-    element_forces(e, m, act, s.X, s.V, ns, nts, s.EA, status);
+    element_forces(e, m, act, s.X, s.XL, s.V, ns, nts, s.EA, status);
     __syncthreads();
     // vertices: x' = x + dt w passes x-bar through and adds dt x-bar to w-bar; the ground
     // projection; w = v + dt (f / m + g) gives v-bar = w-bar and f-bar = dt w-bar / m
@@ -393,7 +432,7 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
       const float nv0 = -e.fem_vol[el];
 #pragma unroll
       for (int q = 0; q < 9; ++q) Pb[q] *= nv0;
-      edge_mat(s.X, ns, t, Ds);
+      edge_mat_x(s.X, s.XL, ns, t, Ds);
       mul3(Ds, Dm, F);
       stress_adj(m, F, elem_act(e, act, el), Pb, Fb, &ab);
       s.ABE[el] += ab;
@@ -433,7 +472,7 @@ __global__ void __launch_bounds__(kFemThreads) k_fem_reverse(const EnvDesc* __re
 }
 
 size_t fem_smem(int ns, int nts, int gs, bool reverse) {
-  const size_t floats = (reverse ? 15 : 9) * (size_t)ns + (reverse ? 25 : 12) * (size_t)nts;
+  const size_t floats = (reverse ? 18 : 12) * (size_t)ns + (reverse ? 25 : 12) * (size_t)nts;
   const size_t ints = (size_t)ns + 1 + 4 * (size_t)nts + (reverse ? (size_t)gs + 1 + nts : 0);
   return 4 * (floats + ints);
 }
