@@ -1,18 +1,20 @@
 // server.cu -- continuous-batching rollout server (mpm_server_* / mpm_submit / mpm_poll).
 //
 // Requests (an environment spec, its initial state, a horizon of actions, optionally the
-// reward adjoints for a gradient) arrive at any time.  A scheduler thread, per tick:
+// reward adjoints for a gradient) arrive at any time.  A scheduler thread:
 //   1. enqueues one control step of every resident environment in the forward phase (one
-//      launch per stage for all of them, stream A) and one reverse control step of every
-//      environment in the reverse phase (stream B), so the two phases overlap;
+//      launch per stage for all of them, stream A) and, independently, one reverse control
+//      step of every environment in the reverse phase (stream B): each lane starts its next
+//      tick as soon as its last one has finished, so the two phases overlap;
 //   2. while that runs, admits queued requests in arrival order as long as a slot is free
 //      and the memory budget (a fraction of device memory) holds their buffers: their
 //      buffers are carved from the server's device pool and their state, actions and reward
 //      adjoints uploaded on a third stream (C), once, so each whole rollout stays on the
 //      device; they join the resident set at the next tick;
-//   3. waits for the tick, then retires finished requests: rewards, final positions and (if
-//      asked) action gradients go back to host memory, the buffers go back to the pool and
-//      waiters are woken.
+//   3. when a lane's tick has finished, retires its finished requests: rewards, final
+//      positions and (if asked) action gradients go back to host memory, the buffers go back
+//      to the pool and waiters are woken; requests that asked for gradients move from the
+//      forward lane to the reverse lane.
 // The pool grows by cudaMalloc up to the budget and is freed only when the server is
 // destroyed, so admissions and retirements make no cudaMalloc or cudaFree (a cudaFree
 // synchronises the whole device and would stall the streams of the running requests).
@@ -164,7 +166,6 @@ struct mpm_server {
   std::condition_variable cv_work, cv_done;
   std::deque<std::shared_ptr<Req>> pending;
   std::unordered_map<uint64_t, std::shared_ptr<Req>> tickets;
-  std::vector<std::shared_ptr<Req>> resident;  // scheduler thread only
   double used = 0;                             // bytes of resident requests
   bool stop = false;
   std::thread th;
@@ -335,109 +336,163 @@ std::vector<std::shared_ptr<Req>> admit_pending(mpm_server* s, Group& scratch, s
   return admitted;
 }
 
+// Forward and reverse environments run as two lanes, each on its own stream with its own
+// group: a lane enqueues its next tick as soon as its last one has finished, so a long reverse
+// tick does not hold up the forward lane (or the other way round).  Requests whose forward
+// phase ends wait for the reverse lane's next tick to join it; admitted requests join the
+// forward lane at its next tick.
 void scheduler(mpm_server* s) {
   cudaSetDevice(s->device);
   Group scratch;
-  bool layout_changed = true;
-  std::vector<std::shared_ptr<Req>> incoming;  // uploaded, joining at the next tick
+  std::vector<std::shared_ptr<Req>> fw, bw, to_bw, incoming;
+  bool fw_busy = false, bw_busy = false, fw_changed = true, bw_changed = true;
+  cudaEvent_t ev_f = nullptr, ev_b = nullptr;
+  cudaEventCreateWithFlags(&ev_f, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ev_b, cudaEventDisableTiming);
+  auto lanes = [&]() { return fw.size() + bw.size() + to_bw.size(); };
+  auto fail_all = [&](std::vector<std::shared_ptr<Req>>& v, int status) {
+    for (auto& r : v) finish(s, r, status);
+    v.clear();
+  };
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      if (s->resident.empty() && incoming.empty() && s->pending.empty() && !s->stop)
+      if (lanes() == 0 && incoming.empty() && s->pending.empty() && !s->stop)
         s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
       if (s->stop) break;
     }
-    for (auto& r : incoming) {
-      r->phase = 1;
-      r->steps = 0;
-      s->resident.push_back(r);
-      layout_changed = true;
-    }
-    incoming.clear();
-    if (s->resident.empty()) {  // nothing to run: admit, and start at the next tick
-      incoming = admit_pending(s, scratch, 0);
-      continue;
-    }
-    // ---- groups: forward-phase and reverse-phase environments (no work in flight here)
-    std::vector<std::shared_ptr<Req>> fw, bw;
-    for (auto& r : s->resident) (r->phase == 1 ? fw : bw).push_back(r);
-    if (layout_changed) {
-      std::vector<EnvDesc> df, db;
-      std::vector<mpm_env_spec> sf, sbv;
-      for (auto& r : fw) df.push_back(r->desc), sf.push_back(r->spec);
-      for (auto& r : bw) db.push_back(r->desc), sbv.push_back(r->spec);
-      if (group_build(s->gf, df, sf) != cudaSuccess || group_build(s->gb, db, sbv) != cudaSuccess) {
+    // ---- forward lane: bookkeeping of its finished tick, then its next tick
+    if (fw_busy && cudaEventQuery(ev_f) != cudaErrorNotReady) {
+      fw_busy = false;
+      if (cudaEventSynchronize(ev_f) != cudaSuccess) {
         cudaGetLastError();
-        for (auto& r : s->resident) finish(s, r, MPM_ERR_OOM);
-        s->resident.clear();
-        continue;
-      }
-      layout_changed = false;
-    }
-    // ---- one tick: forward step (stream A) and reverse step (stream B) overlap
-    if (!fw.empty()) enqueue_forward(s->gf, s->sf, true, nullptr, s->gf.A_max, nullptr, false);
-    if (!bw.empty()) {
-      for (int e = 0; e < (int)bw.size(); ++e)
-        if (bw[e]->enter_reverse) {
-          const Launch Le = env_launch(s->gb, e, s->sb);
-          launch_bwd_init(Le, bw[e]->T);
-          launch_adj_in(Le, nullptr, nullptr, nullptr, nullptr);
-          bw[e]->enter_reverse = false;
-        }
-      enqueue_reverse(s->gb, s->sb, nullptr, nullptr, s->gb.n_envs, s->gb.A_max, false);
-    }
-    // ---- admissions upload on stream C while the tick runs
-    incoming = admit_pending(s, scratch, s->resident.size());
-    cudaError_t ef = cudaStreamSynchronize(s->sf);
-    cudaError_t eb = cudaStreamSynchronize(s->sb);
-    if (ef != cudaSuccess || eb != cudaSuccess) {
-      cudaGetLastError();
-      for (auto& r : s->resident) finish(s, r, MPM_ERR_CUDA);
-      s->resident.clear();
-      layout_changed = true;
-      continue;
-    }
-    // ---- bookkeeping and retirement
-    std::vector<std::shared_ptr<Req>> keep;
-    for (auto& r : s->resident) {
-      r->steps += 1;
-      bool retire = false;
-      int status = MPM_OK;
-      if (r->phase == 1 && r->steps == r->T) {
-        int bits = 0;
-        if (collect_forward(s, *r, scratch, &bits) != cudaSuccess) {
-          cudaGetLastError();
-          retire = true;
-          status = MPM_ERR_CUDA;
-        } else if (r->grad && !(bits & 6)) {
-          r->phase = 2;
-          r->steps = 0;
-          r->enter_reverse = true;
-          layout_changed = true;
-        } else {
-          retire = true;
-          status = status_of(bits);
-        }
-      } else if (r->phase == 2 && r->steps == r->T) {
-        r->agrad.resize((size_t)r->T * r->A);
-        if (r->A > 0) cudaMemcpy(r->agrad.data(), r->desc.agrad_env, (size_t)r->T * r->A * 4, cudaMemcpyDeviceToHost);
-        EnvCtr c;
-        cudaMemcpy(&c, r->desc.ctr, sizeof c, cudaMemcpyDeviceToHost);
-        retire = true;
-        status = status_of(c.status);
-      }
-      if (retire) {
-        finish(s, r, status);
-        layout_changed = true;
+        fail_all(fw, MPM_ERR_CUDA);
+        fw_changed = true;
       } else {
-        keep.push_back(r);
+        std::vector<std::shared_ptr<Req>> keep;
+        for (auto& r : fw) {
+          if (++r->steps < r->T) {
+            keep.push_back(r);
+            continue;
+          }
+          fw_changed = true;
+          int bits = 0;
+          if (collect_forward(s, *r, scratch, &bits) != cudaSuccess) {
+            cudaGetLastError();
+            finish(s, r, MPM_ERR_CUDA);
+          } else if (r->grad && !(bits & 6)) {
+            r->phase = 2;
+            r->steps = 0;
+            r->enter_reverse = true;
+            to_bw.push_back(r);
+          } else {
+            finish(s, r, status_of(bits));
+          }
+        }
+        fw.swap(keep);
       }
     }
-    s->resident.swap(keep);
+    if (!fw_busy) {
+      for (auto& r : incoming) {
+        r->phase = 1;
+        r->steps = 0;
+        fw.push_back(r);
+        fw_changed = true;
+      }
+      incoming.clear();
+      if (!fw.empty() && fw_changed) {
+        std::vector<EnvDesc> d;
+        std::vector<mpm_env_spec> sp;
+        for (auto& r : fw) d.push_back(r->desc), sp.push_back(r->spec);
+        if (group_build(s->gf, d, sp) != cudaSuccess) {
+          cudaGetLastError();
+          fail_all(fw, MPM_ERR_OOM);
+        }
+        fw_changed = false;
+      }
+      if (!fw.empty()) {
+        enqueue_forward(s->gf, s->sf, true, nullptr, s->gf.A_max, nullptr, false);
+        cudaEventRecord(ev_f, s->sf);
+        fw_busy = true;
+      }
+    }
+    // ---- reverse lane
+    if (bw_busy && cudaEventQuery(ev_b) != cudaErrorNotReady) {
+      bw_busy = false;
+      if (cudaEventSynchronize(ev_b) != cudaSuccess) {
+        cudaGetLastError();
+        fail_all(bw, MPM_ERR_CUDA);
+        bw_changed = true;
+      } else {
+        std::vector<std::shared_ptr<Req>> keep;
+        for (auto& r : bw) {
+          if (++r->steps < r->T) {
+            keep.push_back(r);
+            continue;
+          }
+          bw_changed = true;
+          r->agrad.resize((size_t)r->T * r->A);
+          if (r->A > 0) cudaMemcpy(r->agrad.data(), r->desc.agrad_env, (size_t)r->T * r->A * 4, cudaMemcpyDeviceToHost);
+          EnvCtr c;
+          cudaMemcpy(&c, r->desc.ctr, sizeof c, cudaMemcpyDeviceToHost);
+          finish(s, r, status_of(c.status));
+        }
+        bw.swap(keep);
+      }
+    }
+    if (!bw_busy) {
+      for (auto& r : to_bw) {
+        bw.push_back(r);
+        bw_changed = true;
+      }
+      to_bw.clear();
+      if (!bw.empty() && bw_changed) {
+        std::vector<EnvDesc> d;
+        std::vector<mpm_env_spec> sp;
+        for (auto& r : bw) d.push_back(r->desc), sp.push_back(r->spec);
+        if (group_build(s->gb, d, sp) != cudaSuccess) {
+          cudaGetLastError();
+          fail_all(bw, MPM_ERR_OOM);
+        }
+        bw_changed = false;
+      }
+      if (!bw.empty()) {
+        for (int e = 0; e < (int)bw.size(); ++e)
+          if (bw[e]->enter_reverse) {
+            const Launch Le = env_launch(s->gb, e, s->sb);
+            launch_bwd_init(Le, bw[e]->T);
+            launch_adj_in(Le, nullptr, nullptr, nullptr, nullptr);
+            bw[e]->enter_reverse = false;
+          }
+        enqueue_reverse(s->gb, s->sb, nullptr, nullptr, s->gb.n_envs, s->gb.A_max, false);
+        cudaEventRecord(ev_b, s->sb);
+        bw_busy = true;
+      }
+    }
+    // ---- admissions upload on stream C while the lanes run; then wait for either lane
+    for (;;) {
+      if (incoming.empty()) incoming = admit_pending(s, scratch, lanes());
+      const bool f_done = !fw_busy || cudaEventQuery(ev_f) != cudaErrorNotReady;
+      const bool b_done = !bw_busy || cudaEventQuery(ev_b) != cudaErrorNotReady;
+      if (!fw_busy && !bw_busy) break;  // nothing in flight: back to the top (idle wait)
+      if ((fw_busy && f_done) || (bw_busy && b_done)) break;
+      if (!fw_busy && !incoming.empty()) break;  // the idle forward lane can start them
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) break;
+      }
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
   }
-  for (auto& r : incoming) finish(s, r, MPM_ERR_STATE);
-  for (auto& r : s->resident) finish(s, r, MPM_ERR_STATE);
-  s->resident.clear();
+  cudaStreamSynchronize(s->sf);
+  cudaStreamSynchronize(s->sb);
+  cudaGetLastError();
+  fail_all(incoming, MPM_ERR_STATE);
+  fail_all(fw, MPM_ERR_STATE);
+  fail_all(bw, MPM_ERR_STATE);
+  fail_all(to_bw, MPM_ERR_STATE);
+  if (ev_f) cudaEventDestroy(ev_f);
+  if (ev_b) cudaEventDestroy(ev_b);
   scratch.release();
 }
 
