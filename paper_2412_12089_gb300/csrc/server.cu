@@ -336,6 +336,45 @@ std::vector<std::shared_ptr<Req>> admit_pending(mpm_server* s, Group& scratch, s
   return admitted;
 }
 
+// A lane's tick as a captured CUDA graph while the lane's group stays the same: the first tick
+// after a change runs directly, the second is captured, later ones replay it (the step index
+// and tape positions live in device counters, so a replay advances like a direct launch).
+struct LaneGraph {
+  cudaGraphExec_t exec = nullptr;
+  int stable = 0;  // ticks run since the group last changed
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    stable = 0;
+  }
+  template <class Body>
+  cudaError_t run(bool changed, cudaStream_t st, Body body) {
+    if (changed) reset();
+    if (stable >= 1) {
+      if (!exec) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+          body(st);
+          if (cudaStreamEndCapture(st, &g) == cudaSuccess && g) {
+            if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+          }
+          if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+        if (!exec) {  // capture failed: stay with direct launches for this group
+          stable = -1000000;
+          body(st);
+          return cudaGetLastError();
+        }
+      }
+      return cudaGraphLaunch(exec, st);
+    }
+    body(st);
+    ++stable;
+    return cudaGetLastError();
+  }
+};
+
 // Forward and reverse environments run as two lanes, each on its own stream with its own
 // group: a lane enqueues its next tick as soon as its last one has finished, so a long reverse
 // tick does not hold up the forward lane (or the other way round).  Requests whose forward
@@ -346,6 +385,7 @@ void scheduler(mpm_server* s) {
   Group scratch;
   std::vector<std::shared_ptr<Req>> fw, bw, to_bw, incoming;
   bool fw_busy = false, bw_busy = false, fw_changed = true, bw_changed = true;
+  LaneGraph fg, bg;
   cudaEvent_t ev_f = nullptr, ev_b = nullptr;
   cudaEventCreateWithFlags(&ev_f, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&ev_b, cudaEventDisableTiming);
@@ -400,7 +440,8 @@ void scheduler(mpm_server* s) {
         fw_changed = true;
       }
       incoming.clear();
-      if (!fw.empty() && fw_changed) {
+      const bool rebuilt = !fw.empty() && fw_changed;
+      if (rebuilt) {
         std::vector<EnvDesc> d;
         std::vector<mpm_env_spec> sp;
         for (auto& r : fw) d.push_back(r->desc), sp.push_back(r->spec);
@@ -411,7 +452,11 @@ void scheduler(mpm_server* s) {
         fw_changed = false;
       }
       if (!fw.empty()) {
-        enqueue_forward(s->gf, s->sf, true, nullptr, s->gf.A_max, nullptr, false);
+        if (fg.run(rebuilt, s->sf, [&](cudaStream_t st) {
+              enqueue_forward(s->gf, st, true, nullptr, s->gf.A_max, nullptr, false);
+            }) != cudaSuccess) {
+          cudaGetLastError();
+        }
         cudaEventRecord(ev_f, s->sf);
         fw_busy = true;
       }
@@ -446,7 +491,8 @@ void scheduler(mpm_server* s) {
         bw_changed = true;
       }
       to_bw.clear();
-      if (!bw.empty() && bw_changed) {
+      const bool rebuilt = !bw.empty() && bw_changed;
+      if (rebuilt) {
         std::vector<EnvDesc> d;
         std::vector<mpm_env_spec> sp;
         for (auto& r : bw) d.push_back(r->desc), sp.push_back(r->spec);
@@ -457,6 +503,7 @@ void scheduler(mpm_server* s) {
         bw_changed = false;
       }
       if (!bw.empty()) {
+        // a request's first reverse tick starts its pass (only on ticks after a change)
         for (int e = 0; e < (int)bw.size(); ++e)
           if (bw[e]->enter_reverse) {
             const Launch Le = env_launch(s->gb, e, s->sb);
@@ -464,7 +511,11 @@ void scheduler(mpm_server* s) {
             launch_adj_in(Le, nullptr, nullptr, nullptr, nullptr);
             bw[e]->enter_reverse = false;
           }
-        enqueue_reverse(s->gb, s->sb, nullptr, nullptr, s->gb.n_envs, s->gb.A_max, false);
+        if (bg.run(rebuilt, s->sb, [&](cudaStream_t st) {
+              enqueue_reverse(s->gb, st, nullptr, nullptr, s->gb.n_envs, s->gb.A_max, false);
+            }) != cudaSuccess) {
+          cudaGetLastError();
+        }
         cudaEventRecord(ev_b, s->sb);
         bw_busy = true;
       }
@@ -493,6 +544,8 @@ void scheduler(mpm_server* s) {
   fail_all(to_bw, MPM_ERR_STATE);
   if (ev_f) cudaEventDestroy(ev_f);
   if (ev_b) cudaEventDestroy(ev_b);
+  fg.reset();
+  bg.reset();
   scratch.release();
 }
 
