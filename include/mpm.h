@@ -347,18 +347,18 @@ mpm_status mpm_set_obs_adjoint(mpm_ctx* ctx, const float* obs_adj, void* stream)
  * choices are also kept for the process, per (material, grid resolution, particles per cell
  * rounded to a power of two) and, for the grid kernels, as one CTA count: every context and
  * server group built later starts from them.  The
- * shapes, named by their shared-box capacity: 512 and 1024 nodes for 256-particle CTAs of
- * four warps, 256 nodes for 64-particle CTAs of one warp.  It then tunes the grid kernels
+ * shapes, named by the cell capacity of their per-CTA counting sort: 512 and 1024 cells for
+ * 256-particle CTAs of four warps, 256 cells for 64-particle CTAs of one warp.  It then tunes the grid kernels
  * and G2P (mpm_autotune_config).  The state is not changed.  Call it after mpm_set_state,
  * between steps.
  *   box_out: [4] host, chosen capacity by material (MPM_MAT_*), 0 for absent materials;
- *   ms_out:  [4][3] host, fastest trial's P2G time (ms) per material with 512, 1024 and 256 nodes;
+ *   ms_out:  [4][3] host, fastest trial's P2G time (ms) per material with 512, 1024 and 256 cells;
  *   either may be NULL.  trials in [1, 1000], else MPM_ERR_INVALID_ARG.  Synchronises.
  * Passage: none in the paper (launch-shape tuning of this library).
  */
 mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* ms_out);
 /*
- * The rest of what mpm_autotune chose, after the scatter box and with the same trials (each
+ * The rest of what mpm_autotune chose, after the scatter shape and with the same trials (each
  * trial writes only the grids and, for G2P, the first block of the checkpoint tape's substep
  * ring, which is scratch between reverse passes; without a tape G2P keeps the default):
  *   grid_blocks: CTAs of the persistent grid-update and grid-adjoint kernels, the fastest

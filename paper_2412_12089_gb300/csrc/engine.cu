@@ -385,8 +385,8 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
     if (sa.material != sb.material) return sa.material < sb.material;
     return sa.substeps > sb.substeps;
   });
-  // scatter-box capacity until autotuned; MPM_SCATTER_BOX=512|1024 sets it (tests use it
-  // to run both kernel builds)
+  // scatter shape (cell capacity of its counting sort) until autotuned; MPM_SCATTER_BOX=
+  // 512|1024|256 sets it (tests use it to run every kernel build)
   int box0 = 512;
   if (const char* b = std::getenv("MPM_SCATTER_BOX")) {
     const int v = std::atoi(b);
@@ -621,7 +621,7 @@ cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, TuneTimes* t
     if (e == cudaSuccess) e = cudaEventElapsedTime(t_ms, e0, e1);
     return e;
   };
-  // scatter box, per material: P2G of the live state, then the grid update clears the grid
+  // scatter shape, per material: P2G of the live state, then the grid update clears the grid
   for (size_t mi = 0; mi < g.mats.size() && err == cudaSuccess; ++mi) {
     MatGroup& m = g.mats[mi];
     float best = 0.0f;

@@ -2,16 +2,16 @@
 //
 // One substep of every environment in a batch = three launches over all environments:
 //   P2G  (App. D.3 CPIC step 2): one CTA per work item (a run of up to CHUNK particles of
-//        one environment, consecutive in the binned order).  The CTA accumulates mass and
-//        momentum into a shared-memory box spanning its particles' stencils, then flushes
-//        the box to the dense grid with float4 atomics and marks the touched 4^3 tiles
-//        active (appending them to a device list).
+//        one environment, consecutive in the binned order).  The CTA groups its particles
+//        by cell, sums each cell's mass and momentum per stencil node in registers, adds the
+//        sums to the dense grid with float4 atomics and marks the touched 4^3 tiles active
+//        (appending them to a device list).
 //   GRID (CPIC step 3): persistent warps over the active-tile list; node-local update
 //        (p/m, gravity, softened SDF contact with friction, walls).
 //   G2P  (CPIC step 4): one thread per particle; coalesced SoA reads, 27 float4 grid
 //        gathers through L1, F update and plastic projection, coalesced SoA writes.
-// The adjoint kernels mirror them: G2P^T scatters grid-velocity adjoints with the P2G
-// box scheme, GRID^T is node-local and reduces the collider-pose adjoint per
+// The adjoint kernels mirror them: G2P^T scatters grid-velocity adjoints with P2G's
+// grouped scheme, GRID^T is node-local and reduces the collider-pose adjoint per
 // environment, P2G^T gathers grid adjoints per particle (Sec. 4.1 discrete adjoint).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -144,7 +144,8 @@ __device__ __forceinline__ void load_state(const float* b, long long np, int j, 
   for (int c = 0; c < kComp; ++c) s[c] = b[c * np + j];
 }
 
-// Shared-memory box over a CTA's particle stencils: node (ix,iy,iz) -> box index.
+// Bounding box of a CTA's particle stencils (nodes lx.. lx+nx-1, ...); its cells index the
+// scatter's counting sort.
 struct Box {
   int lx, ly, lz, nx, ny, nz;
 };
@@ -196,26 +197,6 @@ __device__ __forceinline__ void mark_tile(const EnvDesc& e, int env, int ix, int
   }
 }
 
-// Flush a shared box of kNc components into a dense grid with float4 atomics (nodes whose
-// first, or any for adjoints, component is non-zero), marking tiles if requested.
-template <bool kMark, bool kAnyNonzero, int kNc>
-__device__ __forceinline__ void flush_box(const EnvDesc& e, int env, const Box& bx, const float* sv, int stride,
-                                          float4* grid, uint2* active, int* active_n) {
-  int vol = bx.nx * bx.ny * bx.nz;
-  int G = e.G;
-  for (int i = threadIdx.x; i < vol; i += blockDim.x) {
-    float4 val = make_float4(sv[i], sv[stride + i], sv[2 * stride + i], kNc == 4 ? sv[3 * stride + i] : 0.0f);
-    bool nz = kAnyNonzero ? (val.x != 0.0f || val.y != 0.0f || val.z != 0.0f || val.w != 0.0f) : (val.x != 0.0f);
-    if (!nz) continue;
-    int ix = bx.lx + i % bx.nx;
-    int r = i / bx.nx;
-    int iy = bx.ly + r % bx.ny;
-    int iz = bx.lz + r / bx.ny;
-    atomicAdd(grid + ((long long)iz * G + iy) * G + ix, val);
-    if (kMark) mark_tile(e, env, ix, iy, iz, active, active_n);
-  }
-}
-
 __device__ __forceinline__ unsigned cell_pack(int b0, int b1, int b2) {
   return (unsigned)b0 | ((unsigned)b1 << 10) | ((unsigned)b2 << 20);
 }
@@ -226,26 +207,27 @@ __device__ __forceinline__ unsigned cell_pack(int b0, int b1, int b2) {
 //     w_ip (q_p + A_p r_ip)            (r_ip = x_i - x_p)
 // (and w_ip m_p for P2G's mass).  A CTA does it for its chunk of binned particles group by
 // group, a group being the chunk's particles of one cell base (found by a counting sort in
-// shared memory; runs of equal cell base in binned order when the chunk's box is too large).
-// (1) Every particle writes a record to shared memory: q, its offsets g = f dx from the base
-// node, the weights of the three axes and A.  (2) Work units (group, z offset c) sum the
-// group's contributions to the nine nodes base + (0..2, 0..2, c) in registers and add them
-// into a shared-memory box (no two units of a group touch the same node), or, when the
-// chunk's box is too large, straight into the grid with float4 atomics.  Groups are taken in
-// cell order (ordering them by size to balance a warp's lanes cost more than it saved).
-// (3) The box is flushed to the grid with float4 atomics.
+// shared memory; runs of equal cell base in binned order when the chunk's cells outnumber the
+// sort's capacity).  (1) Every particle writes a record to shared memory.  (2) Work units
+// (group, z offset c) sum the group's contributions to the nine nodes base + (0..2, 0..2, c)
+// in registers and add them straight into the grid with float4 atomics: nine per unit, so a
+// node receives one atomic per occupied cell of its stencil instead of one per particle.
+// Groups are taken in cell order (ordering them by size to balance a warp's lanes cost more
+// than it saved).  An earlier version added the units into a shared-memory box of the
+// chunk's nodes and flushed the box to the grid; without the box the kernels need fewer
+// barriers and less shared memory, and G2P^T keeps more L1 for its grid gather.
 
-// Scatter shapes the kernels are built for, by shared-box capacity (nodes): 256-particle
-// chunks on four-warp CTAs with a 512- or 1024-node box, or the same chunks split into four
-// 64-particle CTAs of one warp each with a 256-node box (kScBoxWarp), whose barriers are
-// warp-wide only.  The autotuner picks one per material.  A 256-particle chunk of a dense
-// body spans 150-400 nodes, a 64-particle one 60-200.
+// Scatter shapes the kernels are built for, by the capacity (cells) of the chunk's counting
+// sort: 256-particle chunks on four-warp CTAs sorting up to 512 or 1024 cells, or the same
+// chunks split into four 64-particle CTAs of one warp each sorting up to 256 cells
+// (kScBoxWarp), whose barriers are warp-wide only.  The autotuner picks one per material.  A
+// 256-particle chunk of a dense body spans 40-150 cells, a 64-particle one 15-60.
 constexpr int kScBoxSmall = 512;
 constexpr int kScBoxLarge = 1024;
 constexpr int kScBoxWarp = 256;
 constexpr int kRec = 24;  // floats per particle record
 
-// Threads per CTA of the scatter kernels built for a box capacity.
+// Threads per CTA of the scatter kernels built for a sort capacity.
 template <int kScBox>
 struct ScatterThreads {
   static constexpr int value = kScBox == kScBoxWarp ? 32 : kBlock;
@@ -257,7 +239,7 @@ struct ScatterShared {
   float4 rec[kRec / 4 * NT * kPPT];       // particle records (96 B each): quad j of particle l at
                                           // rec[j * NT * kPPT + l], so the lanes of a warp
                                           // reading different particles hit different banks
-  float box[4 * kScBox];                  // box nodes, component-major
+  unsigned cellcnt[kScBox];               // particles per cell of the chunk, then offsets
   unsigned key[NT * kPPT];                // packed cell base per particle (~0u: none)
   unsigned short gstart[NT * kPPT + 1];   // first particle of each group, then the end
   unsigned short sidx[NT * kPPT];         // grouped position -> particle record
@@ -276,8 +258,9 @@ __device__ __forceinline__ bool scatter_part(const WorkItem& it0, WorkItem& it) 
   return it.count > 0;
 }
 
-// Record quads: (q0 q1 q2 gx) (gy gz wx0 wx1) (wx2 wy0 wy1 wy2) (wz0 wz1 wz2 A00)
-// (A01 A02 A10 A11) (A12 A20 A21 A22), quad j at r[j * kRecStride] (r = rec + particle).
+// G2P^T's record quads: (q0 q1 q2 gx) (gy gz wx0 wx1) (wx2 wy0 wy1 wy2) (wz0 wz1 wz2 A00)
+// (A01 A02 A10 A11) (A12 A20 A21 A22), quad j at r[j * kRecStride] (r = rec + particle), with
+// g = f dx the particle's offset from its base node.
 template <int kRecStride>
 __device__ __forceinline__ void write_record(float4* r, const float* q, const float* g, const float* wx,
                                              const float* wy, const float* wz, const float* A) {
@@ -289,7 +272,26 @@ __device__ __forceinline__ void write_record(float4* r, const float* q, const fl
   r[5 * kRecStride] = make_float4(A[5], A[6], A[7], A[8]);
 }
 
-// Steps (2) and (3), after make_box (whose barriers publish the records and keys).
+// P2G's record quads: (b0 b1 b2 wx0) (wx1 wx2 wy0 wy1) (wy2 wz0 wz1 wz2) (X0 X1 X2 Y0)
+// (Y1 Y2 Z0 Z1) (Z2 - - -), with b = q - A g the value at the base node and X, Y, Z = dx times
+// the columns of A: the value at node base + (a, b, c) is b + a X + b Y + c Z, which the unit
+// loop builds by additions along the stencil.  (G2P^T keeps the record above: its register
+// budget has no room for the extra products.)
+template <int kRecStride>
+__device__ __forceinline__ void write_record_affine(float4* r, const float* q, const float* g, const float* wx,
+                                                    const float* wy, const float* wz, const float* A, float dx) {
+  float bq[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) bq[c] = q[c] - (A[3 * c] * g[0] + A[3 * c + 1] * g[1] + A[3 * c + 2] * g[2]);
+  r[0] = make_float4(bq[0], bq[1], bq[2], wx[0]);
+  r[kRecStride] = make_float4(wx[1], wx[2], wy[0], wy[1]);
+  r[2 * kRecStride] = make_float4(wy[2], wz[0], wz[1], wz[2]);
+  r[3 * kRecStride] = make_float4(dx * A[0], dx * A[3], dx * A[6], dx * A[1]);
+  r[4 * kRecStride] = make_float4(dx * A[4], dx * A[7], dx * A[2], dx * A[5]);
+  r[5 * kRecStride] = make_float4(dx * A[8], 0.f, 0.f, 0.f);
+}
+
+// Step (2), after make_box (whose barriers publish the records and keys).
 // kMass: P2G (mass component m w, tiles marked active); else G2P^T (three components).
 template <bool kMass, int kScBox>
 __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const EnvDesc& e, int env, int count,
@@ -298,27 +300,13 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
                                                int* active_n) {
   constexpr int NT = ScatterThreads<kScBox>::value;
   constexpr int kRecStride = NT * kPPT;
-  const bool fits = sred[3] >= 0 && bx.nx * bx.ny * bx.nz <= kScBox;
   const int cnx = bx.nx - 2, cny = bx.ny - 2;
-  // per cell of the box: particles, then offsets.  It lives in the box's fourth component,
-  // which G2P^T does not use and P2G clears (for its mass) once the sort is done.
-  unsigned* cnt = reinterpret_cast<unsigned*>(sh.box + 3 * kScBox);
+  // the counting sort needs a counter per cell of the chunk's bounding box of cell bases
+  const bool fits = sred[3] >= 0 && cnx * cny * (bx.nz - 2) <= kScBox;
+  unsigned* cnt = sh.cellcnt;  // per cell: particles, then offsets
   if (fits) {
-    const int vol = bx.nx * bx.ny * bx.nz, cvol = cnx * cny * (bx.nz - 2);
-    for (int q = threadIdx.x; q < vol; q += NT) {
-      sh.box[q] = 0.f;
-      sh.box[kScBox + q] = 0.f;
-      sh.box[2 * kScBox + q] = 0.f;
-    }
+    const int cvol = cnx * cny * (bx.nz - 2);
     for (int q = threadIdx.x; q < cvol; q += NT) cnt[q] = 0u;
-  } else if (kMass) {
-#pragma unroll
-    for (int p = 0; p < kPPT; ++p)
-      if (valid[p])
-        for (int cz = 0; cz < 3; cz += 2)
-          for (int cy = 0; cy < 3; cy += 2)
-            for (int cx = 0; cx < 3; cx += 2)
-              mark_tile(e, env, base[p][0] + cx, base[p][1] + cy, base[p][2] + cz, active, active_n);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int ngrp = 0;
@@ -395,11 +383,6 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
     for (int q = 0; q < kPPT * (NT / 32); ++q) ngrp += sh.seg[q];
   }
   if (threadIdx.x == 0) sh.gstart[ngrp] = (unsigned short)count;
-  __syncthreads();  // the grouped positions are written (they read the counts) before the clear
-  if (kMass && fits) {  // the cell counts are no longer read: clear the mass component
-    const int vol = bx.nx * bx.ny * bx.nz;
-    for (int q = threadIdx.x; q < vol; q += NT) sh.box[3 * kScBox + q] = 0.f;
-  }
   __syncthreads();
   const float dx = e.dx;
   // units: (group, z offset c), each summing the nine nodes base + (0..2, 0..2, c)
@@ -409,7 +392,11 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
     const int q0 = sh.gstart[g], q1 = sh.gstart[g + 1];
     const unsigned key = sh.key[sh.sidx[q0]];
     const int cx = (int)(key & 1023u), cy = (int)((key >> 10) & 1023u), cz = (int)(key >> 20);
-    const float cdx = (float)oc * dx;
+    // P2G: one unit per group marks the tiles of the group's stencil (those of its corners)
+    if (kMass && oc == 0)
+      for (int mz = 0; mz < 3; mz += 2)
+        for (int my = 0; my < 3; my += 2)
+          for (int mx = 0; mx < 3; mx += 2) mark_tile(e, env, cx + mx, cy + my, cz + mz, active, active_n);
     float am[3][3], ap[3][3][3];
 #pragma unroll
     for (int ob = 0; ob < 3; ++ob)
@@ -418,60 +405,79 @@ __device__ __forceinline__ void scatter_groups(ScatterShared<kScBox>& sh, const 
         am[ob][a] = 0.f;
         ap[ob][a][0] = ap[ob][a][1] = ap[ob][a][2] = 0.f;
       }
-    for (int q = q0; q < q1; ++q) {
-      const float4* r = sh.rec + sh.sidx[q];
-      const float4 r0 = r[0], r1 = r[kRecStride], r2 = r[2 * kRecStride], r3 = r[3 * kRecStride],
-                   r4 = r[4 * kRecStride], r5 = r[5 * kRecStride];
-      const float wzc = oc == 0 ? r3.x : (oc == 1 ? r3.y : r3.z);
-      const float rz = cdx - r1.y;
-      const float tz0 = r0.x + r4.y * rz, tz1 = r0.y + r5.x * rz, tz2 = r0.z + r5.w * rz;
-      const float wya[3] = {r2.y, r2.z, r2.w};
-      const float wxa[3] = {r1.z, r1.w, r2.x};
-      float rxa[3];
+    if (kMass) {
+      const float ocf = (float)oc;
+      for (int q = q0; q < q1; ++q) {
+        const float4* r = sh.rec + sh.sidx[q];
+        const float4 r0 = r[0], r1 = r[kRecStride], r2 = r[2 * kRecStride], r3 = r[3 * kRecStride],
+                     r4 = r[4 * kRecStride];
+        const float z2 = reinterpret_cast<const float*>(r + 5 * kRecStride)[0];
+        const float wzc = oc == 0 ? r2.y : (oc == 1 ? r2.z : r2.w);
+        const float wya[3] = {r1.z, r1.w, r2.x};
+        const float wxa[3] = {r0.w, r1.x, r1.y};
+        // values along the stencil: b, plus c Z for the layer, b Y for the row, a X per node
+        float t0 = r0.x + ocf * r4.z, t1 = r0.y + ocf * r4.w, t2 = r0.z + ocf * z2;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) rxa[a] = (float)a * dx - r0.w;
+        for (int ob = 0; ob < 3; ++ob) {
+          if (ob > 0) {
+            t0 += r3.w;
+            t1 += r4.x;
+            t2 += r4.y;
+          }
+          const float wyz = wya[ob] * wzc;
+          float u0 = t0, u1 = t1, u2 = t2;
 #pragma unroll
-      for (int ob = 0; ob < 3; ++ob) {
-        const float ry = (float)ob * dx - r1.x;
-        const float wyz = wya[ob] * wzc;
-        const float t0 = tz0 + r4.x * ry, t1 = tz1 + r4.w * ry, t2 = tz2 + r5.z * ry;
+          for (int a = 0; a < 3; ++a) {
+            if (a > 0) {
+              u0 += r3.x;
+              u1 += r3.y;
+              u2 += r3.z;
+            }
+            const float wt = wxa[a] * wyz;
+            am[ob][a] += wt;
+            ap[ob][a][0] += wt * u0;
+            ap[ob][a][1] += wt * u1;
+            ap[ob][a][2] += wt * u2;
+          }
+        }
+      }
+    } else {
+      const float cdx = (float)oc * dx;
+      for (int q = q0; q < q1; ++q) {
+        const float4* r = sh.rec + sh.sidx[q];
+        const float4 r0 = r[0], r1 = r[kRecStride], r2 = r[2 * kRecStride], r3 = r[3 * kRecStride],
+                     r4 = r[4 * kRecStride], r5 = r[5 * kRecStride];
+        const float wzc = oc == 0 ? r3.x : (oc == 1 ? r3.y : r3.z);
+        const float rz = cdx - r1.y;
+        const float tz0 = r0.x + r4.y * rz, tz1 = r0.y + r5.x * rz, tz2 = r0.z + r5.w * rz;
+        const float wya[3] = {r2.y, r2.z, r2.w};
+        const float wxa[3] = {r1.z, r1.w, r2.x};
+        float rxa[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float wt = wxa[a] * wyz;
-          if (kMass) am[ob][a] += wt;
-          ap[ob][a][0] += wt * (t0 + r3.w * rxa[a]);
-          ap[ob][a][1] += wt * (t1 + r4.z * rxa[a]);
-          ap[ob][a][2] += wt * (t2 + r5.y * rxa[a]);
+        for (int a = 0; a < 3; ++a) rxa[a] = (float)a * dx - r0.w;
+#pragma unroll
+        for (int ob = 0; ob < 3; ++ob) {
+          const float ry = (float)ob * dx - r1.x;
+          const float wyz = wya[ob] * wzc;
+          const float t0 = tz0 + r4.x * ry, t1 = tz1 + r4.w * ry, t2 = tz2 + r5.z * ry;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float wt = wxa[a] * wyz;
+            ap[ob][a][0] += wt * (t0 + r3.w * rxa[a]);
+            ap[ob][a][1] += wt * (t1 + r4.z * rxa[a]);
+            ap[ob][a][2] += wt * (t2 + r5.y * rxa[a]);
+          }
         }
       }
     }
 #pragma unroll
     for (int ob = 0; ob < 3; ++ob) {
-      if (fits) {
-        const int row = ((cz + oc - bx.lz) * bx.ny + (cy + ob - bx.ly)) * bx.nx + (cx - bx.lx);
-        constexpr int o = kMass ? 1 : 0;
+      float4* gp = grid + ((long long)(cz + oc) * e.G + (cy + ob)) * e.G + cx;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          if (kMass) atomicAdd(&sh.box[row + a], am[ob][a] * pm);
-          atomicAdd(&sh.box[o * kScBox + row + a], ap[ob][a][0]);
-          atomicAdd(&sh.box[(o + 1) * kScBox + row + a], ap[ob][a][1]);
-          atomicAdd(&sh.box[(o + 2) * kScBox + row + a], ap[ob][a][2]);
-        }
-      } else {
-        float4* gp = grid + ((long long)(cz + oc) * e.G + (cy + ob)) * e.G + cx;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-          atomicAdd(gp + a, kMass ? make_float4(am[ob][a] * pm, ap[ob][a][0], ap[ob][a][1], ap[ob][a][2])
-                                  : make_float4(ap[ob][a][0], ap[ob][a][1], ap[ob][a][2], 0.f));
-      }
+      for (int a = 0; a < 3; ++a)
+        atomicAdd(gp + a, kMass ? make_float4(am[ob][a] * pm, ap[ob][a][0], ap[ob][a][1], ap[ob][a][2])
+                                : make_float4(ap[ob][a][0], ap[ob][a][1], ap[ob][a][2], 0.f));
     }
-  }
-  if (fits) {
-    __syncthreads();
-    if (kMass)
-      flush_box<true, false, 4>(e, env, bx, sh.box, kScBox, grid, active, active_n);
-    else
-      flush_box<false, true, 3>(e, env, bx, sh.box, kScBox, grid, nullptr, nullptr);
   }
 }
 
@@ -540,7 +546,7 @@ __global__ void __launch_bounds__(ScatterThreads<BOX>::value, BOX == kScBoxWarp 
     bspline(f2, wz, dw);
     const float mv[3] = {pm * s[3], pm * s[4], pm * s[5]};
     const float g[3] = {f0 * dx, f1 * dx, f2 * dx};
-    write_record<NT * kPPT>(sh.rec + l, mv, g, wx, wy, wz, A);
+    write_record_affine<NT * kPPT>(sh.rec + l, mv, g, wx, wy, wz, A, dx);
   }
   if (oob) atomicOr(&e.ctr->status, 1);
   const Box bx = make_box(base, valid, sred);
@@ -1955,8 +1961,10 @@ LaunchScope::~LaunchScope() {
 
 static inline int nblk(int n, int b) { return (n + b - 1) / b; }
 
-// Six P2G CTAs per SM need the largest shared-memory carveout (the gather-heavy kernels keep
-// the default, which leaves more L1 for their grid reads).
+// Six P2G CTAs per SM need the largest shared-memory carveout (P2G reads nothing twice).
+// The gather kernels keep the default, which leaves more L1 for their grid reads: G2P^T, at
+// four CTAs per SM, ran 12% slower with the carveout forced to 196 KB (five CTAs) or 228 KB,
+// and 6% slower at three CTAs with more L1.
 template <int BOX>
 static void p2g_carveout(int pct) {
   cudaFuncSetAttribute(k_p2g<MAT_NEOHOOKEAN, BOX>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);

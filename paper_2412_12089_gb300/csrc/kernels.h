@@ -36,8 +36,8 @@ struct Launch {
   int grid_blocks;       // CTAs of the persistent grid kernels
   int env0, n_env;       // environment range of the per-env kernels
   cudaStream_t stream;
-  int sc_box = 512;      // scatter shape by shared-box capacity (nodes): 512 or 1024 (256-particle
-                         // CTAs of four warps) or 256 (64-particle CTAs of one warp)
+  int sc_box = 512;      // scatter shape by the cell capacity of its counting sort: 512 or 1024
+                         // (256-particle CTAs of four warps) or 256 (64-particle CTAs of one warp)
   int wait_polls = -1;   // polls of G2P's first wait on its staged copies (< 0: the full limit)
   int g2p_stage = 1;     // G2P stages a chunk's x and H by bulk copies (when read in place)
 };

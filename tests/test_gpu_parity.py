@@ -407,9 +407,9 @@ def test_gradients_mixed_batch_grid_tape(tape_tiles, monkeypatch):
 
 @pytest.mark.parametrize("box", ["512", "1024", "256"])
 def test_scatter_box_builds_match_oracle(box, monkeypatch):
-    """Every scatter shape (512- and 1024-node boxes on 256-particle four-warp CTAs, the
-    256-node box on 64-particle one-warp CTAs) of the scatter kernels (P2G forward, G2P^T in
-    reverse) gives the oracle's substep and gradients."""
+    """Every scatter shape (512- and 1024-cell counting sorts on 256-particle four-warp CTAs,
+    the 256-cell sort on 64-particle one-warp CTAs) of the scatter kernels (P2G forward, G2P^T
+    in reverse) gives the oracle's substep and gradients."""
     monkeypatch.setenv("MPM_SCATTER_BOX", box)
     T = 1
     w = small("dough", seed=15, substeps=3, T=T, n_envs=2, n_range=(500, 3000))
@@ -424,6 +424,32 @@ def test_scatter_box_builds_match_oracle(box, monkeypatch):
         ag, (xb, vb, Cb, Fb), qb = orc.rollout_adj(sp, so, np.array(s.pose0, np.float64),
                                                    w.actions[:T, e, :A].astype(np.float64), rbar=np.ones(T))
         assert rel_err(g["action_grad"][:, e, :A], ag) < 1e-3
+
+
+@pytest.mark.parametrize("box", ["512", "256"])
+def test_sparse_cloud_groups_by_runs(box, monkeypatch):
+    """Particles scattered thinly (about 0.1 per cell) over most of the domain, so a chunk's
+    cells outnumber its counting sort's capacity and the scatter kernels group the chunk by
+    runs of equal cell base in binned order instead, marking tiles per run: two substeps and
+    the gradient of sum |x_T - x*|^2 against the oracle."""
+    monkeypatch.setenv("MPM_SCATTER_BOX", box)
+    n = 1500
+    w = small("cube", seed=21, n=n, G=32, substeps=2, T=1)
+    rng = np.random.default_rng(21)
+    w.inits[0].x = (0.15 + 0.7 * rng.random((n, 3))).astype(np.float32)
+    w = perturb(w, seed=22)
+    x0 = w.inits[0].x.astype(np.float64)
+    target = x0 + np.array([0.02, 0.0, 0.0])
+    g, st = _gpu_grads(w, 1, xbT=lambda xT: (2.0 * (xT - target)).astype(np.float32))
+    oT, _, _ = oracle_run(w, 0, 1)
+    xs = st["x"].cpu().numpy()
+    assert rel_err(xs, oT.x) < 1e-4, rel_err(xs, oT.x)  # two substeps
+    sp = orc.make_spec(w.specs[0])
+    so = orc.State.from_init(w.inits[0])
+    ag, (xb, vb, Cb, Fb), qb = orc.rollout_adj(sp, so, np.zeros(4), np.zeros((1, 1)),
+                                               adj_final=(2.0 * (oT.x - target), None, None, None))
+    for name, got, ref in (("x", g["xb0"], xb), ("v", g["vb0"], vb), ("C", g["Cb0"], Cb), ("F", g["Fb0"], Fb)):
+        assert rel_err(got, ref) < 1e-3, (name, rel_err(got, ref))
 
 
 def test_autotune_picks_a_box_and_keeps_results():
