@@ -54,8 +54,8 @@ MEASURED_TRAFFIC = {
     # ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of launches over 2,097,152
     # binned fluid particles (256 envs x 8192, 64^3; state 210 MB, above L2), in bytes per
     # particle, scaled by particle count
-    "g2p_adj": (210.2, "be5d8ba9f948872c"),  # 512-node box, mean of 2 adjoint-substep launches
-    "p2g": (95.4, "be5d8ba9f948872c"),       # 512-node box, mean of 18 launches
+    "g2p_adj": (210.9, "55fed9c2f11a821b"),  # 512-cell sort, mean of 2 adjoint-substep launches
+    "p2g": (95.4, "55fed9c2f11a821b"),       # 512-cell sort, mean of 18 launches
 }
 
 
@@ -610,10 +610,10 @@ def main():
     for i in range(args.warmup):
         one_step()
         if i == 0:
-            # autotune the scatter kernels' shared-box capacity on a binned state (the captured
+            # autotune the scatter kernels' shape on a binned state (the captured
             # graphs are dropped and captured again with the choice)
             chosen, p2g_ms = mpm.mpm_autotune(b.ctx, trials=3)
-            tuned = {"scatter_box_nodes": chosen, "p2g_trial_ms_512_1024_256w": p2g_ms, **mpm.mpm_autotune_config(b.ctx)}
+            tuned = {"scatter_shape_cells": chosen, "p2g_trial_ms_512_1024_256w": p2g_ms, **mpm.mpm_autotune_config(b.ctx)}
     torch.cuda.synchronize()
     tiles = max(mpm.mpm_last_active_tiles(b.ctx), 0)
 
