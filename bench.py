@@ -558,6 +558,8 @@ def main():
     ap.add_argument("--jumper-envs", type=int, default=64, help="envs of the 100k-particle jumper leg (0 = off)")
     ap.add_argument("--no-direct", action="store_true", help="skip the direct-launch (no graphs) timing")
     ap.add_argument("--no-legs", action="store_true", help="skip the cube (C1) and dough (C2) legs")
+    ap.add_argument("--keep-fraction", type=float, default=0.0,
+                    help="mpm_options.keep_fraction of the benchmarked batch (0: the library's default, < 0: keep none)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -586,7 +588,7 @@ def main():
     # ---- workload: env shard of this rank (weak scaling: every rank runs a full batch)
     w = wl.fluid(n_envs=args.envs, n=args.particles, seed=1000 * rank, T=args.control_steps, substeps=args.substeps)
     T, S, P = w.T, w.specs[0].substeps, w.n_particles
-    b = Batch(w.specs, max_steps=T, use_graphs=True, device=local)
+    b = Batch(w.specs, max_steps=T, use_graphs=True, device=local, keep_fraction=args.keep_fraction)
     xs = {k: torch.as_tensor(np.concatenate([getattr(i, k) for i in w.inits])).to(dev) for k in ("x", "v", "C", "F")}
     poses = torch.as_tensor(np.array([s.pose0 for s in w.specs], np.float32)).to(dev)
     acts = torch.as_tensor(w.actions).to(dev)
@@ -616,6 +618,8 @@ def main():
             tuned = {"scatter_shape_cells": chosen, "p2g_trial_ms_512_1024_256w": p2g_ms, **mpm.mpm_autotune_config(b.ctx)}
     torch.cuda.synchronize()
     tiles = max(mpm.mpm_last_active_tiles(b.ctx), 0)
+    kept_steps = mpm.mpm_kept_steps(b.ctx)  # recorded steps whose substep states are kept
+    device_gb = mpm.mpm_device_bytes(b.ctx) / 1e9
 
     # ---- timed region: the rollouts replay captured CUDA graphs, no per-launch events
     stream = torch.cuda.current_stream()
@@ -740,7 +744,7 @@ def main():
     # ---- the same rollouts with direct launches (no graphs, no events), a second number
     direct = None
     if not args.no_direct:
-        bd = Batch(w.specs, max_steps=T, use_graphs=False, device=local)
+        bd = Batch(w.specs, max_steps=T, use_graphs=False, device=local, keep_fraction=args.keep_fraction)
         b = bd
         one_step()
         mpm.mpm_autotune(bd.ctx, trials=3)
@@ -797,7 +801,7 @@ def main():
                        "control_steps": T, "substeps": S, "parallelism": f"env-shard x{world}",
                        "l2": "inputs larger than L2 (state and grids > 129 MB per pass)",
                        "launch": "captured CUDA graphs replayed per control step and per reverse step",
-                       "autotuned": tuned},
+                       "autotuned": tuned, "kept_steps": kept_steps, "device_gb": round(device_gb, 1)},
             "direct_launch": direct,
             "legs": legs,
             "rollout_ms": {"p50": step_ms[len(step_ms) // 2], "p99": step_ms[-1], "what": "one batched fwd+adjoint rollout"},

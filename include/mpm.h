@@ -151,6 +151,14 @@ typedef struct {
     float grid_tape_fraction; /* share of the device's free memory (after the arena) that the
                                  grid tape may take: recorded steps keep every substep's grid
                                  so the reverse pass need not rebuild it; 0 = 0.5, < 0 = none */
+    float keep_fraction;      /* share of the device's free memory after the grid tape (less
+                                 this context's staging buffers) that kept substep states may
+                                 take: each recorded step writes its substep states there (step
+                                 t in slot t mod n, n = the whole steps that fit, at most
+                                 max_steps), and the reverse pass of the last n recorded steps
+                                 reads them instead of recomputing them from the step's
+                                 checkpoint; needs the grid tape; 0 = 0.8, < 0 = none.  Callers
+                                 built against the header without this field must zero it. */
 } mpm_options;
 
 typedef struct mpm_ctx mpm_ctx;
@@ -179,6 +187,11 @@ int64_t mpm_n_particles(const mpm_ctx* ctx);
 int32_t mpm_action_dim(const mpm_ctx* ctx);
 int32_t mpm_tape_length(const mpm_ctx* ctx);
 int64_t mpm_device_bytes(const mpm_ctx* ctx);
+/* Recorded control steps whose substep states the context keeps (mpm_options.keep_fraction):
+ * the reverse pass skips the recompute of the last this many.  0 for a NULL context.
+ * Passage: Sec. 4.1 (checkpoints at control-step boundaries, substeps recomputed in reverse);
+ *   keeping them instead, where memory allows, is this library's trade of memory for time. */
+int32_t mpm_kept_steps(const mpm_ctx* ctx);
 /* Text of the last failure of a call on this context ("" if none); owned by the context,
  * valid until its next call.
  * Passage: none in the paper (error reporting of the C ABI). */

@@ -21,14 +21,14 @@ def _torch():
 
 
 class Batch:
-    def __init__(self, specs, max_steps=0, per_env_launch=False, use_graphs=True, device=0):
+    def __init__(self, specs, max_steps=0, per_env_launch=False, use_graphs=True, device=0, keep_fraction=0.0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("Batch needs a CUDA device")
         self.specs = list(specs)
         self.device = torch.device("cuda", device)
         self.ctx = mpm.mpm_create(self.specs, max_steps=max_steps, per_env_launch=per_env_launch,
-                                  use_graphs=use_graphs, device=device)
+                                  use_graphs=use_graphs, device=device, keep_fraction=keep_fraction)
         L = mpm.lib()
         self.n_envs = L.mpm_n_envs(self.ctx)
         self.P = L.mpm_n_particles(self.ctx)

@@ -294,7 +294,7 @@ void env_fill(EnvDesc& d, const mpm_env_spec& s, const EnvLayout& L, char* base,
 
 void Group::release() {
   void* ptrs[] = {d_desc, d_items, d_items_env, active, active_n, sort.keys[0], sort.keys[1], sort.vals[0],
-                  sort.vals[1], sort.hist, tape.mp, tape.list, tape.slot, tape.cursor, d_fem};
+                  sort.vals[1], sort.hist, tape.mp, tape.list, tape.slot, tape.cursor, d_fem, keep};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d_desc = nullptr;
@@ -308,6 +308,9 @@ void Group::release() {
   tape_mp_cap = tape_list_cap = tape_slot_cap = tape_cursor_cap = 0;
   d_fem = nullptr;
   fem_cap = 0;
+  keep = nullptr;
+  keep_cap = 0;
+  keep_n = 0;
 }
 
 namespace {
@@ -464,10 +467,12 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
   }
   g.tape.cap = 0;
   if (g.want_tape && g.tape_T > 0 && g.tape_budget > 0.0 && g.S_max > 0) {
-    // pool: the budget, or 1.5x a generous estimate of the active tiles (P/32 + 1024 per
-    // substep) when that is smaller; MPM_GRID_TAPE_TILES caps it (tests make it overflow)
+    // pool: the budget, or 1.5x a generous estimate of the active tiles (P/64 + 1024 per
+    // substep: a dense body at eight particles per cell fills about P/130) when that is
+    // smaller, so the memory it would not use goes to kept substep states; a substep whose
+    // tiles do not fit is rebuilt by P2G.  MPM_GRID_TAPE_TILES caps it (tests make it overflow)
     constexpr double kTileBytes = 64.0 * sizeof(float4) + sizeof(uint2);
-    const double est = 1.5 * (double)g.tape_T * g.S_max * ((double)g.P / 32.0 + 1024.0);
+    const double est = 1.5 * (double)g.tape_T * g.S_max * ((double)g.P / 64.0 + 1024.0);
     long long tiles = (long long)std::min(g.tape_budget / kTileBytes, est);
     if (const char* cap = std::getenv("MPM_GRID_TAPE_TILES")) {
       const long long c = std::atoll(cap);
@@ -488,6 +493,41 @@ cudaError_t group_build(Group& g, const std::vector<EnvDesc>& descs, const std::
       cudaGetLastError();  // the tape is an optimisation: run without it
     }
   }
+  // kept substep states: as many recorded steps as keep_frac of the memory left after the tape
+  // (less keep_reserve) holds, at most tape_T; only with a grid tape (which the reverse pass's
+  // adjoint substeps still need)
+  g.keep_n = 0;
+  size_t per_step = 0;  // floats: every particle environment's S - 1 blocks
+  for (int i = 0; i < g.n_envs; ++i)
+    if (specs[i].material != kMatFem && specs[i].substeps > 1)
+      per_step += (size_t)(specs[i].substeps - 1) * (size_t)g.desc[i].block;
+  if (g.tape.cap > 0 && g.keep_frac > 0.0 && g.tape_T > 0 && per_step > 0) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+    const double budget = g.keep_frac * std::max(0.0, (double)free_b - g.keep_reserve);
+    long long n = std::min<long long>((long long)(budget / (4.0 * (double)per_step)), g.tape_T);
+    if (const char* ks = std::getenv("MPM_KEEP_STEPS")) {
+      const long long c = std::atoll(ks);
+      if (c >= 0) n = std::min(n, c);
+    }
+    if (n > 0 && ensure_exact(g.keep, g.keep_cap, (size_t)n * per_step) == cudaSuccess)
+      g.keep_n = (int)n;
+    else
+      cudaGetLastError();  // an optimisation too: recompute every step without it
+  }
+  // environment i's keep_n slots follow those of the environments before it
+  size_t off = 0;
+  bool any = false;
+  for (int i = 0; i < g.n_envs; ++i) {
+    EnvDesc& d = g.desc[i];
+    const bool k = g.keep_n > 0 && specs[i].material != kMatFem && specs[i].substeps > 1;
+    any = any || d.keep_n != 0 || k;
+    d.keep = k ? g.keep + off : nullptr;
+    d.keep_n = k ? g.keep_n : 0;
+    if (k) off += (size_t)g.keep_n * (size_t)(specs[i].substeps - 1) * (size_t)d.block;
+  }
+  if (any && g.n_envs && (e = cudaMemcpy(g.d_desc, g.desc.data(), sizeof(EnvDesc) * g.n_envs, cudaMemcpyHostToDevice)))
+    return e;
   return cudaSuccess;
 }
 
@@ -534,11 +574,14 @@ Launch mat_launch(const Launch& L, const MatGroup& m, int k) {
 }
 
 // tape: record every substep's grid into the grid tape (recorded steps), or NULL.
-void substeps_forward(const Launch& L, const std::vector<MatGroup>& mats, int S, const GridTape* tape) {
+// record: the step is recorded; its substep states go to the kept slots when the environment
+// keeps states (REF_FWDK), else substeps run in place in the next slot.
+void substeps_forward(const Launch& L, const std::vector<MatGroup>& mats, int S, const GridTape* tape,
+                      bool record) {
   for (int k = 0; k < S; ++k) {
     cudaMemsetAsync(L.active_n, 0, sizeof(int), L.stream);
-    const StateRef src{k == 0 ? REF_LIVE : REF_NEXT, k};
-    const StateRef dst{REF_NEXT, k};
+    const StateRef src = record ? StateRef{REF_FWDK, k} : StateRef{k == 0 ? REF_LIVE : REF_NEXT, k};
+    const StateRef dst = record ? StateRef{REF_FWDK, k + 1} : StateRef{REF_NEXT, k};
     for (auto& m : mats) launch_p2g(mat_launch(L, m, k), src, k == 0, k);
     if (tape) launch_tape_alloc(L, *tape, k);
     launch_grid(L, k, GRID_FWD, false, tape);
@@ -553,19 +596,22 @@ struct FemList {
   int n = 0, nv_max = 0, act_max = 0, nt_max = 0;
 };
 
+// kept: the step's substep states were kept by the forward pass, so they are not recomputed.
 void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, const float* rbar, float* agrad,
-                  int n_tot, int a_max, const GridTape* tape, const ObsAdj* obs, const FemList& fem) {
+                  int n_tot, int a_max, const GridTape* tape, const ObsAdj* obs, const FemList& fem,
+                  bool kept = false) {
   launch_rev_begin(L);
   launch_reward_adj(L, rbar, n_tot);
   if (obs) launch_obs_adj(L, *obs, 0);  // observation of the step's end state
   launch_adj_ref(L);
   launch_fem_reverse(L, fem.list, fem.n, fem.nv_max, fem.act_max, fem.nt_max);
-  // recompute substep states 1..S-1 into the ring (envs with S > k + 1); the grid of each
-  // substep comes from the tape when it was kept, else P2G rebuilds it
-  for (int k = 0; k + 1 < S; ++k) {
+  // recompute substep states 1..S-1 into the ring (envs with S > k + 1), unless the forward
+  // pass kept them; the grid of each substep comes from the tape when it was kept, else P2G
+  // rebuilds it
+  for (int k = 0; !kept && k + 1 < S; ++k) {
     cudaMemsetAsync(L.active_n, 0, sizeof(int), L.stream);
-    const StateRef src{k == 0 ? REF_REV : REF_RING, k};
-    const StateRef dst{REF_RING, k + 1};
+    const StateRef src{REF_REVK, k};
+    const StateRef dst{REF_REVK, k + 1};
     if (tape) launch_restore(L, *tape, k);
     for (auto& m : mats) launch_p2g(mat_launch(L, m, k + 1), src, k == 0, k, tape);
     launch_grid(L, k, GRID_FWD, true);
@@ -574,27 +620,13 @@ void reverse_step(const Launch& L, const std::vector<MatGroup>& mats, int S, con
   // adjoint substeps, last to first (envs with S > k)
   for (int k = S - 1; k >= 0; --k) {
     cudaMemsetAsync(L.active_n, 0, sizeof(int), L.stream);
-    const StateRef src{k == 0 ? REF_REV : REF_RING, k};
+    const StateRef src{REF_REVK, k};
     if (tape) launch_restore(L, *tape, k);
     for (auto& m : mats) launch_p2g(mat_launch(L, m, k), src, k == 0, k, tape);
     launch_grid(L, k, GRID_KEEP, true);
-    // the end state of substep k: ring block k+1 for envs with S > k+1 (a prefix of the
-    // material's items), the step's end checkpoint for envs whose last substep is k
-    for (auto& m : mats) {
-      const Launch Lm = mat_launch(L, m, k);
-      const int n_ring = m.n_gt[std::min(k + 1, (int)m.n_gt.size() - 1)];
-      if (n_ring > 0) {
-        Launch La = Lm;
-        La.n_items = n_ring;
-        launch_g2p_adj(La, src, StateRef{REF_RING, k + 1}, k == 0, k);
-      }
-      if (Lm.n_items > n_ring) {
-        Launch Lb = Lm;
-        Lb.item_offset += n_ring;
-        Lb.n_items -= n_ring;
-        launch_g2p_adj(Lb, src, StateRef{REF_REVEND, 0}, k == 0, k);
-      }
-    }
+    // the end state of substep k (REF_REVK k+1): its kept or ring block for envs with
+    // S > k+1, the step's end checkpoint for envs whose last substep is k
+    for (auto& m : mats) launch_g2p_adj(mat_launch(L, m, k), src, StateRef{REF_REVK, k + 1}, k == 0, k);
     launch_grid_adj(L, k);
     for (auto& m : mats) launch_p2g_adj(mat_launch(L, m, k), src, k == 0, k);
   }
@@ -734,7 +766,7 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
     launch_fem_forward(L, g.d_fem, (int)g.fem_envs.size(), g.fem_nv_max, g.fem_nt_max);
     if (g.S_max > 0) {
       bin_envs(L, 0, g.P, g.cell_bits, g.key_bits, g.sort);
-      substeps_forward(L, g.mats, g.S_max, record && g.tape.cap > 0 ? &g.tape : nullptr);
+      substeps_forward(L, g.mats, g.S_max, record && g.tape.cap > 0 ? &g.tape : nullptr, record);
     }
     launch_reward_end(L, rew, record);
     return;
@@ -754,18 +786,18 @@ void enqueue_forward(Group& g, cudaStream_t st, bool record, const float* act_in
     one[0].n_gt[S] = 0;
     launch_step_begin(L, act_in, a_max, record);
     bin_envs(L, g.desc[e].poff, g.spec[e].n_particles, g.cell_bits, g.cell_bits, g.sort);
-    substeps_forward(L, one, S, nullptr);
+    substeps_forward(L, one, S, nullptr, record);
     launch_reward_end(L, rew, record);
   }
 }
 
 void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env,
-                     const ObsAdj* obs) {
+                     const ObsAdj* obs, bool kept) {
   if (g.n_envs == 0) return;
   if (!per_env) {
     FemList fem{g.d_fem, (int)g.fem_envs.size(), g.fem_nv_max, g.fem_act_max, g.fem_nt_max};
     reverse_step(group_launch(g, st), g.mats, g.S_max, rbar, agrad, n_tot, a_max, g.tape.cap > 0 ? &g.tape : nullptr,
-                 obs, fem);
+                 obs, fem, kept && g.keep_n > 0);
     return;
   }
   int fem_i = 0;

@@ -88,6 +88,17 @@ struct Group {
   double tape_budget = 0.0;
   GridTape tape{nullptr, nullptr, nullptr, nullptr, 0, 0, 0};  // tape.cap == 0: no tape
   size_t tape_mp_cap = 0, tape_list_cap = 0, tape_slot_cap = 0, tape_cursor_cap = 0;
+  // Kept substep states: with a grid tape, the forward pass of a recorded step writes its
+  // substep states to slot (t mod keep_n) of every environment's keep buffer instead of
+  // running in place, so the reverse pass of the last keep_n recorded steps skips their
+  // recompute.
+  // The owner sets keep_frac (share of the memory free after the tape, less keep_reserve
+  // bytes it allocates later; 0: none); group_build sizes keep_n (at most tape_T;
+  // MPM_KEEP_STEPS caps it, for tests).
+  double keep_frac = 0.0, keep_reserve = 0.0;
+  int keep_n = 0;
+  float* keep = nullptr;
+  size_t keep_cap = 0;  // floats
   void release();
 };
 
@@ -118,7 +129,9 @@ struct TuneTimes {
 cudaError_t autotune_scatter(Group& g, cudaStream_t st, int trials, TuneTimes* t);
 // One reverse control step of every environment (step index from the device counters).
 // obs: adjoints of the task observations at the step boundaries, or NULL.
+// kept: the step is among the last g.keep_n recorded, whose substep states the forward pass
+// kept (every environment of the group is at the same step): no recompute.
 void enqueue_reverse(Group& g, cudaStream_t st, const float* rbar, float* agrad, int n_tot, int a_max, bool per_env,
-                     const ObsAdj* obs = nullptr);
+                     const ObsAdj* obs = nullptr, bool kept = false);
 
 }  // namespace mpm

@@ -112,8 +112,26 @@ __device__ __forceinline__ int ref_slot(const EnvCtr& c, int kind) {
   }
 }
 
+// Whether the step being reversed had its substep states kept by the forward pass: the last
+// keep_n recorded steps did (the reverse pass leaves live at base + T).
+__device__ __forceinline__ bool rev_kept(const EnvDesc& e, const EnvCtr& c) {
+  return e.keep_n > 0 && c.live - c.base - c.rev <= e.keep_n;
+}
+
 __device__ __forceinline__ float* ref_block(const EnvDesc& e, const EnvCtr& c, StateRef r) {
   if (r.kind == REF_RING) return e.ring + (long long)(r.k - 1) * e.block;
+  if (r.kind == REF_FWDK) {
+    if (r.k == 0) return e.slots + (long long)c.live * e.block;
+    if (r.k >= e.S || e.keep_n == 0) return e.slots + (long long)c.next * e.block;
+    const int m = (c.live - c.base) % e.keep_n;
+    return e.keep + ((long long)m * (e.S - 1) + (r.k - 1)) * e.block;
+  }
+  if (r.kind == REF_REVK) {
+    if (r.k == 0) return e.slots + (long long)(c.base + c.rev) * e.block;
+    if (r.k >= e.S) return e.slots + (long long)(c.base + c.rev + 1) * e.block;
+    if (rev_kept(e, c)) return e.keep + ((long long)(c.rev % e.keep_n) * (e.S - 1) + (r.k - 1)) * e.block;
+    return e.ring + (long long)(r.k - 1) * e.block;
+  }
   return e.slots + (long long)ref_slot(c, r.kind) * e.block;
 }
 
@@ -2022,7 +2040,7 @@ void launch_p2g(const Launch& L, StateRef src, bool use_perm, int k, const GridT
   // a conditional rebuild (all its CTAs exit at once when the tape kept the grid) is timed
   // as "other", so the P2G class holds only full scatters
   Timed tm_(skip_kept ? KC_OTHER : KC_P2G, L.stream);
-  const int rev = src.kind == REF_RING || src.kind == REF_REV ? 1 : 0;
+  const int rev = src.kind == REF_RING || src.kind == REF_REV || src.kind == REF_REVK ? 1 : 0;
   if (L.sc_box == kScBoxLarge) p2g_dispatch<kScBoxLarge>(L, src, use_perm, k, rev, skip_kept);
   else if (L.sc_box == kScBoxWarp) p2g_dispatch<kScBoxWarp>(L, src, use_perm, k, rev, skip_kept);
   else p2g_dispatch<kScBoxSmall>(L, src, use_perm, k, rev, skip_kept);
@@ -2048,7 +2066,7 @@ void launch_g2p(const Launch& L, StateRef src, StateRef dst, bool use_perm, int 
   (void)k;
   if (L.n_items == 0) return;
   Timed tm_(KC_G2P, L.stream);
-  const int rev = (dst.kind == REF_RING) ? 1 : 0;
+  const int rev = (dst.kind == REF_RING || dst.kind == REF_REVK) ? 1 : 0;
   switch (L.material) {
     case MAT_NEOHOOKEAN: k_g2p<MAT_NEOHOOKEAN><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls, L.g2p_stage); break;
     case MAT_VONMISES: k_g2p<MAT_VONMISES><<<L.n_items, kBlock, 0, L.stream>>>(L.envs, L.items, L.item_offset, src, dst, use_perm ? 1 : 0, rev, L.wait_polls, L.g2p_stage); break;

@@ -7,6 +7,9 @@
 //           n_pad particles each (x0..2, v0..2, C00..C22, H00..H22 with H = F - I), then n_pad u32 meta
 //           words (caller particle id in bits 0..19, actuator group + 1 in bits 20..31)
 //   ring    S-1 blocks of the same layout: substep states recomputed in reverse mode
+//   keep    keep_n slots of S-1 blocks each: the substep states of the last keep_n recorded
+//           control steps, written by the forward pass (step t in slot t mod keep_n), so the
+//           reverse pass reads them instead of recomputing (none when keep_n == 0)
 //   adj     two 24-component adjoint blocks (no meta)
 //   perm    per slot, the binning permutation computed at that slot's step start
 //   grid_*  G^3 float4 nodes each, node (ix, iy, iz) at (iz*G + iy)*G + ix
@@ -86,6 +89,7 @@ struct EnvDesc {
   float* slots;
   long long block;  // floats per state block = 25 * n_pad
   float* ring;
+  float* keep;      // keep_n * (S - 1) blocks, or NULL
   float* adj0;
   float* adj1;
   unsigned* perm;
@@ -106,7 +110,7 @@ struct EnvDesc {
   float* agrad_env;       // [T][A] action gradients
   long long poff;     // offset of this env's particles in the batch's global index space
   unsigned key_env;   // environment index placed in the high bits of the binning key
-  int pad_;
+  int keep_n;         // recorded control steps whose substep states are kept (0: none)
 };
 
 constexpr int kMatFem = 4;  // material id of tetrahedral-FEM environments
@@ -127,7 +131,13 @@ enum : int {
   REF_NEXT = 1,  // ctr.next
   REF_REV = 2,   // ctr.base + ctr.rev (start of the step being reversed)
   REF_RING = 3,  // ring block k-1 for substep index k >= 1
-  REF_REVEND = 4 // ctr.base + ctr.rev + 1 (end of the step being reversed)
+  REF_REVEND = 4, // ctr.base + ctr.rev + 1 (end of the step being reversed)
+  REF_FWDK = 5,   // the state after k substeps of the control step being recorded: ctr.live
+                  // (k = 0), ctr.next (k = S), else keep slot (t mod keep_n) block k-1 with
+                  // t = live - base, or ctr.next in place when no states are kept
+  REF_REVK = 6    // the state after k substeps of the step being reversed: the step's start
+                  // (k = 0) and end (k = S) checkpoints, else its kept block when the step is
+                  // among the last keep_n recorded, or ring block k-1 (recomputed)
 };
 
 struct StateRef {

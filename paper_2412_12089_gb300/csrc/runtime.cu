@@ -59,9 +59,9 @@ struct mpm_ctx {
   int bwd_T = 0, bwd_next = -1;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t g_fwd[2] = {nullptr, nullptr};
-  cudaGraphExec_t g_rev = nullptr;
+  cudaGraphExec_t g_rev[2] = {nullptr, nullptr};  // reverse step: recomputing, on kept states
   long long g_fwd_kernels[2] = {0, 0};
-  long long g_rev_kernels = 0;
+  long long g_rev_kernels[2] = {0, 0};
   long long launches = 0;        // kernels this context launched (graph replays included)
   int time_kc = 0;               // kernel class timed with events (0 = none, -1 = all)
   std::vector<cudaEvent_t> ev;   // start/stop pairs of timed launches
@@ -163,9 +163,11 @@ void body_fwd(mpm_ctx* c, cudaStream_t st, void* arg) {
 
 ObsAdj obs_of(const mpm_ctx* c) { return ObsAdj{c->obs_adj, c->obs_on, c->obs_dim, c->nsub_max, c->n_envs}; }
 
-void body_rev(mpm_ctx* c, cudaStream_t st, void*) {
+// arg: bool, the step's substep states were kept by the forward pass
+void body_rev(mpm_ctx* c, cudaStream_t st, void* arg) {
   const ObsAdj o = obs_of(c);
-  enqueue_reverse(c->g, st, c->rbar, c->agrad, c->n_envs, c->A_max, c->per_env, c->obs_adj ? &o : nullptr);
+  enqueue_reverse(c->g, st, c->rbar, c->agrad, c->n_envs, c->A_max, c->per_env, c->obs_adj ? &o : nullptr,
+                  *(bool*)arg);
 }
 
 Launch io_launch(mpm_ctx* ctx, cudaStream_t st) {
@@ -187,6 +189,7 @@ int64_t mpm_n_particles(const mpm_ctx* ctx) { return ctx ? ctx->P : 0; }
 int32_t mpm_action_dim(const mpm_ctx* ctx) { return ctx ? ctx->A_max : 0; }
 int32_t mpm_tape_length(const mpm_ctx* ctx) { return ctx ? ctx->h_live - ctx->h_base : 0; }
 int64_t mpm_device_bytes(const mpm_ctx* ctx) { return ctx ? (int64_t)ctx->total_bytes : 0; }
+int32_t mpm_kept_steps(const mpm_ctx* ctx) { return ctx ? (int32_t)ctx->g.keep_n : 0; }
 
 mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* opt, mpm_ctx** out) {
   if (!out) return MPM_ERR_INVALID_ARG;
@@ -270,6 +273,10 @@ mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* 
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
     const double frac = o.grid_tape_fraction > 0.0f ? std::min(1.0, (double)o.grid_tape_fraction) : 0.5;
     ctx->g.tape_budget = frac * (double)free_b;
+    // kept substep states: a share of what the tape leaves, less the staging buffers below
+    ctx->g.keep_frac = o.keep_fraction < 0.0f ? 0.0 : (o.keep_fraction > 0.0f ? std::min(1.0, (double)o.keep_fraction) : 0.8);
+    ctx->g.keep_reserve = (double)sizeof(float) * (double)P * (kComp + 8) +
+                          (double)sizeof(float) * o.max_steps * n_envs * (A_max + 1) * 2.0 + (1u << 30);
   }
   cudaError_t ge = group_build(ctx->g, desc, ctx->specs);
   if (ge != cudaSuccess)
@@ -295,7 +302,7 @@ mpm_status mpm_create(const mpm_env_spec* specs, int n_envs, const mpm_options* 
     return bail(fail(ctx, MPM_ERR_CUDA, "stream"));
   ctx->total_bytes = ctx->arena_bytes + sizeof(unsigned) * P * 4 + sizeof(float) * P * kComp +
                      sizeof(uint2) * ctx->g.tiles + (tape ? sizeof(float) * (size_t)ctx->T_cap * n_envs * (A_max + 1) : 0) +
-                     (size_t)ctx->g.tape.cap * (64 * sizeof(float4) + sizeof(uint2));
+                     (size_t)ctx->g.tape.cap * (64 * sizeof(float4) + sizeof(uint2)) + sizeof(float) * ctx->g.keep_cap;
   *out = ctx;
   return MPM_OK;
 }
@@ -305,7 +312,8 @@ void mpm_destroy(mpm_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (auto& g : ctx->g_fwd)
     if (g) cudaGraphExecDestroy(g);
-  if (ctx->g_rev) cudaGraphExecDestroy(ctx->g_rev);
+  for (auto& g : ctx->g_rev)
+    if (g) cudaGraphExecDestroy(g);
   for (auto e : ctx->ev) cudaEventDestroy(e);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   ctx->g.release();
@@ -437,9 +445,12 @@ static mpm_status bwd_begin(mpm_ctx* ctx, const float* xb, const float* vb, cons
   return MPM_OK;
 }
 
-// One reverse step (the next one down), through the captured reverse-step graph.
-static mpm_status bwd_step(mpm_ctx* ctx, cudaStream_t st) {
-  return run_graph_or_direct(ctx, &ctx->g_rev, &ctx->g_rev_kernels, st, body_rev, nullptr);
+// One reverse step (the next one down, t of T recorded), through the captured reverse-step
+// graph: the one without the recompute when the forward pass kept the step's substep states.
+static mpm_status bwd_step(mpm_ctx* ctx, cudaStream_t st, int t, int T) {
+  bool kept = ctx->g.keep_n > 0 && !ctx->per_env && T - t <= ctx->g.keep_n;
+  const int i = kept ? 1 : 0;
+  return run_graph_or_direct(ctx, &ctx->g_rev[i], &ctx->g_rev_kernels[i], st, body_rev, &kept);
 }
 
 // End of a reverse pass: the initial state's observation adjoint (when set), then the initial
@@ -486,7 +497,7 @@ mpm_status mpm_backward(mpm_ctx* ctx, const float* xb, const float* vb, const fl
   else
     CK(cudaMemsetAsync(ctx->rbar, 0, sizeof(float) * T * ctx->n_envs, st));
   for (int t = T - 1; t >= 0; --t)
-    if ((s = bwd_step(ctx, st)) != MPM_OK) return s;
+    if ((s = bwd_step(ctx, st, t, T)) != MPM_OK) return s;
   if ((s = bwd_end(ctx, xb0, vb0, Cb0, Fb0, pose_grad0, st)) != MPM_OK) return s;
   if (action_grad)
     CK(cudaMemcpyAsync(action_grad, ctx->agrad, sizeof(float) * (size_t)T * ctx->n_envs * ctx->A_max,
@@ -534,7 +545,7 @@ mpm_status mpm_backward_step(mpm_ctx* ctx, const float* reward_adj, const float*
       CK(cudaMemsetAsync(ctx->obs_on, 0, sizeof(int), st));
     }
   }
-  const mpm_status s = bwd_step(ctx, st);
+  const mpm_status s = bwd_step(ctx, st, t, ctx->bwd_T);
   if (s != MPM_OK) return s;
   if (action_grad)
     CK(cudaMemcpyAsync(action_grad, ctx->agrad + (size_t)t * ne * ctx->A_max, sizeof(float) * ne * ctx->A_max,
@@ -677,10 +688,11 @@ mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* m
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
-  if (ctx->g_rev) {
-    cudaGraphExecDestroy(ctx->g_rev);
-    ctx->g_rev = nullptr;
-  }
+  for (auto& g : ctx->g_rev)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
   for (int m = 0; m < 4; ++m) {
     if (box_out) box_out[m] = 0;
     for (int b = 0; b < kNScatterBoxes && ms_out; ++b) ms_out[kNScatterBoxes * m + b] = 0.0f;

@@ -50,7 +50,8 @@ class MpmEnvSpec(ct.Structure):
 
 class MpmOptions(ct.Structure):
     _fields_ = [("max_steps", ct.c_int32), ("per_env_launch", ct.c_int32), ("use_graphs", ct.c_int32),
-                ("chunk", ct.c_int32), ("device", ct.c_int32), ("grid_tape_fraction", ct.c_float)]
+                ("chunk", ct.c_int32), ("device", ct.c_int32), ("grid_tape_fraction", ct.c_float),
+                ("keep_fraction", ct.c_float)]
 
 
 class MpmServerOptions(ct.Structure):
@@ -92,6 +93,7 @@ def lib():
         "mpm_action_dim": (i32, [_P]),
         "mpm_tape_length": (i32, [_P]),
         "mpm_device_bytes": (i64, [_P]),
+        "mpm_kept_steps": (i32, [_P]),
         "mpm_last_error": (ct.c_char_p, [_P]),
         "mpm_set_state": (i32, [_P, _P, _P, _P, _P, _P, _P, _P]),
         "mpm_get_state": (i32, [_P, _P, _P, _P, _P, _P, _P]),
@@ -217,10 +219,12 @@ def check(code, ctx=None, srv=None):
 
 # ----------------------------------------------------------------------------- same-name wrappers
 
-def mpm_create(specs, max_steps=0, per_env_launch=False, use_graphs=True, chunk=0, device=0, grid_tape_fraction=0.0):
+def mpm_create(specs, max_steps=0, per_env_launch=False, use_graphs=True, chunk=0, device=0, grid_tape_fraction=0.0,
+               keep_fraction=0.0):
     cs = [to_c_spec(s) if not isinstance(s, MpmEnvSpec) else s for s in specs]  # alive through the call
     arr = (MpmEnvSpec * len(specs))(*cs)
-    opt = MpmOptions(max_steps, 1 if per_env_launch else 0, 1 if use_graphs else 0, chunk, device, grid_tape_fraction)
+    opt = MpmOptions(max_steps, 1 if per_env_launch else 0, 1 if use_graphs else 0, chunk, device, grid_tape_fraction,
+                     keep_fraction)
     h = _P()
     code = lib().mpm_create(arr, len(specs), ct.byref(opt), ct.byref(h))
     if code != MPM_OK:
@@ -343,6 +347,10 @@ def mpm_tape_length(ctx):
 
 def mpm_device_bytes(ctx):
     return lib().mpm_device_bytes(ctx)
+
+
+def mpm_kept_steps(ctx):
+    return lib().mpm_kept_steps(ctx)
 
 
 KERNEL_CLASS = {"p2g": 1, "grid": 2, "g2p": 3, "g2p_adj": 4, "grid_adj": 5, "p2g_adj": 6, "bin": 7, "other": 8}
