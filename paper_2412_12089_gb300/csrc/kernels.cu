@@ -135,6 +135,14 @@ __device__ __forceinline__ float* ref_block(const EnvDesc& e, const EnvCtr& c, S
   return e.slots + (long long)ref_slot(c, r.kind) * e.block;
 }
 
+// The blocks of two state references, resolved by one thread and published in shared memory
+// by the caller's next barrier (G2P: resolved in every thread, the resolution's branches cost
+// it 72 bytes of spills; out of line in this one thread they cost nothing).
+__device__ __noinline__ void resolve_refs(const EnvDesc& s, const EnvCtr& c, StateRef r0, StateRef r1, float** blk) {
+  blk[0] = ref_block(s, c, r0);
+  blk[1] = ref_block(s, c, r1);
+}
+
 // slot whose pose / actions / permutation belong to the running control step
 __device__ __forceinline__ int step_slot(const EnvCtr& c, int rev) { return rev ? c.base + c.rev : c.live; }
 
@@ -846,9 +854,12 @@ __global__ void __launch_bounds__(kBlock, 8) k_g2p(const EnvDesc* __restrict__ e
   __shared__ alignas(8) unsigned long long bar;
   const WorkItem it = items[item_off + blockIdx.x];
   if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __shared__ float* blk[2];
   load_env(envs, it.env, e, c);  // its barriers also publish the mbarrier's initialisation
-  const float* b = ref_block(e, c, src);
-  float* o = ref_block(e, c, dst);
+  if (threadIdx.x == 0) resolve_refs(e, c, src, dst, blk);
+  __syncthreads();
+  const float* b = blk[0];
+  float* o = blk[1];
   const int sslot = step_slot(c, rev);
   const unsigned* perm = use_perm ? e.perm + (long long)sslot * e.n_pad : nullptr;
   const long long np = e.n_pad;

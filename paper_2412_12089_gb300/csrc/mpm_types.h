@@ -89,7 +89,6 @@ struct EnvDesc {
   float* slots;
   long long block;  // floats per state block = 25 * n_pad
   float* ring;
-  float* keep;      // keep_n * (S - 1) blocks, or NULL
   float* adj0;
   float* adj1;
   unsigned* perm;
@@ -111,6 +110,7 @@ struct EnvDesc {
   long long poff;     // offset of this env's particles in the batch's global index space
   unsigned key_env;   // environment index placed in the high bits of the binning key
   int keep_n;         // recorded control steps whose substep states are kept (0: none)
+  float* keep;        // keep_n * (S - 1) blocks, or NULL
 };
 
 constexpr int kMatFem = 4;  // material id of tetrahedral-FEM environments
