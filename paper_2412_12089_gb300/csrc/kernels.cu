@@ -593,10 +593,9 @@ struct NodeFwd {
 
 // Forward node update; records the trace needed by its adjoint.
 // Signed distance from world point (x, y, z) to a capsule (radius R, half length hl along the
-// body x axis) at pose q.
-__device__ __forceinline__ float capsule_distance(float R, float hl, const float* q, float x, float y, float z) {
-  float st, ct;
-  sincosf(q[3], &st, &ct);
+// body x axis) at pose q, with st, ct = sin, cos of its angle q[3].
+__device__ __forceinline__ float capsule_distance(float R, float hl, const float* q, float st, float ct, float x,
+                                                  float y, float z) {
   const float rx = x - q[0], ry = y - q[1], rz = z - q[2];
   const float px = ct * rx + st * ry, py = -st * rx + ct * ry;
   const float ex = px - fminf(fmaxf(px, -hl), hl);
@@ -605,20 +604,25 @@ __device__ __forceinline__ float capsule_distance(float R, float hl, const float
 
 // Union of capsules: the nearest capsule to the node (smallest signed distance, the first on a
 // tie) decides the contact.  q, u hold capsule 0's pose and velocity on entry and the chosen
-// capsule's on return; ps is the slot's pose vector, kdt the substep's time since the slot.
+// capsule's on return, sc = (sin, cos) of capsule 0's angle on entry and of the chosen one's
+// on return; ps is the slot's pose vector, kdt the substep's time since the slot.
 __device__ __forceinline__ int nearest_capsule(const EnvDesc& e, const float* ps, float kdt, float x, float y,
-                                               float z, float* q, float* u) {
+                                               float z, float* q, float* u, float* sc) {
   const float R = e.coll_dims[0], hl = e.coll_dims[1];
-  float best = capsule_distance(R, hl, q, x, y, z);
+  float best = capsule_distance(R, hl, q, sc[0], sc[1], x, y, z);
   int which = 0;
+  float bs = sc[0], bc = sc[1];
   for (int j = 1; j < e.n_caps; ++j) {
-    float qj[4];
+    float qj[4], sj, cj;
 #pragma unroll
     for (int i = 0; i < 4; ++i) qj[i] = ps[4 * j + i] + kdt * e.acc[ACC_U + 4 * j + i];
-    const float dj = capsule_distance(R, hl, qj, x, y, z);
+    sincosf(qj[3], &sj, &cj);
+    const float dj = capsule_distance(R, hl, qj, sj, cj, x, y, z);
     if (dj < best) {
       best = dj;
       which = j;
+      bs = sj;
+      bc = cj;
     }
   }
   if (which != 0) {
@@ -627,15 +631,19 @@ __device__ __forceinline__ int nearest_capsule(const EnvDesc& e, const float* ps
       u[i] = e.acc[ACC_U + 4 * which + i];
       q[i] = ps[4 * which + i] + kdt * u[i];
     }
+    sc[0] = bs;
+    sc[1] = bc;
   }
   return which;
 }
 
 // q, u: the collider pose and velocity (capsule 0 for the capsule union, replaced by the
-// nearest capsule's, whose index is t.which); ps, kdt as for nearest_capsule.
+// nearest capsule's, whose index is t.which); ps, kdt as for nearest_capsule; st0, ct0: sin and
+// cos of q[3] on entry (the same for every node of the environment at this substep, so the
+// callers form them once per tile).
 template <bool kAdj>
 __device__ __forceinline__ void node_forward(const EnvDesc& e, int ix, int iy, int iz, float4 mp, float* q, float* u,
-                                             const float* ps, float kdt, NodeFwd& t) {
+                                             const float* ps, float kdt, float st0, float ct0, NodeFwd& t) {
   const float inv_m = 1.0f / mp.x;
   t.v0[0] = mp.y * inv_m;
   t.v0[1] = mp.z * inv_m;
@@ -647,14 +655,15 @@ __device__ __forceinline__ void node_forward(const EnvDesc& e, int ix, int iy, i
   t.branch = 0;
   t.which = 0;
   if (e.coll_kind != COLL_NONE) {
-    if (e.coll_kind == COLL_CAPSULES) t.which = nearest_capsule(e, ps, kdt, ix * e.dx, iy * e.dx, iz * e.dx, q, u);
+    float sc[2] = {st0, ct0};
+    if (e.coll_kind == COLL_CAPSULES) t.which = nearest_capsule(e, ps, kdt, ix * e.dx, iy * e.dx, iz * e.dx, q, u, sc);
     Coll cl;
     cl.kind = e.coll_kind;
 #pragma unroll
     for (int i = 0; i < 4; ++i) cl.dims[i] = e.coll_dims[i];
     cl.mu = e.coll_mu;
     cl.alpha = e.alpha;
-    contact_eval<kAdj>(cl, ix * e.dx, iy * e.dx, iz * e.dx, q, u, t.ct);
+    contact_eval<kAdj>(cl, ix * e.dx, iy * e.dx, iz * e.dx, q, u, sc[0], sc[1], t.ct);
     t.sc = t.ct.d > 0.0f ? expf(-e.alpha * t.ct.d) : 1.0f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) t.vr[i] = t.v1[i] - t.ct.vb[i];
@@ -767,6 +776,8 @@ __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, 
     const EnvCtr c = *e.ctr;
     float q0[4], u0[4];
     const float* ps = step_pose(e, c, rev, k, q0, u0);
+    float st0, ct0;
+    sincosf(q0[3], &st0, &ct0);
     const float kdt = (float)k * e.dt;
     const int TG = e.G >> 2;
     const int tz = at.y / (TG * TG), ty = (at.y / TG) % TG, tx = at.y % TG;
@@ -781,7 +792,7 @@ __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, 
       if (mp.x > 0.0f) {
         NodeFwd t;
         float q[4] = {q0[0], q0[1], q0[2], q0[3]}, u[4] = {u0[0], u0[1], u0[2], u0[3]};
-        node_forward<false>(e, ix, iy, iz, mp, q, u, ps, kdt, t);
+        node_forward<false>(e, ix, iy, iz, mp, q, u, ps, kdt, st0, ct0, t);
         out.x = (t.zero & 1u) ? 0.0f : t.v3[0];
         out.y = (t.zero & 2u) ? 0.0f : t.v3[1];
         out.z = (t.zero & 4u) ? 0.0f : t.v3[2];
@@ -1361,6 +1372,8 @@ __global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ en
     const EnvCtr c = *e.ctr;
     float q0[4], u0[4];
     const float* ps = step_pose(e, c, 1, k, q0, u0);
+    float st0, ct0;
+    sincosf(q0[3], &st0, &ct0);
     const float kdt = (float)k * e.dt;
     const int TG = e.G >> 2;
     const int tz = at.y / (TG * TG), ty = (at.y / TG) % TG, tx = at.y % TG;
@@ -1384,7 +1397,7 @@ __global__ void __launch_bounds__(256) k_grid_adj(const EnvDesc* __restrict__ en
         const float4 vd = e.grid_vb[id];
         NodeFwd t;
         float q[4] = {q0[0], q0[1], q0[2], q0[3]}, u[4] = {u0[0], u0[1], u0[2], u0[3]};
-        node_forward<true>(e, ix, iy, iz, mp, q, u, ps, kdt, t);
+        node_forward<true>(e, ix, iy, iz, mp, q, u, ps, kdt, st0, ct0, t);
         const bool ident = t.zero == 0u && !t.ground && (e.coll_kind == COLL_NONE || t.sc == 0.0f);
         if (ident) {
           // the node update is the identity map on velocities here: p-bar = v-bar/m exactly,
@@ -2105,9 +2118,23 @@ void launch_g2p_adj(const Launch& L, StateRef src, StateRef nxt, bool use_perm, 
   else g2p_adj_dispatch<kScBoxSmall>(L, src, nxt, use_perm, k);
 }
 
+// CTAs of k_grid_adj that fit on the device at once (0 if the runtime cannot say).  The grid
+// adjoint's persistent warps stop at this: its registers hold fewer CTAs per SM than the grid
+// update's, whose autotuned CTA count the launch shares, and CTAs beyond one resident wave
+// only add a tail.
+static int grid_adj_resident() {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_adj, 256, 0) != cudaSuccess)
+    return 0;
+  return sms * per_sm;
+}
+
 void launch_grid_adj(const Launch& L, int k) {
+  static const int resident = grid_adj_resident();
   Timed tm_(KC_GRID_ADJ, L.stream);
-  k_grid_adj<<<L.grid_blocks, 256, 0, L.stream>>>(L.envs, L.active, L.active_n, k);
+  const int blocks = resident > 0 ? std::min(L.grid_blocks, resident) : L.grid_blocks;
+  k_grid_adj<<<blocks, 256, 0, L.stream>>>(L.envs, L.active, L.active_n, k);
 }
 
 void launch_p2g_adj(const Launch& L, StateRef src, bool use_perm, int k) {

@@ -477,13 +477,27 @@ struct Coll {
   float mu, alpha;
 };
 
+// Length of the outside part (mx, my, mz) = max(q, 0) of a box SDF, rounded the same way
+// wherever it is formed (the container compares these lengths between its boxes).
+MPM_HD float box_outside_len(float mx, float my, float mz) {
+  return sqrtf(__fmaf_rn(mz, mz, __fmaf_rn(my, my, __fmul_rn(mx, mx))));
+}
+
+// Signed distance of point p to the box of half extents h, alone: the d of sdf_box, bit for
+// bit (outside: the length of max(q, 0); inside: the largest q).
+MPM_HD float box_distance(float px, float py, float pz, float hx, float hy, float hz) {
+  const float qx = fabsf(px) - hx, qy = fabsf(py) - hy, qz = fabsf(pz) - hz;
+  if (qx > 0.0f || qy > 0.0f || qz > 0.0f) return box_outside_len(fmaxf(qx, 0.0f), fmaxf(qy, 0.0f), fmaxf(qz, 0.0f));
+  return (qx >= qy && qx >= qz) ? qx : (qy >= qz ? qy : qz);
+}
+
 // Box SDF in its frame: d, gradient n, Hessian H (symmetric, 6 entries xx,xy,xz,yy,yz,zz).
 MPM_HD void sdf_box(float px, float py, float pz, float hx, float hy, float hz, float& d, float* n, float* H) {
   float sx = px >= 0.0f ? 1.0f : -1.0f, sy = py >= 0.0f ? 1.0f : -1.0f, sz = pz >= 0.0f ? 1.0f : -1.0f;
   float qx = fabsf(px) - hx, qy = fabsf(py) - hy, qz = fabsf(pz) - hz;
   if (qx > 0.0f || qy > 0.0f || qz > 0.0f) {
     float mx = fmaxf(qx, 0.0f), my = fmaxf(qy, 0.0f), mz = fmaxf(qz, 0.0f);
-    float l = sqrtf(mx * mx + my * my + mz * mz);
+    float l = box_outside_len(mx, my, mz);
     float r = 1.0f / l;
     d = l;
     n[0] = sx * mx * r; n[1] = sy * my * r; n[2] = sz * mz * r;
@@ -530,23 +544,29 @@ MPM_HD void sdf_body(const Coll& c, float px, float py, float pz, float& d, floa
     sdf_box(px, py, pz, c.dims[0], c.dims[1], c.dims[2], d, nb, Hb);
   } else {
     // open-top container: floor and four walls; the walls reach down through the floor
-    // (z in [-az - w, az]) and overlap at the vertical edges, so no two boxes share a face
-    float a = c.dims[0], w = c.dims[1], az = c.dims[2];
-    float hw = 0.5f * w, hz = az + hw;
-    sdf_box(px, py, pz + az + hw, a + w, a + w, hw, d, nb, Hb);
-    float dk, nk[3], Hk[6];
-#define MPM_WALL(OX, OY, HX, HY)                                             \
-  sdf_box(px - (OX), py - (OY), pz + hw, HX, HY, hz, dk, nk, Hk);            \
-  if (dk < d) {                                                              \
-    d = dk;                                                                  \
-    nb[0] = nk[0]; nb[1] = nk[1]; nb[2] = nk[2];                             \
-    for (int i_ = 0; i_ < 6; ++i_) Hb[i_] = Hk[i_];                          \
+    // (z in [-az - w, az]) and overlap at the vertical edges, so no two boxes share a face.
+    // The nearest box (the first on a tie, floor first) gives d, its gradient and Hessian:
+    // the five distances are compared alone, and only the chosen box is evaluated in full.
+    const float a = c.dims[0], w = c.dims[1], az = c.dims[2];
+    const float hw = 0.5f * w, hz = az + hw, ao = a + hw, aw = a + w;
+    // the chosen box: the point in its frame (bx, by, bz) and its half extents (hx, hy, hzb)
+    float bx = px, by = py, bz = pz + az + hw, hx = aw, hy = aw, hzb = hw;
+    float best = box_distance(bx, by, bz, hx, hy, hzb);
+#define MPM_WALL(OX, OY, HX, HY)                                   \
+  {                                                                \
+    const float wx = px - (OX), wy = py - (OY), wz = pz + hw;      \
+    const float dk = box_distance(wx, wy, wz, HX, HY, hz);         \
+    if (dk < best) {                                               \
+      best = dk;                                                   \
+      bx = wx; by = wy; bz = wz; hx = (HX); hy = (HY); hzb = hz;   \
+    }                                                              \
   }
-    MPM_WALL(a + hw, 0.0f, hw, a + w)
-    MPM_WALL(-(a + hw), 0.0f, hw, a + w)
-    MPM_WALL(0.0f, a + hw, a + w, hw)
-    MPM_WALL(0.0f, -(a + hw), a + w, hw)
+    MPM_WALL(ao, 0.0f, hw, aw)
+    MPM_WALL(-ao, 0.0f, hw, aw)
+    MPM_WALL(0.0f, ao, aw, hw)
+    MPM_WALL(0.0f, -ao, aw, hw)
 #undef MPM_WALL
+    sdf_box(bx, by, bz, hx, hy, hzb, d, nb, Hb);
   }
 }
 
@@ -559,11 +579,11 @@ struct Contact {
   float vb[3];    // body velocity at the node
 };
 
-// Collider at world point (x, y, z), pose q = (c, theta), pose velocity u = (v_c, omega).
+// Collider at world point (x, y, z), pose q = (c, theta), pose velocity u = (v_c, omega);
+// st, ct = sin theta, cos theta (the caller's, formed once for all nodes that share the pose).
 template <bool kAdjoint>
-MPM_HD void contact_eval(const Coll& c, float x, float y, float z, const float* q, const float* u, Contact& o) {
-  float st, ct;
-  sincosf(q[3], &st, &ct);
+MPM_HD void contact_eval(const Coll& c, float x, float y, float z, const float* q, const float* u, float st, float ct,
+                         Contact& o) {
   float rx = x - q[0], ry = y - q[1], rz = z - q[2];
   float px = ct * rx + st * ry, py = -st * rx + ct * ry, pz = rz;  // R(-theta) r
   float nb[3], Hb[6];
