@@ -54,8 +54,8 @@ MEASURED_TRAFFIC = {
     # ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of launches over 2,097,152
     # binned fluid particles (256 envs x 8192, 64^3; state 210 MB, above L2), in bytes per
     # particle, scaled by particle count
-    "g2p_adj": (210.9, "55fed9c2f11a821b"),  # 512-cell sort, mean of 2 adjoint-substep launches
-    "p2g": (95.4, "55fed9c2f11a821b"),       # 512-cell sort, mean of 18 launches
+    "g2p_adj": (209.1, "27eab834d0514a19"),  # 512-cell sort, one adjoint substep (k = 3) of the full capture
+    "p2g": (107.3, "27eab834d0514a19"),      # 512-cell sort, mean of 21 launches (autotuner trials: state not in L2)
 }
 
 
