@@ -752,9 +752,9 @@ __device__ __forceinline__ int tape_step_rev(const EnvDesc* envs, int env0, cons
 
 // Recording (rec.mp set): the active tiles' (m, p) are also copied into the tape slot that
 // k_tape_alloc reserved for this substep.
-__global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, const uint2* __restrict__ active,
-                                              const int* __restrict__ active_n, int k, int mode, int rev,
-                                              GridTape rec, int env0) {
+__global__ void __launch_bounds__(256, 3) k_grid(const EnvDesc* __restrict__ envs, const uint2* __restrict__ active,
+                                                 const int* __restrict__ active_n, int k, int mode, int rev,
+                                                 GridTape rec, int env0) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -769,30 +769,41 @@ __global__ void __launch_bounds__(256) k_grid(const EnvDesc* __restrict__ envs, 
       first = sl.x;
     }
   }
+  // A tile is a chain of dependent loads (list entry, descriptor, counters and pose, nodes):
+  // the next tile's list entry is read one tile ahead, and a tile's two nodes per lane are
+  // read before its counters and pose, so that those loads overlap.
+  uint2 at_next = warp < n ? active[warp] : make_uint2(0u, 0u);
   for (int w = warp; w < n; w += nwarps) {
-    const uint2 at = active[w];
+    const uint2 at = at_next;
+    if (w + nwarps < n) at_next = active[w + nwarps];
     if (keep && lane == 0) rec.list[first + w] = at;
     const EnvDesc& e = envs[at.x];
+    const int TG = e.G >> 2;
+    const int tz = at.y / (TG * TG), ty = (at.y / TG) % TG, tx = at.y % TG;
+    float4 mp[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int l = lane + 32 * h;
+      const int ix = tx * 4 + (l & 3), iy = ty * 4 + ((l >> 2) & 3), iz = tz * 4 + (l >> 4);
+      mp[h] = e.grid_mp[((long long)iz * e.G + iy) * e.G + ix];
+    }
     const EnvCtr c = *e.ctr;
     float q0[4], u0[4];
     const float* ps = step_pose(e, c, rev, k, q0, u0);
     float st0, ct0;
     sincosf(q0[3], &st0, &ct0);
     const float kdt = (float)k * e.dt;
-    const int TG = e.G >> 2;
-    const int tz = at.y / (TG * TG), ty = (at.y / TG) % TG, tx = at.y % TG;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int l = lane + 32 * h;
       const int ix = tx * 4 + (l & 3), iy = ty * 4 + ((l >> 2) & 3), iz = tz * 4 + (l >> 4);
       const long long id = ((long long)iz * e.G + iy) * e.G + ix;
-      const float4 mp = e.grid_mp[id];
-      if (keep) rec.mp[(first + w) * 64 + l] = mp;
+      if (keep) rec.mp[(first + w) * 64 + l] = mp[h];
       float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (mp.x > 0.0f) {
+      if (mp[h].x > 0.0f) {
         NodeFwd t;
         float q[4] = {q0[0], q0[1], q0[2], q0[3]}, u[4] = {u0[0], u0[1], u0[2], u0[3]};
-        node_forward<false>(e, ix, iy, iz, mp, q, u, ps, kdt, st0, ct0, t);
+        node_forward<false>(e, ix, iy, iz, mp[h], q, u, ps, kdt, st0, ct0, t);
         out.x = (t.zero & 1u) ? 0.0f : t.v3[0];
         out.y = (t.zero & 2u) ? 0.0f : t.v3[1];
         out.z = (t.zero & 4u) ? 0.0f : t.v3[2];
