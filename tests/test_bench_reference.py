@@ -21,3 +21,18 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_roofline_traffic_belongs_to_these_kernel_sources():
+    """The DRAM traffic bench.py reports beside the roofline comes from an ncu capture of the
+    kernel sources as they are now; a kernel change must be recaptured before it is reported
+    (bench.py then prints null), and the profile summary names the same source hash."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    h = bench.kernel_source_hash()
+    for kernel, (per_particle, src_hash) in bench.MEASURED_TRAFFIC.items():
+        assert src_hash == h, (kernel, src_hash, h)
+        assert 0 < per_particle < 1000
+    with open(os.path.join(ROOT, "profiles", "dram_traffic_fluid256_1x5.md")) as fh:
+        assert h in fh.read()
