@@ -374,9 +374,10 @@ mpm_status mpm_autotune(mpm_ctx* ctx, int32_t trials, int32_t* box_out, float* m
  * The rest of what mpm_autotune chose, after the scatter shape and with the same trials (each
  * trial writes only the grids and, for G2P, the first block of the checkpoint tape's substep
  * ring, which is scratch between reverse passes; without a tape G2P keeps the default):
- *   grid_blocks: CTAs of the persistent grid-update and grid-adjoint kernels, the fastest
- *     grid update of 304, 608, 1216 and 2432 CTAs (2, 4, 8, 16 per SM); grid_ms: [4] their
- *     fastest trials' times (ms);
+ *   grid_blocks: CTAs of the persistent grid-update kernel, the fastest grid update of 304,
+ *     608, 1216 and 2432 CTAs (2, 4, 8, 16 per SM); the grid adjoint launches as many, or
+ *     as many as fit on the device at once if fewer; grid_ms: [4] their fastest trials'
+ *     times (ms);
  *   g2p_stage: [4] by material, 1 if G2P stages each chunk's x and H in shared memory by
  *     bulk copies, 0 if it loads them directly (-1 for absent materials); g2p_ms: [4][2]
  *     fastest trial's G2P time (ms) without and with the staging.

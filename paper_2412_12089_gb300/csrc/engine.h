@@ -63,7 +63,7 @@ struct Group {
   std::vector<WorkItem> items, items_env;
   std::vector<MatGroup> mats;
   int wait_polls = -1;     // G2P's first bounded wait (test-only MPM_TEST_G2P_WAIT_POLLS; < 0: full)
-  int grid_blocks = 152 * 8;  // CTAs of the persistent grid kernels (autotuned)
+  int grid_blocks = 152 * 8;  // CTAs of the persistent grid update (autotuned); the grid adjoint caps it
   std::vector<int> env_item0, env_nitems;
   // FEM environments (their step kernels run one CTA per environment) and their extents
   std::vector<int> fem_envs;

@@ -33,7 +33,7 @@ struct Launch {
   int item_offset;       // first item (per-environment launches)
   uint2* active;         // active-tile list (env, tile)
   int* active_n;         // its length (device)
-  int grid_blocks;       // CTAs of the persistent grid kernels
+  int grid_blocks;       // CTAs of the persistent grid update (the grid adjoint caps it at one resident wave)
   int env0, n_env;       // environment range of the per-env kernels
   cudaStream_t stream;
   int sc_box = 512;      // scatter shape by the cell capacity of its counting sort: 512 or 1024
