@@ -328,6 +328,28 @@ def test_box_and_container_sdf_closed_form():
     assert abs(d - 0.003) < 1e-14 and np.allclose(n, [-1, 0, 0])
 
 
+def test_container_nearest_box_and_ties():
+    """The container is the union of a floor and four walls: its SDF is the smallest of the
+    five box distances, and a point exactly as near to two boxes takes the first of them
+    (floor, +x, -x, +y, -y), the rule both sides share.  Dyadic dimensions make the ties exact."""
+    a, w, az = 0.125, 0.03125, 0.125
+    sc = spec_for(collider="container", coll_dims=(a, w, az, 0))
+    q = np.array([0.5, 0.5, 0.25, 0.0])
+    e = 2.0 ** -7
+    # inside the cavity, e from the floor's top face and e from the +x wall's inner face
+    d, n, _, _ = orc.collider(sc, [0.5 + a - e, 0.5, 0.25 - az + e], q)
+    assert d == e and np.array_equal(n, [0.0, 0.0, 1.0])
+    # e from the -y wall and the +x wall at once: +x comes first
+    d, n, _, _ = orc.collider(sc, [0.5 + a - e, 0.5 - a + e, 0.25], q)
+    assert d == e and np.array_equal(n, [-1.0, 0.0, 0.0])
+    # nearer to the -y wall than to the +x wall: the nearest box wins whatever its order
+    d, n, _, _ = orc.collider(sc, [0.5 + a - 2 * e, 0.5 - a + e, 0.25], q)
+    assert d == e and np.array_equal(n, [0.0, 1.0, 0.0])
+    # inside the floor slab, nearer its top face than any wall: negative distance, up normal
+    d, n, _, _ = orc.collider(sc, [0.5, 0.5, 0.25 - az - e], q)
+    assert d == -e and np.array_equal(n, [0.0, 0.0, 1.0])
+
+
 @pytest.mark.parametrize("kind,dims", [("capsule", (0.03, 0.12, 0, 0)), ("box", (0.08, 0.05, 0.04, 0)),
                                        ("container", (0.1, 0.02, 0.1, 0))])
 def test_sdf_gradient_and_hessian_fd(kind, dims):
